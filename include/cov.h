@@ -1,0 +1,195 @@
+/*
+ * cov.h -- C ABI of the GB300 (sm_103a) covariance-method library.
+ *
+ * The library computes the estimated covariance matrix of the covariance
+ * method (arXiv 1303.2285, Section 2.2, Eq. 2.1-2.2): for an N x M complex
+ * input A and a P x Q sliding window, each window position (p, q) is
+ * column-stacked into the PQ-vector x (x[i + P*j] = A[p+i][q+j], 0-based),
+ * and
+ *
+ *     R = (1/K) * sum over all K = (N-P+1)(M-Q+1) positions of x * x^H
+ *
+ * (COV_MEAN; COV_SUM returns the plain sum of Eq. 2.2). R is PQ x PQ and
+ * Hermitian; the library writes both triangles, with the lower one the exact
+ * conjugate of the upper one and a zero imaginary part on the diagonal.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Complex numbers are interleaved (re, im): COV_C64 = two floats (8 bytes),
+ *   COV_C128 = two doubles (16 bytes).
+ * - A is row-major with leading dimension lda >= M (in complex elements);
+ *   R is row-major PQ x PQ, dense (leading dimension PQ).
+ * - All data pointers (A, R, G, dA, workspace, descriptor tables) are DEVICE
+ *   pointers owned by the caller, unless a parameter says "host". The library
+ *   keeps no reference to them after the call returns, never frees them, and
+ *   overwrites (never accumulates into) its outputs.
+ * - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL is
+ *   the legacy default stream). The returned status covers host-side argument
+ *   checks and launch errors only. A kernel that gives up a bounded wait
+ *   records COV_ETIMEOUT (or COV_EDEVICE) in the workspace's status word; read
+ *   it with cov_check_device_status.
+ * - No entry point falls back to a CPU implementation: every result is
+ *   computed by this library's CUDA kernels.
+ * - Entry points that take (workspace, ws_bytes) never allocate device
+ *   memory. cov_estimate and cov_estimate_backward_alloc allocate a
+ *   stream-ordered workspace (cudaMallocAsync / cudaFreeAsync) on `stream`.
+ */
+#ifndef COV_H
+#define COV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cov_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  COV_OK = 0,
+  COV_EINVAL = 1,       /* null pointer, size out of range, P > N, lda < M, ... */
+  COV_ECUDA = 2,        /* a CUDA runtime call or a kernel launch failed */
+  COV_EWORKSPACE = 3,   /* workspace missing, too small or not 256-byte aligned */
+  COV_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+  COV_EUNSUPPORTED = 5, /* valid arguments the selected algorithm cannot take */
+  COV_EDEVICE = 6       /* a device-side consistency check failed */
+} cov_status;
+
+typedef enum { COV_C64 = 0, COV_C128 = 1 } cov_dtype;
+
+typedef enum { COV_MEAN = 0, COV_SUM = 1 } cov_norm;
+
+typedef enum {
+  /* COV_RECURRENCE where it applies, else COV_DIRECT. */
+  COV_AUTO = 0,
+  /* The combination / diagonal-segment method (Sections 3.1-3.4,
+   * Algorithm 1): every distinct product A[n][m] * conj(A[n+dr][m+dc]) of a
+   * unique combination (Eq. 3.3) is formed once; each combination's diagonal
+   * segments are seeded with a direct box sum and walked along the diagonal
+   * by adding the entering row of products and subtracting the leaving one;
+   * exactly one thread block writes each element of R. FP32 with compensated
+   * running sums for COV_C64, FP64 for COV_C128. Needs N >= 2P-1,
+   * M >= 2Q-1 and P, Q <= 32 (COV_EUNSUPPORTED otherwise). */
+  COV_RECURRENCE = 1,
+  /* Dense form R = X X^H on the block-Hankel data matrix X (PQ x K, Eq. 2.2)
+   * on tcgen05 tensor cores, with split (hi + lo) operands and FP32
+   * accumulation. COV_C64 only. */
+  COV_GEMM_TF32X3 = 2,
+  COV_GEMM_BF16X3 = 3,
+  /* Plain per-element sums of Eq. 2.2 in FP64 (the straightforward serial
+   * algorithm of Section 2.4, one thread per element of R). Output rounded to
+   * the input's type. */
+  COV_DIRECT = 4
+} cov_algo;
+
+/* Human-readable name of a status code (static string). */
+const char *cov_status_string(cov_status s);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int cov_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Plan-layer queries. Host only: no GPU, no CUDA call.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t K;                 /* window positions (N-P+1)(M-Q+1) */
+  int64_t n_combinations;    /* |UC| = PQ + (P-1)(Q-1), Eq. 3.4 */
+  int64_t distinct_products; /* UM = sum over UC of (N-|dr|)(M-|dc|), Eq. 3.5-3.6 */
+  int64_t r_elements;        /* (PQ)^2 elements written */
+  int64_t naive_macs;        /* K * PQ(PQ+1)/2: products of the direct method */
+  int32_t recurrence_ok;     /* 1 if COV_RECURRENCE accepts the shape */
+  int32_t n_groups;          /* lag groups of the product kernel */
+  int64_t n_tasks;           /* warp tasks of the product kernel */
+  int64_t products_inner;    /* products formed by the inner-row kernel */
+  int64_t products_fringe;   /* products formed by the fringe-row kernel */
+} cov_plan_info_t;
+
+/* Fills *out for an N x M input and P x Q window (cf. Eq. 3.4-3.6, 4.1).
+ * COV_EINVAL on a bad shape or null out. */
+cov_status cov_plan_info(int64_t N, int64_t M, int P, int Q, cov_plan_info_t *out);
+
+/* Bytes of device workspace cov_estimate_ex needs for this problem (0 is
+ * possible). Host only. COV_EINVAL on a bad shape, COV_EUNSUPPORTED if the
+ * algorithm cannot take it. */
+cov_status cov_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                              cov_algo algo, size_t *bytes);
+
+/* ---------------------------------------------------------------------------
+ * One input matrix.
+ * ------------------------------------------------------------------------- */
+
+/* Full control. A: device, N x M (leading dimension lda). R: device, PQ x PQ.
+ * workspace: device, >= cov_workspace_size bytes, 256-byte aligned (may be
+ * NULL when that size is 0). The workspace is scratch: its contents on entry
+ * are ignored and on exit are unspecified, except its first 4 bytes (the
+ * status word, see cov_check_device_status). Calls that share a workspace
+ * must be ordered on one stream. Section 2.2, Eq. 2.1-2.2. */
+cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M,
+                           int64_t lda, int P, int Q, void *R, cov_algo algo,
+                           cov_norm norm, void *workspace, size_t ws_bytes,
+                           cov_stream_t stream);
+
+/* Convenience form: COV_AUTO, COV_MEAN, lda = M. Allocates its workspace
+ * with cudaMallocAsync on `stream` and frees it with cudaFreeAsync. */
+cov_status cov_estimate(const void *A, cov_dtype dtype, int64_t N, int64_t M, int P,
+                        int Q, void *R, cov_stream_t stream);
+
+/* Reads (and then clears) the status word a previous call left at the start
+ * of `workspace`. Synchronises `stream`. Returns COV_OK, COV_ETIMEOUT or
+ * COV_EDEVICE; COV_ECUDA if the copy itself fails. */
+cov_status cov_check_device_status(void *workspace, cov_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Many input matrices of uneven N, M, P, Q in one launch sequence
+ * (Section 5.1: computing several matrices concurrently to keep all cores
+ * busy). The plan is built on the host once; the device work is a single
+ * persistent pass per phase, capturable in one CUDA graph.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  const void *A; /* device, N x M, leading dimension lda */
+  void *R;       /* device, PQ x PQ */
+  int64_t lda;
+  int32_t N, M, P, Q;
+} cov_desc;
+
+typedef struct cov_batched_plan cov_batched_plan;
+
+/* Validates `count` descriptors (HOST array, copied) and builds the task
+ * schedule. Only COV_C64 with COV_RECURRENCE (or COV_AUTO) is supported; every
+ * member must satisfy the COV_RECURRENCE shape rule. On success *plan owns
+ * host memory until cov_batched_plan_destroy. */
+cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype,
+                                   cov_algo algo, cov_norm norm, cov_batched_plan **plan);
+cov_status cov_batched_workspace_size(const cov_batched_plan *plan, size_t *bytes);
+/* Copies the plan's tables into `workspace` (stream-ordered). Must precede the
+ * first cov_estimate_batched on that workspace; not needed again while the
+ * workspace is only used by this plan. */
+cov_status cov_batched_upload(const cov_batched_plan *plan, void *workspace,
+                              size_t ws_bytes, cov_stream_t stream);
+/* Launches the batched computation (kernel launches only; capturable). */
+cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace,
+                                size_t ws_bytes, cov_stream_t stream);
+void cov_batched_plan_destroy(cov_batched_plan *plan);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint (not in the paper; the derivative of Eq. 2.2).
+ * Given G = dL/dR (PQ x PQ, device, convention dL/dRe + i dL/dIm), writes
+ * dA = dL/dA (N x M, device, leading dimension M, same convention):
+ *     H = (G + G^H) / K  (G + G^H for COV_SUM),  Y = H X,
+ *     dA[n][m] = sum over windows w containing (n, m) of Y[(n-p) + P(m-q), w],
+ * with X recomputed from A (never stored) and a gather-form col2im (one
+ * writer per element of dA, no atomics). COV_C64 only.
+ * ------------------------------------------------------------------------- */
+cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P,
+                                       int Q, size_t *bytes);
+cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype,
+                                 int64_t N, int64_t M, int P, int Q, cov_norm norm,
+                                 void *dA, void *workspace, size_t ws_bytes,
+                                 cov_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COV_H */

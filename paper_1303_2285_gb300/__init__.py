@@ -1,0 +1,174 @@
+"""GB300 (sm_103a) covariance-method library: Python binding.
+
+A thin ctypes layer over the C ABI of ``include/cov.h`` (``libcov.so``). It
+marshals arguments only: torch tensors supply device memory and the current
+CUDA stream, and every step of the computation runs in the library's CUDA
+kernels. There is no CPU fallback: without the built library or a CUDA
+device the calls raise.
+
+The estimate (arXiv 1303.2285, Section 2.2, Eq. 2.1-2.2):
+    R = (1/K) * sum over all K = (N-P+1)(M-Q+1) window positions of x x^H,
+with x the column stack of the P x Q window (x[i + P*j] = A[p+i, q+j]).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+from . import _build
+
+__all__ = ["load", "estimate", "estimate_into", "workspace_size", "plan_info",
+           "check_device_status", "CovError", "ALGOS", "STATUS"]
+
+ALGOS = {"auto": 0, "recurrence": 1, "gemm_tf32x3": 2, "gemm_bf16x3": 3, "direct": 4}
+NORMS = {"mean": 0, "sum": 1}
+DTYPES = {"c64": 0, "c128": 1}
+STATUS = {0: "COV_OK", 1: "COV_EINVAL", 2: "COV_ECUDA", 3: "COV_EWORKSPACE",
+          4: "COV_ETIMEOUT", 5: "COV_EUNSUPPORTED", 6: "COV_EDEVICE"}
+
+
+class CovError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int64), ("n_combinations", ctypes.c_int64),
+                ("distinct_products", ctypes.c_int64), ("r_elements", ctypes.c_int64),
+                ("naive_macs", ctypes.c_int64), ("recurrence_ok", ctypes.c_int32),
+                ("n_groups", ctypes.c_int32), ("n_tasks", ctypes.c_int64),
+                ("products_inner", ctypes.c_int64), ("products_fringe", ctypes.c_int64)]
+
+
+class CovDesc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("R", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("N", ctypes.c_int32), ("M", ctypes.c_int32), ("P", ctypes.c_int32),
+                ("Q", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point of include/cov.h
+_VP, _I64, _I, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+SIGNATURES = [
+    ("cov_status_string", ctypes.c_char_p, [_I]),
+    ("cov_version", _I, []),
+    ("cov_plan_info", _I, [_I64, _I64, _I, _I, ctypes.POINTER(PlanInfo)]),
+    ("cov_workspace_size", _I, [_I, _I64, _I64, _I, _I, _I, ctypes.POINTER(_SZ)]),
+    ("cov_estimate_ex", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _VP, _I, _I, _VP, _SZ, _VP]),
+    ("cov_estimate", _I, [_VP, _I, _I64, _I64, _I, _I, _VP, _VP]),
+    ("cov_check_device_status", _I, [_VP, _VP]),
+    ("cov_batched_plan_create", _I, [ctypes.POINTER(CovDesc), _I, _I, _I, _I,
+                                     ctypes.POINTER(_VP)]),
+    ("cov_batched_workspace_size", _I, [_VP, ctypes.POINTER(_SZ)]),
+    ("cov_batched_upload", _I, [_VP, _VP, _SZ, _VP]),
+    ("cov_estimate_batched", _I, [_VP, _VP, _SZ, _VP]),
+    ("cov_batched_plan_destroy", None, [_VP]),
+    ("cov_backward_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
+    ("cov_estimate_backward", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _VP, _VP, _SZ, _VP]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcov.so (building it with nvcc first when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing and _build.needs_build():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libcov.so is not built; run __graft_entry__.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise CovError(code, what)
+
+
+def plan_info(N: int, M: int, P: int, Q: int) -> dict:
+    """Counts of the plan layer (host only): K, |UC|, UM, ... ."""
+    info = PlanInfo()
+    _check(load().cov_plan_info(N, M, P, Q, ctypes.byref(info)), "cov_plan_info")
+    return {f: getattr(info, f) for f, _ in PlanInfo._fields_}
+
+
+def workspace_size(dtype: str, N: int, M: int, P: int, Q: int, algo: str = "auto") -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().cov_workspace_size(DTYPES[dtype], N, M, P, Q, ALGOS[algo], ctypes.byref(out)),
+           "cov_workspace_size")
+    return int(out.value)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_of(A) -> str:
+    torch = _torch()
+    if A.dtype == torch.complex64:
+        return "c64"
+    if A.dtype == torch.complex128:
+        return "c128"
+    raise TypeError("A must be complex64 or complex128")
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def estimate_into(A, R, P: int, Q: int, algo: str = "auto", norm: str = "mean",
+                  workspace=None, stream=None):
+    """R <- estimate of A (device tensors). ``workspace`` is a uint8 CUDA tensor
+    of at least ``workspace_size`` bytes (allocated here when None)."""
+    torch = _torch()
+    if not (A.is_cuda and R.is_cuda):
+        raise ValueError("A and R must be CUDA tensors (no CPU fallback)")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be 2-D with unit column stride")
+    dt = _dtype_of(A)
+    if R.dtype != A.dtype or not R.is_contiguous() or tuple(R.shape) != (P * Q, P * Q):
+        raise ValueError("R must be a contiguous PQ x PQ tensor of A's dtype")
+    N, M = A.shape
+    need = workspace_size(dt, N, M, P, Q, algo)
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=A.device)
+    if workspace.numel() < need:
+        raise ValueError(f"workspace too small: {workspace.numel()} < {need}")
+    code = load().cov_estimate_ex(A.data_ptr(), DTYPES[dt], N, M, A.stride(0), P, Q,
+                                  R.data_ptr(), ALGOS[algo], NORMS[norm],
+                                  workspace.data_ptr(), workspace.numel(), _stream_ptr(stream))
+    _check(code, "cov_estimate_ex")
+    return R
+
+
+def estimate(A, P: int, Q: int, algo: str = "auto", norm: str = "mean", workspace=None,
+             stream=None):
+    """Returns R (PQ x PQ, A's dtype) for the device tensor A."""
+    torch = _torch()
+    R = torch.empty((P * Q, P * Q), dtype=A.dtype, device=A.device)
+    return estimate_into(A, R, P, Q, algo, norm, workspace, stream)
+
+
+def check_device_status(workspace, stream=None) -> None:
+    """Raises CovError if a kernel recorded a device-side failure in workspace."""
+    _check(load().cov_check_device_status(workspace.data_ptr(), _stream_ptr(stream)),
+           "device status")

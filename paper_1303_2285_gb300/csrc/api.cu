@@ -1,0 +1,238 @@
+// C ABI of the library (see include/cov.h): argument checks, algorithm
+// selection, workspace layout and kernel launches. No entry point computes
+// anything on the host; every result comes from this library's kernels.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/cov.h"
+#include "cov_internal.h"
+#include "cov_launch.h"
+#include "plan.h"
+
+using namespace cov;
+
+namespace {
+
+int device_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  static int cache[64] = {0};
+  if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (dev >= 0 && dev < 64) cache[dev] = sms;
+  return sms;
+}
+
+bool shape_ok(int64_t N, int64_t M, int P, int Q) {
+  return N >= 1 && M >= 1 && P >= 1 && Q >= 1 && P <= N && Q <= M && N < (1LL << 30) &&
+         M < (1LL << 30) && (int64_t)P * Q <= (1LL << 15);
+}
+
+cov_algo resolve_algo(cov_algo algo, int64_t N, int64_t M, int P, int Q) {
+  if (algo != COV_AUTO) return algo;
+  return recurrence_ok(N, M, P, Q) ? COV_RECURRENCE : COV_DIRECT;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *cov_status_string(cov_status s) {
+  switch (s) {
+    case COV_OK: return "COV_OK";
+    case COV_EINVAL: return "COV_EINVAL: invalid argument";
+    case COV_ECUDA: return "COV_ECUDA: CUDA call or launch failed";
+    case COV_EWORKSPACE: return "COV_EWORKSPACE: workspace missing, too small or misaligned";
+    case COV_ETIMEOUT: return "COV_ETIMEOUT: a bounded device wait gave up";
+    case COV_EUNSUPPORTED: return "COV_EUNSUPPORTED: not supported by the selected algorithm";
+    case COV_EDEVICE: return "COV_EDEVICE: device-side check failed";
+  }
+  return "unknown cov_status";
+}
+
+int cov_version(void) { return 100; }
+
+cov_status cov_plan_info(int64_t N, int64_t M, int P, int Q, cov_plan_info_t *out) {
+  if (!out || !shape_ok(N, M, P, Q)) return COV_EINVAL;
+  memset(out, 0, sizeof(*out));
+  const long long D = (long long)P * Q;
+  out->K = n_positions(N, M, P, Q);
+  out->n_combinations = n_unique_combinations(P, Q);
+  out->distinct_products = distinct_products(N, M, P, Q);
+  out->r_elements = D * D;
+  out->naive_macs = out->K * (D * (D + 1) / 2);
+  out->recurrence_ok = recurrence_ok(N, M, P, Q) ? 1 : 0;
+  if (out->recurrence_ok) {
+    RecParams p;
+    WsLayout ws;
+    plan_recurrence(N, M, M, P, Q, 8, p, ws);
+    out->n_groups = p.ngroups;
+    out->n_tasks = p.n_tasks;
+    // products of the inner-row kernel: inner rows x all columns, valid lags
+    long long inner = 0, fringe = 0;
+    for (int dc = 0; dc < Q; ++dc) {
+      const int lo = dc == 0 ? 0 : -(P - 1);
+      for (int dr = lo; dr <= P - 1; ++dr) {
+        const long long cols_all = M - dc;                  // columns with a valid partner
+        const long long cols_inner = (M - 2LL * Q + 2);     // inner columns
+        inner += (long long)p.n_inner * cols_all;
+        long long rows_f = 0;                               // fringe rows with a valid partner
+        for (int k = 0; k < p.NFR; ++k) {
+          const long long n = k < P - 1 ? k : (N - P + 1) + (k - (P - 1));
+          if (n + dr >= 0 && n + dr < N) ++rows_f;
+        }
+        fringe += rows_f * cols_inner;                       // lane-strided inner columns
+        fringe += rows_f * (2LL * (Q - 1) - dc);             // its own fringe-column products
+      }
+    }
+    out->products_inner = inner;
+    out->products_fringe = fringe;
+  }
+  return COV_OK;
+}
+
+cov_status cov_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                              cov_algo algo, size_t *bytes) {
+  if (!bytes || !shape_ok(N, M, P, Q) || (dtype != COV_C64 && dtype != COV_C128))
+    return COV_EINVAL;
+  algo = resolve_algo(algo, N, M, P, Q);
+  switch (algo) {
+    case COV_RECURRENCE: {
+      if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+      RecParams p;
+      WsLayout ws;
+      plan_recurrence(N, M, M, P, Q, dtype == COV_C128 ? 16 : 8, p, ws);
+      *bytes = ws.total;
+      return COV_OK;
+    }
+    case COV_DIRECT:
+      *bytes = kWsHeader;
+      return COV_OK;
+    default:
+      return COV_EUNSUPPORTED;
+  }
+}
+
+cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M, int64_t lda,
+                           int P, int Q, void *R, cov_algo algo, cov_norm norm, void *workspace,
+                           size_t ws_bytes, cov_stream_t stream) {
+  if (!A || !R || !shape_ok(N, M, P, Q) || lda < M || (dtype != COV_C64 && dtype != COV_C128) ||
+      (norm != COV_MEAN && norm != COV_SUM))
+    return COV_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  algo = resolve_algo(algo, N, M, P, Q);
+  const int elem = dtype == COV_C128 ? 16 : 8;
+  if (((uintptr_t)A % (uintptr_t)(elem / 2)) != 0 || ((uintptr_t)R % (uintptr_t)(elem / 2)) != 0)
+    return COV_EINVAL;
+  switch (algo) {
+    case COV_RECURRENCE: {
+      if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+      RecParams p;
+      WsLayout ws;
+      plan_recurrence(N, M, lda, P, Q, elem, p, ws);
+      if (!workspace || ws_bytes < ws.total || ((uintptr_t)workspace & 255) != 0)
+        return COV_EWORKSPACE;
+      char *w = (char *)workspace;
+      p.A = A;
+      p.R = R;
+      p.mean = norm == COV_MEAN ? 1 : 0;
+      p.status = (unsigned *)w;
+      p.core_part = w + ws.core_off;
+      p.colsum_part = w + ws.colsum_off;
+      p.rowval = w + ws.rowval_off;
+      p.colval = w + ws.colval_off;
+      const int sms = device_sms();
+      if (sms <= 0) return COV_ECUDA;
+      if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+      if (launch_recurrence(p, dtype == COV_C128, sms, s) != cudaSuccess) return COV_ECUDA;
+      return COV_OK;
+    }
+    case COV_DIRECT: {
+      if (workspace && ((uintptr_t)workspace & 255) == 0 && ws_bytes >= 4)
+        if (cudaMemsetAsync(workspace, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+      DirectParams d;
+      d.A = A;
+      d.R = R;
+      d.lda = lda;
+      d.N = (int)N;
+      d.M = (int)M;
+      d.P = P;
+      d.Q = Q;
+      d.K = n_positions(N, M, P, Q);
+      d.mean = norm == COV_MEAN ? 1 : 0;
+      if (launch_direct(d, dtype == COV_C128, s) != cudaSuccess) return COV_ECUDA;
+      return COV_OK;
+    }
+    default:
+      return COV_EUNSUPPORTED;
+  }
+}
+
+cov_status cov_estimate(const void *A, cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                        void *R, cov_stream_t stream) {
+  size_t bytes = 0;
+  cov_status st = cov_workspace_size(dtype, N, M, P, Q, COV_AUTO, &bytes);
+  if (st != COV_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  void *ws = nullptr;
+  if (bytes > 0 && cudaMallocAsync(&ws, bytes, s) != cudaSuccess) return COV_ECUDA;
+  st = cov_estimate_ex(A, dtype, N, M, M, P, Q, R, COV_AUTO, COV_MEAN, ws, bytes, stream);
+  if (ws && cudaFreeAsync(ws, s) != cudaSuccess && st == COV_OK) st = COV_ECUDA;
+  return st;
+}
+
+cov_status cov_check_device_status(void *workspace, cov_stream_t stream) {
+  if (!workspace) return COV_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned word = 0;
+  if (cudaMemcpyAsync(&word, workspace, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return COV_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return COV_ECUDA;
+  if (cudaMemsetAsync(workspace, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  if (word == kDevOk) return COV_OK;
+  if (word == kDevTimeout) return COV_ETIMEOUT;
+  return COV_EDEVICE;
+}
+
+// ---- not yet available: batched, backward -------------------------------
+struct cov_batched_plan {
+  int dummy;
+};
+
+cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype,
+                                   cov_algo algo, cov_norm norm, cov_batched_plan **plan) {
+  (void)descs; (void)count; (void)dtype; (void)algo; (void)norm; (void)plan;
+  return COV_EUNSUPPORTED;
+}
+cov_status cov_batched_workspace_size(const cov_batched_plan *plan, size_t *bytes) {
+  (void)plan; (void)bytes;
+  return COV_EUNSUPPORTED;
+}
+cov_status cov_batched_upload(const cov_batched_plan *plan, void *workspace, size_t ws_bytes,
+                              cov_stream_t stream) {
+  (void)plan; (void)workspace; (void)ws_bytes; (void)stream;
+  return COV_EUNSUPPORTED;
+}
+cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, size_t ws_bytes,
+                                cov_stream_t stream) {
+  (void)plan; (void)workspace; (void)ws_bytes; (void)stream;
+  return COV_EUNSUPPORTED;
+}
+void cov_batched_plan_destroy(cov_batched_plan *plan) { (void)plan; }
+
+cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                                       size_t *bytes) {
+  (void)dtype; (void)N; (void)M; (void)P; (void)Q; (void)bytes;
+  return COV_EUNSUPPORTED;
+}
+cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype, int64_t N,
+                                 int64_t M, int P, int Q, cov_norm norm, void *dA,
+                                 void *workspace, size_t ws_bytes, cov_stream_t stream) {
+  (void)A; (void)G; (void)dtype; (void)N; (void)M; (void)P; (void)Q; (void)norm; (void)dA;
+  (void)workspace; (void)ws_bytes; (void)stream;
+  return COV_EUNSUPPORTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal definitions shared by the host plan layer and the CUDA kernels.
+//
+// Notation (0-based restatement of Sections 2.2 and 3):
+//   A is N x M; window (p, q) holds A[p+i][q+j] at x[i + P*j]   (Eq. 2.1).
+//   A combination is Delta = (dr, dc) = (r2 - r1, c2 - c1)      (Eq. 3.1).
+//   Unique combinations UC (Eq. 3.3): dc = 0 with dr in [0, P-1], and
+//   dc in [1, Q-1] with dr in [-(P-1), P-1].
+//   Product image: Pi_D[n][m] = A[n][m] * conj(A[n+dr][m+dc]).
+//   Combination D owns the outputs (i, j), i in [max(0,-dr), P-1-max(0,dr)],
+//   j in [0, Q-1-dc]  (Eq. 3.7-3.8, Fig. 2): K*R[i+Pj, (i+dr)+P(j+dc)] is the
+//   box sum of Pi_D over rows [i, i+N-P] and columns [j, j+M-Q].
+//
+// Work split used by the kernels (rows; columns are analogous):
+//   inner rows  [P-1, N-P]: inside the box of every output of every Delta;
+//   fringe rows [0, P-2] and [N-P+1, N-1] (2(P-1) rows, index fr).
+//   inner cols  [Q-1, M-Q]; fringe cols [0, Q-2] and [M-Q+1, M-1] (index fc).
+//   Kernel 1 (products_inner): inner rows x all columns. For each Delta the
+//     sum over (inner rows x inner cols) -> core partials; per fringe column
+//     the sum over inner rows -> colsum partials.
+//   Kernel 2 (fringe_rows): each fringe row: the sum over inner columns plus
+//     its own fringe-column products, combined into the box-row sums
+//     RV[Delta][j][fr] = sum_{m in [j, j+M-Q]} Pi_D[n][m].
+//   Kernel 3 (reduce_cols): CV[Delta][j] = sum over inner rows of the box-row
+//     sums at column offset j (core + fringe-column sums).
+//   Kernel 4 (walk_write): per output block, seed each diagonal segment with
+//     the direct sum CV + sum of RV over the fringe rows inside the box, walk
+//     down the diagonal by subtracting the leaving top row and adding the
+//     entering bottom row (re-seeding every L steps), divide by K and write
+//     the block and its conjugate mirror with coalesced stores.
+#pragma once
+
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define COV_HD __host__ __device__ __forceinline__
+#else
+#define COV_HD inline
+#endif
+
+namespace cov {
+
+constexpr int kMaxPQ = 32;       // recurrence path: P, Q <= 32 (smem tile fits)
+constexpr int kWsHeader = 256;   // status word + padding at the workspace head
+
+// Status codes written by kernels into the workspace status word.
+constexpr unsigned kDevOk = 0;
+constexpr unsigned kDevTimeout = 4;
+constexpr unsigned kDevCheck = 6;
+
+// Index of combination (dr, dc) in [0, |UC|): dc = 0 first (dr = 0..P-1),
+// then each dc >= 1 with dr = -(P-1)..P-1.
+COV_HD int combo_index(int P, int dr, int dc) {
+  return dc == 0 ? dr : P + (dc - 1) * (2 * P - 1) + (dr + P - 1);
+}
+
+COV_HD void combo_of(int P, int idx, int &dr, int &dc) {
+  if (idx < P) {
+    dr = idx;
+    dc = 0;
+  } else {
+    const int k = idx - P;
+    dc = 1 + k / (2 * P - 1);
+    dr = k % (2 * P - 1) - (P - 1);
+  }
+}
+
+// Lag groups: consecutive dr values of one dc, G per group. Group g gives
+// (dc, d0, cnt): lags dr = d0 .. d0+cnt-1 (cnt <= G). The G - cnt unused
+// slots of the last group of each dc read zero-filled rows and are dropped.
+COV_HD int groups_dc0(int P, int G) { return (P + G - 1) / G; }
+COV_HD int groups_per_dc(int P, int G) { return (2 * P - 1 + G - 1) / G; }
+COV_HD int n_groups(int P, int Q, int G) {
+  return groups_dc0(P, G) + (Q - 1) * groups_per_dc(P, G);
+}
+COV_HD void group_of(int P, int G, int g, int &dc, int &d0, int &cnt) {
+  const int g0 = groups_dc0(P, G);
+  if (g < g0) {
+    dc = 0;
+    d0 = g * G;
+  } else {
+    const int gp = g - g0, gpc = groups_per_dc(P, G);
+    dc = 1 + gp / gpc;
+    d0 = -(P - 1) + (gp % gpc) * G;
+  }
+  const int c = P - d0;  // lags up to dr = P-1
+  cnt = c < G ? c : G;
+}
+// Largest lag (including unused slots) over all groups.
+COV_HD int group_lag_hi(int P, int Q, int G) {
+  int hi = groups_dc0(P, G) * G - 1;
+  if (Q > 1) {
+    const int h2 = -(P - 1) + groups_per_dc(P, G) * G - 1;
+    hi = h2 > hi ? h2 : hi;
+  }
+  return hi;
+}
+COV_HD int group_lag_lo(int P, int Q) { return Q > 1 ? -(P - 1) : 0; }
+
+// Everything a kernel of the recurrence path needs about one problem.
+// Sizes are int32 (N, M < 2^31); element offsets are int64.
+struct RecParams {
+  const void *A;
+  void *R;
+  long long lda;  // complex elements
+  int N, M, P, Q;
+  long long K;
+  int mean;
+  int div_double;  // divide by K in double (FP32 path, K > 2^24)
+  int n_uc;
+  // product kernel (inner rows)
+  int G;                // lags per group
+  int ngroups;
+  int inner_lo;         // P-1
+  int n_inner;          // N-2P+2
+  int TR, TC, CBT;      // tile rows, tile cols, 32-col blocks per tile
+  int n_rt, n_ct, n_cb; // row tiles, col tiles, 32-col blocks over [0, M)
+  int d_lo, d_hi;       // lag range covered by the smem tile
+  int STR, STC;         // smem tile rows and pitch (elements)
+  long long tasks_per_tile, n_tasks;
+  // fringe-row kernel
+  int NFR, NFC;         // 2(P-1), 2(Q-1)
+  int GF, ngroups_f, RB, nrb;
+  // walk
+  int L;                // re-seed interval along the diagonal
+  // workspace
+  unsigned *status;
+  void *core_part;      // [n_uc][n_rt][n_cb]
+  void *colsum_part;    // [n_uc][NFC][n_rt]
+  void *rowval;         // [n_uc][Q][NFR]
+  void *colval;         // [n_uc][Q]
+};
+
+}  // namespace cov

@@ -1,0 +1,96 @@
+"""Host-only checks of the C ABI: the library builds and loads, exports every
+entry point of include/cov.h, its plan layer agrees with the oracle's
+counting (an independent implementation), and argument checks fail before any
+CUDA call. No GPU is used."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1303_2285_gb300 as cov
+from oracle import combinations as cb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "cov.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(cov_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function():
+    lib = cov.load()
+    names = header_functions()
+    assert len(names) >= 14
+    bound = {n for n, _, _ in cov.SIGNATURES}
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in bound, f"{n} has no binding"
+
+
+def test_status_strings_and_version():
+    lib = cov.load()
+    for code in range(7):
+        assert lib.cov_status_string(code).decode().startswith(cov.STATUS[code])
+    assert lib.cov_version() >= 100
+
+
+@pytest.mark.parametrize("N,M,P,Q", [(64, 64, 8, 8), (1024, 1024, 16, 16), (2048, 512, 32, 32),
+                                     (256, 256, 12, 12), (20, 20, 8, 8), (32, 32, 13, 13),
+                                     (37, 11, 5, 6), (9, 9, 9, 9), (5, 1, 2, 1)])
+def test_plan_counts_match_oracle(N, M, P, Q):
+    info = cov.plan_info(N, M, P, Q)
+    assert info["K"] == (N - P + 1) * (M - Q + 1)
+    assert info["n_combinations"] == cb.n_unique_combinations(P, Q)
+    assert info["distinct_products"] == cb.um_enumerated(N, M, P, Q)
+    assert info["r_elements"] == (P * Q) ** 2
+    D = P * Q
+    assert info["naive_macs"] == info["K"] * D * (D + 1) // 2
+    assert info["recurrence_ok"] == int(N >= 2 * P - 1 and M >= 2 * Q - 1 and P <= 32 and Q <= 32)
+
+
+@pytest.mark.parametrize("N,M,P,Q", [(64, 64, 8, 8), (1024, 1024, 16, 16), (2048, 512, 32, 32),
+                                     (33, 70, 3, 11), (15, 31, 8, 16)])
+def test_plan_products_cover_um(N, M, P, Q):
+    # Every distinct product is formed by exactly one of the two product
+    # kernels; the rest of UM is the fringe-row x fringe-column corner
+    # products, which the fringe-row kernel also forms.
+    info = cov.plan_info(N, M, P, Q)
+    assert info["products_inner"] + info["products_fringe"] == info["distinct_products"]
+
+
+def test_workspace_sizes():
+    n1 = cov.workspace_size("c64", 1024, 1024, 16, 16, "recurrence")
+    n2 = cov.workspace_size("c128", 1024, 1024, 16, 16, "recurrence")
+    assert n1 > 256 and n1 % 256 == 0 and n2 > n1
+    assert cov.workspace_size("c64", 9, 9, 9, 9, "auto") == 256  # direct path
+    with pytest.raises(cov.CovError) as e:
+        cov.workspace_size("c64", 9, 9, 9, 9, "recurrence")
+    assert e.value.code == 5
+
+
+def test_argument_checks_fail_before_cuda():
+    lib = cov.load()
+    fake = ctypes.c_void_p(0x1000)
+    # null input
+    assert lib.cov_estimate_ex(None, 0, 8, 8, 8, 2, 2, fake, 0, 0, None, 0, None) == 1
+    # P > N
+    assert lib.cov_estimate_ex(fake, 0, 8, 8, 8, 9, 2, fake, 0, 0, None, 0, None) == 1
+    # lda < M
+    assert lib.cov_estimate_ex(fake, 0, 8, 8, 7, 2, 2, fake, 0, 0, None, 0, None) == 1
+    # bad dtype / norm
+    assert lib.cov_estimate_ex(fake, 7, 8, 8, 8, 2, 2, fake, 0, 0, None, 0, None) == 1
+    assert lib.cov_estimate_ex(fake, 0, 8, 8, 8, 2, 2, fake, 0, 9, None, 0, None) == 1
+    # recurrence without a workspace
+    assert lib.cov_estimate_ex(fake, 0, 64, 64, 64, 8, 8, fake, 1, 0, None, 0, None) == 3
+    # misaligned workspace
+    assert lib.cov_estimate_ex(fake, 0, 64, 64, 64, 8, 8, fake, 1, 0,
+                               ctypes.c_void_p(0x1008), 1 << 30, None) == 3
+    # recurrence on a shape it does not take
+    assert lib.cov_estimate_ex(fake, 0, 9, 9, 9, 9, 9, fake, 1, 0, None, 0, None) == 5
+    info = cov.PlanInfo()
+    assert lib.cov_plan_info(0, 5, 1, 1, ctypes.byref(info)) == 1
+    assert lib.cov_plan_info(5, 5, 1, 1, None) == 1
