@@ -1,0 +1,460 @@
+#!/usr/bin/env python3
+"""Benchmark of the covariance-method hot path on GB300.
+
+Prints ONE JSON line. A step is one call of the combination path
+(COV_RECURRENCE) on the bench workload: the plan, the staging of A, every
+distinct product, the seeds, the diagonal walk and the write of R. Inputs are
+resident in HBM when the timed region starts; L2 is flushed (256 MiB write)
+before every timed step, outside the timed events.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the plain FP64 window loop) on the
+host cores, on a bounded sample of the same workload.
+Under torchrun each rank computes its own matrix (independent problems, no
+data-path collective): weak scaling, value = all ranks' products / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "R elements/s and distinct products/s vs plain FP64 GPU path; % roofline; err vs FP64"
+UNIT = "distinct products/s"
+DEFAULT_WORKLOAD = "cn_1024x1024_w16_f32"
+FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
+FALLBACK_SM_MAX_MHZ = 2070.0
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic per launch of the product kernel from one ncu capture, keyed
+# by a hash of the kernel source at capture time (null when it has changed).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("recurrence.cu", "cov_device.cuh", "cov_internal.h", "plan.cpp"):
+        with open(os.path.join(ROOT, "paper_1303_2285_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index: int) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    c = [x.strip() for x in line.split(",")]
+                    if len(c) < 9 or c[0] != str(gpu_index):
+                        continue
+                    try:
+                        sm.append(float(c[1]))
+                        smax.append(float(c[2]))
+                    except ValueError:
+                        continue
+                    for k, nm in enumerate(names):
+                        if c[5 + k].lower().startswith("active"):
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline leg: the oracle, as it stands, on the host cores. The only part
+# of this file that runs anything under oracle/.
+# ---------------------------------------------------------------------------
+def cpu_baseline_leg(A_np, P, Q, um_full, K_full, budget_s: float, gpu_check=None,
+                     rows=None) -> dict:
+    """Times the oracle on the first `rows` rows of A (chosen to take about
+    budget_s when None) and extrapolates to the full job by window count."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    N, M = A_np.shape
+
+    def run(r):
+        t0 = time.perf_counter()
+        R = oracle.cov_window(A_np[:r], P, Q, threads=threads)
+        return time.perf_counter() - t0, R
+
+    if rows is None:
+        rows = calibrate_rows(A_np, P, Q, budget_s, run)
+    t, R_s = run(rows)
+    k_s = (rows - P + 1) * (M - Q + 1)
+    t_full = t * K_full / k_s
+    out = {"value": um_full / t_full, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": (f"first {rows} of {N} rows of the same input ({k_s} of {K_full} window "
+                      f"positions), full-job time extrapolated by window count"),
+           "sample_seconds": round(t, 3), "rows": rows}
+    if gpu_check is not None:
+        G = gpu_check(A_np[:rows])
+        err = float(np.linalg.norm(G - R_s) / np.linalg.norm(R_s))
+        out["gpu_rel_fro_err_on_sample"] = err
+        out["gpu_max_abs_err_rel_to_max_on_sample"] = float(np.abs(G - R_s).max() / np.abs(R_s).max())
+    return out
+
+
+def calibrate_rows(A_np, P, Q, budget_s, run) -> int:
+    N, M = A_np.shape
+    rows = min(N, P + 7)
+    t, _ = run(rows)
+    per_window = t / ((rows - P + 1) * (M - Q + 1))
+    want_k = max(1, int(budget_s / max(per_window, 1e-9)))
+    return int(min(N, max(P, P - 1 + want_k // (M - Q + 1))))
+
+
+def bench_reference(args, rank, world):
+    import cov_workloads as wl
+    if rank != 0:
+        return 0
+    w = wl.WORKLOADS[args.workload]
+    A_np = wl.workload_input(w)
+    um = _um(w)
+    budget = min(3.0, 150.0 / max(1, args.steps + args.warmup))
+    vals = []
+    last = None
+    rows = None
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline_leg(A_np, w.P, w.Q, um, w.K, budget, rows=rows)
+        rows = r["rows"]
+        if k >= args.warmup:
+            vals.append(r["value"])
+        last = r
+    value = statistics.median(vals)
+    t_step = um / value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _um(w):
+    from oracle import combinations as cb  # counting only
+    return cb.um_enumerated(w.N, w.M, w.P, w.Q)
+
+
+def _config(w):
+    return {"workload": w.name, "N": w.N, "M": w.M, "P": w.P, "Q": w.Q, "K": w.K,
+            "input": {"cn": "i.i.d. CN(0,1)", "sar": "8 complex exponentials + noise at 10 dB SNR",
+                      "int": "integer-valued"}[w.kind] + f", seed {w.seed}",
+            "l2": "flushed before every timed step (256 MiB write, outside the timed events)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def bench_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import cov_workloads as wl
+    import paper_1303_2285_gb300 as cov
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = wl.WORKLOADS[args.workload]
+    dt = torch.complex64 if w.dtype == "c64" else torch.complex128
+    A_np = wl.workload_input(w, index=rank)
+    A = torch.from_numpy(A_np).cuda()
+    D = w.P * w.Q
+    R = torch.empty((D, D), dtype=dt, device="cuda")
+    info = cov.plan_info(w.N, w.M, w.P, w.Q)
+    um = info["distinct_products"]
+    ws = torch.empty(max(256, cov.workspace_size(w.dtype, w.N, w.M, w.P, w.Q, "recurrence")),
+                     dtype=torch.uint8, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def call(Ain=A, Rout=R):
+        cov.estimate_into(Ain, Rout, w.P, w.Q, algo="recurrence", workspace=ws)
+
+    def mk_events(n):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        for e in evs:
+            e.record(stream)
+        return evs
+
+    for k in range(args.warmup):
+        flush.fill_(k & 0xFF)
+        call()
+    torch.cuda.synchronize()
+    cov.check_device_status(ws)
+
+    K = args.steps
+    starts, ends = mk_events(K), mk_events(K)
+    stages = [mk_events(5) for _ in range(K)]
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    barrier()
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_((k + 1) & 0xFF)
+        cov.set_stage_events(stages[k])
+        starts[k].record(stream)
+        call()
+        ends[k].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    cov.set_stage_events(None)
+    clocks = sampler.stop(local) if rank == 0 else None
+    cov.check_device_status(ws)
+    step_ms = [starts[k].elapsed_time(ends[k]) for k in range(K)]
+    stage_ms = [[stages[k][i].elapsed_time(stages[k][i + 1]) for k in range(K)] for i in range(4)]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = um * K * world / total_s
+    ms_per_step = total_s * 1e3 / K
+
+    # ---- end to end through the public API with host buffers -------------
+    A_host = torch.from_numpy(A_np).pin_memory()
+    R_host = torch.empty((D, D), dtype=dt).pin_memory()
+    A_e2e = torch.empty_like(A)
+    Ke = max(3, min(K, 200))
+    e_s, e_e = mk_events(Ke), mk_events(Ke)
+    for k in range(3):
+        A_e2e.copy_(A_host, non_blocking=True)
+        call(A_e2e)
+        R_host.copy_(R, non_blocking=True)
+    barrier()
+    for k in range(Ke):
+        flush.fill_(k & 0xFF)
+        e_s[k].record(stream)
+        A_e2e.copy_(A_host, non_blocking=True)
+        call(A_e2e)
+        R_host.copy_(R, non_blocking=True)
+        e_e[k].record(stream)
+    barrier()
+    e2e_s = sum(e_s[k].elapsed_time(e_e[k]) for k in range(Ke)) / 1e3
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": um * Ke * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": A_host.numel() * A_host.element_size(),
+           "d2h_bytes_per_step": R_host.numel() * R_host.element_size(),
+           "ms_per_step": e2e_s * 1e3 / Ke}
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (products over inner rows) --------
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    f_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * f_max * 1e6  # FLOP/s
+    fp64 = w.dtype == "c128"
+    k1_ms = statistics.mean(stage_ms[0])
+    k1_flops = 8.0 * info["products_inner"]          # 4 FMA per complex product
+    achieved = k1_flops / (k1_ms * 1e-3)
+    traffic = NCU_TRAFFIC.get((w.name, kernel_source_hash()))
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                "kernel": "k_products_inner", "peak_source": (
+                    f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {f_max:.0f} MHz "
+                    f"({'MEASURED_PEAKS.json sm_max_mhz' if 'sm_max_mhz' in peaks else 'recipe max clock'})"
+                    + ("; this workload computes in FP64: the FP32 figure is an upper bound" if fp64 else "")),
+                "algorithmic_flops_per_launch": k1_flops, "launch_ms": k1_ms}
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9
+    bytes_io = w.N * w.M * A.element_size() + D * D * R.element_size()
+    t_roof = max(4.0 * um / (fp32_peak / 2), bytes_io / hbm)
+    step_roofline = {"t_roof_us": t_roof * 1e6, "t_step_us": ms_per_step * 1e3,
+                     "frac": t_roof / (ms_per_step * 1e-3),
+                     "definition": "max(4*UM / FP32 FMA peak, (A+R bytes) / HBM)"}
+
+    # ---- plain FP64 GPU path on the same input, and error vs FP64 ----------
+    Rd = torch.empty_like(R)
+    cov.estimate_into(A, Rd, w.P, w.Q, algo="direct", workspace=ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0, ev1 = mk_events(2)
+    ev0.record(stream)
+    cov.estimate_into(A, Rd, w.P, w.Q, algo="direct", workspace=ws)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    direct_ms = ev0.elapsed_time(ev1)
+    call()
+    torch.cuda.synchronize()
+    Rn, Rdn = R.cpu().numpy().astype(np.complex128), Rd.cpu().numpy().astype(np.complex128)
+    err_fro = float(np.linalg.norm(Rn - Rdn) / np.linalg.norm(Rdn))
+    err_max = float(np.abs(Rn - Rdn).max() / np.abs(Rdn).max())
+    hermitian = bool(np.array_equal(Rn, Rn.conj().T))
+    lam_min = float(np.linalg.eigvalsh(Rn).min())
+    norm2 = float(np.linalg.norm(Rn, 2))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
+        "data": "synthetic", "config": _config(w),
+        "r_elements_per_s": D * D * K * world / total_s,
+        "vs_plain_fp64_gpu": {"speedup": direct_ms / ms_per_step, "fp64_direct_ms": direct_ms},
+        "err_vs_fp64": {"rel_fro": err_fro, "max_abs_rel_to_max": err_max,
+                        "reference": "plain FP64 GPU path (COV_DIRECT) on the same input"},
+        "checks": {"hermitian_exact": hermitian, "min_eig_over_norm": lam_min / norm2},
+        "stages_ms": {n: statistics.mean(s) for n, s in
+                      zip(("products_inner", "fringe_rows", "reduce_cols", "walk_write"), stage_ms)},
+        "roofline": roofline, "step_roofline": step_roofline, "e2e": e2e,
+        "gpu_launches": 4 * K, "clocks": clocks,
+        "wall_ms_incl_l2_flush": wall * 1e3,
+    }
+
+    if world == 1 and not args.no_cpu_baseline:
+        def gpu_check(Asub):
+            At = torch.from_numpy(np.ascontiguousarray(Asub)).cuda()
+            return cov.estimate(At, w.P, w.Q, algo="recurrence").cpu().numpy().astype(np.complex128)
+        line["cpu_baseline"] = cpu_baseline_leg(A_np, w.P, w.Q, um, w.K, args.cpu_seconds, gpu_check)
+    if args.extras:
+        line["rows"] = extras(args, cov, torch, np, wl, mk_events, stream)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(args, cov, torch, np, wl, mk_events, stream) -> dict:
+    """Timings of the other workloads through the same path (not bench lines)."""
+    out = {}
+    for name in ("plain_64x64_w8_f64", "sar_2048x512_w32_f32"):
+        w = wl.WORKLOADS[name]
+        dt = torch.complex64 if w.dtype == "c64" else torch.complex128
+        A = torch.from_numpy(wl.workload_input(w)).cuda()
+        D = w.P * w.Q
+        R = torch.empty((D, D), dtype=dt, device="cuda")
+        ws = torch.empty(cov.workspace_size(w.dtype, w.N, w.M, w.P, w.Q, "recurrence"),
+                         dtype=torch.uint8, device="cuda")
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        for _ in range(5):
+            cov.estimate_into(A, R, w.P, w.Q, algo="recurrence", workspace=ws)
+        n = 50
+        s, e = mk_events(n), mk_events(n)
+        torch.cuda.synchronize()
+        for k in range(n):
+            flush.fill_(k & 0xFF)
+            s[k].record(stream)
+            cov.estimate_into(A, R, w.P, w.Q, algo="recurrence", workspace=ws)
+            e[k].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(s[k].elapsed_time(e[k]) for k in range(n)) / n
+        info = cov.plan_info(w.N, w.M, w.P, w.Q)
+        Rd = torch.empty_like(R)
+        ev = mk_events(2)
+        ev[0].record(stream)
+        cov.estimate_into(A, Rd, w.P, w.Q, algo="direct", workspace=ws)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        dms = ev[0].elapsed_time(ev[1])
+        Rn, Rdn = R.cpu().numpy().astype(np.complex128), Rd.cpu().numpy().astype(np.complex128)
+        out[name] = {"ms_per_call": ms, "distinct_products_per_s": info["distinct_products"] / (ms * 1e-3),
+                     "r_elements_per_s": D * D / (ms * 1e-3), "fp64_direct_ms": dms,
+                     "speedup_vs_fp64_direct": dms / ms,
+                     "err_vs_fp64_direct_rel_fro": float(np.linalg.norm(Rn - Rdn) / np.linalg.norm(Rdn))}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", action="store_true", default=True)
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        return bench_reference(args, rank, world)
+    return bench_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -140,6 +140,16 @@ cov_status cov_estimate(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
  * COV_EDEVICE; COV_ECUDA if the copy itself fails. */
 cov_status cov_check_device_status(void *workspace, cov_stream_t stream);
 
+/* Instrumentation (not in the paper). With events != NULL, each following
+ * cov_estimate_ex call of COV_RECURRENCE records events[0..n_events-1]
+ * (cudaEvent_t handles owned by the caller, n_events >= 5) on its stream:
+ * before its first kernel and after each of its four kernels (products over
+ * inner rows, fringe rows, column reduction, walk-and-write), so that
+ * cudaEventElapsedTime between consecutive events times one kernel. NULL
+ * switches this off. Process-wide host state; not thread safe. COV_EINVAL if
+ * 0 < n_events < 5. */
+cov_status cov_set_stage_events(void *const *events, int n_events);
+
 /* ---------------------------------------------------------------------------
  * Many input matrices of uneven N, M, P, Q in one launch sequence
  * (Section 5.1: computing several matrices concurrently to keep all cores

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("cov_estimate_ex", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _VP, _I, _I, _VP, _SZ, _VP]),
     ("cov_estimate", _I, [_VP, _I, _I64, _I64, _I, _I, _VP, _VP]),
     ("cov_check_device_status", _I, [_VP, _VP]),
+    ("cov_set_stage_events", _I, [ctypes.POINTER(_VP), _I]),
     ("cov_batched_plan_create", _I, [ctypes.POINTER(CovDesc), _I, _I, _I, _I,
                                      ctypes.POINTER(_VP)]),
     ("cov_batched_workspace_size", _I, [_VP, ctypes.POINTER(_SZ)]),
@@ -166,6 +167,17 @@ def estimate(A, P: int, Q: int, algo: str = "auto", norm: str = "mean", workspac
     torch = _torch()
     R = torch.empty((P * Q, P * Q), dtype=A.dtype, device=A.device)
     return estimate_into(A, R, P, Q, algo, norm, workspace, stream)
+
+
+def set_stage_events(events) -> None:
+    """Instrumentation: record the given torch.cuda.Events (5, created) around
+    the four kernels of each following recurrence call; None switches off."""
+    lib = load()
+    if events is None:
+        _check(lib.cov_set_stage_events(None, 0), "cov_set_stage_events")
+        return
+    arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+    _check(lib.cov_set_stage_events(arr, len(events)), "cov_set_stage_events")
 
 
 def check_device_status(workspace, stream=None) -> None:

@@ -30,6 +30,8 @@ bool shape_ok(int64_t N, int64_t M, int P, int Q) {
          M < (1LL << 30) && (int64_t)P * Q <= (1LL << 15);
 }
 
+StageEvents g_stage_events = {{nullptr, nullptr, nullptr, nullptr, nullptr}, false};
+
 cov_algo resolve_algo(cov_algo algo, int64_t N, int64_t M, int P, int Q) {
   if (algo != COV_AUTO) return algo;
   return recurrence_ok(N, M, P, Q) ? COV_RECURRENCE : COV_DIRECT;
@@ -146,7 +148,8 @@ cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M,
       const int sms = device_sms();
       if (sms <= 0) return COV_ECUDA;
       if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
-      if (launch_recurrence(p, dtype == COV_C128, sms, s) != cudaSuccess) return COV_ECUDA;
+      if (launch_recurrence(p, dtype == COV_C128, sms, s, &g_stage_events) != cudaSuccess)
+        return COV_ECUDA;
       return COV_OK;
     }
     case COV_DIRECT: {
@@ -181,6 +184,20 @@ cov_status cov_estimate(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
   st = cov_estimate_ex(A, dtype, N, M, M, P, Q, R, COV_AUTO, COV_MEAN, ws, bytes, stream);
   if (ws && cudaFreeAsync(ws, s) != cudaSuccess && st == COV_OK) st = COV_ECUDA;
   return st;
+}
+
+cov_status cov_set_stage_events(void *const *events, int n_events) {
+  if (!events) {
+    g_stage_events.on = false;
+    return COV_OK;
+  }
+  if (n_events < 5) return COV_EINVAL;
+  for (int k = 0; k < 5; ++k) {
+    if (!events[k]) return COV_EINVAL;
+    g_stage_events.ev[k] = (cudaEvent_t)events[k];
+  }
+  g_stage_events.on = true;
+  return COV_OK;
 }
 
 cov_status cov_check_device_status(void *workspace, cov_stream_t stream) {

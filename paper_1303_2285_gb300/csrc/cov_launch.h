@@ -17,7 +17,14 @@ struct DirectParams {
   int mean;
 };
 
-cudaError_t launch_recurrence(const RecParams &p, bool fp64, int num_sms, cudaStream_t s);
+// Optional events recorded around the four kernels (see cov_set_stage_events).
+struct StageEvents {
+  cudaEvent_t ev[5];
+  bool on;
+};
+
+cudaError_t launch_recurrence(const RecParams &p, bool fp64, int num_sms, cudaStream_t s,
+                              const StageEvents *events);
 cudaError_t launch_direct(const DirectParams &p, bool c128, cudaStream_t s);
 
 }  // namespace cov

@@ -429,8 +429,13 @@ static cudaError_t launch_products(const RecParams &p, int num_sms, cudaStream_t
 }
 
 template <typename T>
-static cudaError_t launch_rec(const RecParams &p, int num_sms, cudaStream_t s) {
+static cudaError_t launch_rec(const RecParams &p, int num_sms, cudaStream_t s,
+                             const StageEvents *ev) {
   cudaError_t e = cudaSuccess;
+  auto mark = [&](int k) -> cudaError_t {
+    return (ev && ev->on) ? cudaEventRecord(ev->ev[k], s) : cudaSuccess;
+  };
+  if ((e = mark(0)) != cudaSuccess) return e;
   if (p.n_inner > 0 && p.n_tasks > 0) {
     switch (p.G) {
       case 4: e = launch_products<T, 4>(p, num_sms, s); break;
@@ -440,6 +445,7 @@ static cudaError_t launch_rec(const RecParams &p, int num_sms, cudaStream_t s) {
     }
     if (e != cudaSuccess) return e;
   }
+  if ((e = mark(1)) != cudaSuccess) return e;
   if (p.NFR > 0) {
     const long long warps = 2LL * p.nrb * p.ngroups_f;
     const long long blocks = (warps + 3) / 4;
@@ -447,12 +453,14 @@ static cudaError_t launch_rec(const RecParams &p, int num_sms, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if ((e = mark(2)) != cudaSuccess) return e;
   {
     const long long blocks = ((long long)p.n_uc + 3) / 4;
     k_reduce_cols<T><<<(unsigned)blocks, 128, 0, s>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if ((e = mark(3)) != cudaSuccess) return e;
   {
     const int nblk = p.Q * (p.Q + 1) / 2;
     const int nthr_need = (2 * p.P - 1) * ((p.P + p.L - 1) / p.L);
@@ -464,12 +472,14 @@ static cudaError_t launch_rec(const RecParams &p, int num_sms, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     kern<<<nblk, nthr, smem, s>>>(p);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  return e;
+  return mark(4);
 }
 
-cudaError_t launch_recurrence(const RecParams &p, bool fp64, int num_sms, cudaStream_t s) {
-  return fp64 ? launch_rec<double>(p, num_sms, s) : launch_rec<float>(p, num_sms, s);
+cudaError_t launch_recurrence(const RecParams &p, bool fp64, int num_sms, cudaStream_t s,
+                              const StageEvents *ev) {
+  return fp64 ? launch_rec<double>(p, num_sms, s, ev) : launch_rec<float>(p, num_sms, s, ev);
 }
 
 }  // namespace cov

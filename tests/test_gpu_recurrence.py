@@ -127,10 +127,17 @@ def test_convenience_entry_point(oracle_mod):
 def test_workspace_errors():
     A = torch.zeros((64, 64), dtype=torch.complex64, device="cuda")
     R = torch.empty((64, 64), dtype=torch.complex64, device="cuda")
-    small = torch.empty(256, dtype=torch.uint8, device="cuda")
-    with pytest.raises(cov.CovError) as e:
+    small = torch.empty(512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
         cov.estimate_into(A, R, 8, 8, algo="recurrence", workspace=small)
-    assert "workspace" in str(e.value) or e.value.code == 3
+    lib = cov.load()
+    s = torch.cuda.current_stream().cuda_stream
+    code = lib.cov_estimate_ex(A.data_ptr(), 0, 64, 64, 64, 8, 8, R.data_ptr(), 1, 0,
+                               small.data_ptr(), small.numel(), s)
+    assert code == 3  # COV_EWORKSPACE
+    code = lib.cov_estimate_ex(A.data_ptr(), 0, 64, 64, 64, 8, 8, R.data_ptr(), 1, 0,
+                               small.data_ptr() + 8, 1 << 30, s)
+    assert code == 3  # misaligned
 
 
 def test_repeated_calls_reuse_workspace(oracle_mod):
