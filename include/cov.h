@@ -135,6 +135,36 @@ cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M,
 cov_status cov_estimate(const void *A, cov_dtype dtype, int64_t N, int64_t M, int P,
                         int Q, void *R, cov_stream_t stream);
 
+/* Size of the static device scratch array behind cov_estimate_noalloc. */
+#define COV_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* Same computation as cov_estimate_ex with COV_RECURRENCE, for callers that
+ * must not allocate device memory during a call: for example a plugin whose
+ * host application's memory pool already holds the device memory, or a
+ * real-time radar / SAR processing loop whose device-memory budget is fixed
+ * at start-up so that no call can fail, stall or fragment memory mid-stream.
+ * The paper has no counterpart; this is a property of the library.
+ *
+ * The scratch space is a static device array of COV_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) inside this library, which every GPU that loads the library holds
+ * until the process exits. The caller still passes A and R (device, as for
+ * cov_estimate_ex). Nothing is allocated or freed: no cudaMalloc, cudaFree
+ * or allocating library routine is called.
+ * - The first call made while a given device is current looks up the array's
+ *   device address on that device (cudaGetSymbolAddress) and caches it; make
+ *   that first call before any stream capture.
+ * - Problems whose scratch need exceeds COV_NOALLOC_SCRATCH_BYTES (see
+ *   cov_workspace_size with COV_RECURRENCE) are rejected with COV_EWORKSPACE
+ *   before any work is queued; COV_EUNSUPPORTED for shapes COV_RECURRENCE
+ *   does not take.
+ * - All calls on a device share the one array, which keeps the previous
+ *   call's contents (each call clears what must start at zero). Calls whose
+ *   work overlaps on the GPU (different streams, or different host threads
+ *   without ordering) race on the array: order them on one stream. */
+cov_status cov_estimate_noalloc(const void *A, cov_dtype dtype, int64_t N, int64_t M,
+                                int64_t lda, int P, int Q, void *R, cov_norm norm,
+                                cov_stream_t stream);
+
 /* Reads (and then clears) the status word a previous call left at the start
  * of `workspace`. Synchronises `stream`. Returns COV_OK, COV_ETIMEOUT or
  * COV_EDEVICE; COV_ECUDA if the copy itself fails. */
