@@ -170,14 +170,15 @@ cov_status cov_estimate_noalloc(const void *A, cov_dtype dtype, int64_t N, int64
  * COV_EDEVICE; COV_ECUDA if the copy itself fails. */
 cov_status cov_check_device_status(void *workspace, cov_stream_t stream);
 
-/* Instrumentation (not in the paper). With events != NULL, each following
- * cov_estimate_ex call of COV_RECURRENCE records events[0..n_events-1]
- * (cudaEvent_t handles owned by the caller, n_events >= 5) on its stream:
- * before its first kernel and after each of its four kernels (products over
- * inner rows, fringe rows, column reduction, walk-and-write), so that
- * cudaEventElapsedTime between consecutive events times one kernel. NULL
- * switches this off. Process-wide host state; not thread safe. COV_EINVAL if
- * 0 < n_events < 5. */
+/* Instrumentation (not in the paper). With events != NULL, following
+ * cov_estimate_ex calls of COV_RECURRENCE record five events each on their
+ * stream: before the first kernel and after each of the four kernels
+ * (products over inner rows, fringe rows, reductions, walk-and-write), so
+ * that cudaEventElapsedTime between consecutive events times one kernel. The
+ * events (cudaEvent_t handles owned by the caller; n_events a multiple of 5,
+ * at most 5*4096) are used in rounds: the c-th call after this one uses
+ * events[5*(c mod n_events/5) ...]. NULL switches this off. Process-wide
+ * host state; not thread safe. COV_EINVAL on a bad count or a null handle. */
 cov_status cov_set_stage_events(void *const *events, int n_events);
 
 /* ---------------------------------------------------------------------------

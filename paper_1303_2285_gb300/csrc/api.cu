@@ -30,7 +30,8 @@ bool shape_ok(int64_t N, int64_t M, int P, int Q) {
          M < (1LL << 30) && (int64_t)P * Q <= (1LL << 15);
 }
 
-StageEvents g_stage_events = {{nullptr, nullptr, nullptr, nullptr, nullptr}, false};
+StageEvents g_stage_events = {nullptr, 0, 0, false};
+cudaEvent_t g_stage_store[5 * 4096];
 
 cov_algo resolve_algo(cov_algo algo, int64_t N, int64_t M, int P, int Q) {
   if (algo != COV_AUTO) return algo;
@@ -143,6 +144,7 @@ cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M,
       p.status = (unsigned *)w;
       p.core_part = w + ws.core_off;
       p.colsum_part = w + ws.colsum_off;
+      p.sin_part = w + ws.sin_off;
       p.rowval = w + ws.rowval_off;
       p.colval = w + ws.colval_off;
       const int sms = device_sms();
@@ -191,11 +193,14 @@ cov_status cov_set_stage_events(void *const *events, int n_events) {
     g_stage_events.on = false;
     return COV_OK;
   }
-  if (n_events < 5) return COV_EINVAL;
-  for (int k = 0; k < 5; ++k) {
+  if (n_events < 5 || n_events % 5 != 0 || n_events > 5 * 4096) return COV_EINVAL;
+  for (int k = 0; k < n_events; ++k) {
     if (!events[k]) return COV_EINVAL;
-    g_stage_events.ev[k] = (cudaEvent_t)events[k];
+    g_stage_store[k] = (cudaEvent_t)events[k];
   }
+  g_stage_events.ev = g_stage_store;
+  g_stage_events.rounds = n_events / 5;
+  g_stage_events.calls = 0;
   g_stage_events.on = true;
   return COV_OK;
 }

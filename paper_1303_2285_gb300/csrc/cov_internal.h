@@ -17,11 +17,12 @@
 //   Kernel 1 (products_inner): inner rows x all columns. For each Delta the
 //     sum over (inner rows x inner cols) -> core partials; per fringe column
 //     the sum over inner rows -> colsum partials.
-//   Kernel 2 (fringe_rows): each fringe row: the sum over inner columns plus
-//     its own fringe-column products, combined into the box-row sums
-//     RV[Delta][j][fr] = sum_{m in [j, j+M-Q]} Pi_D[n][m].
-//   Kernel 3 (reduce_cols): CV[Delta][j] = sum over inner rows of the box-row
-//     sums at column offset j (core + fringe-column sums).
+//   Kernel 2 (fringe_rows): each fringe row's sums over chunks of the inner
+//     columns (partials of S_in[Delta][fr]).
+//   Kernel 3 (reduce): CV[Delta][j] = sum over inner rows of the box-row sums
+//     at column offset j (core + fringe-column sums), and the box-row sums
+//     RV[Delta][j][fr] = sum_{m in [j, j+M-Q]} Pi_D[n][m] of each fringe row
+//     (S_in plus the row's own fringe-column products).
 //   Kernel 4 (walk_write): per output block, seed each diagonal segment with
 //     the direct sum CV + sum of RV over the fringe rows inside the box, walk
 //     down the diagonal by subtracting the leaving top row and adding the
@@ -66,7 +67,8 @@ COV_HD void combo_of(int P, int idx, int &dr, int &dc) {
 
 // Lag groups: consecutive dr values of one dc, G per group. Group g gives
 // (dc, d0, cnt): lags dr = d0 .. d0+cnt-1 (cnt <= G). The G - cnt unused
-// slots of the last group of each dc read zero-filled rows and are dropped.
+// slots of the last group of each dc form products that are never used
+// (their accumulators are dropped); the smem halo covers their rows.
 COV_HD int groups_dc0(int P, int G) { return (P + G - 1) / G; }
 COV_HD int groups_per_dc(int P, int G) { return (2 * P - 1 + G - 1) / G; }
 COV_HD int n_groups(int P, int Q, int G) {
@@ -112,20 +114,27 @@ struct RecParams {
   int ngroups;
   int inner_lo;         // P-1
   int n_inner;          // N-2P+2
-  int TR, TC, CBT;      // tile rows, tile cols, 32-col blocks per tile
+  int TRB;              // rows per warp task (one partial row block)
+  int TPT;              // row blocks per smem tile
+  int TR, TC, CBT;      // tile rows (TRB*TPT), tile cols (64), 32-col blocks per tile
+  int n_rb;             // row blocks over the inner rows
   int n_rt, n_ct, n_cb; // row tiles, col tiles, 32-col blocks over [0, M)
   int d_lo, d_hi;       // lag range covered by the smem tile
-  int STR, STC;         // smem tile rows and pitch (elements)
+  int STR, PITCH;       // smem tile rows and pitch (complex elements; 80 or 96)
+  int use_tma;          // stage tiles with TMA (set at launch)
   long long tasks_per_tile, n_tasks;
   // fringe-row kernel
   int NFR, NFC;         // 2(P-1), 2(Q-1)
   int GF, ngroups_f, RB, nrb;
+  int CWF, NCH;         // inner-column chunk width and count of the fringe-row kernel
+  int QMAXF, FPITCH;    // its column-lag register count (>= Q) and smem pitch
   // walk
   int L;                // re-seed interval along the diagonal
   // workspace
   unsigned *status;
-  void *core_part;      // [n_uc][n_rt][n_cb]
-  void *colsum_part;    // [n_uc][NFC][n_rt]
+  void *core_part;      // [n_uc][n_rb][n_cb]
+  void *colsum_part;    // [n_uc][NFC][n_rb]
+  void *sin_part;       // [n_uc][NFR][NCH]
   void *rowval;         // [n_uc][Q][NFR]
   void *colval;         // [n_uc][Q]
 };

@@ -1,6 +1,7 @@
 // Host-side launch entry points of the kernel files (internal).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "cov_internal.h"
@@ -17,14 +18,25 @@ struct DirectParams {
   int mean;
 };
 
-// Optional events recorded around the four kernels (see cov_set_stage_events).
+// Optional events recorded around the four kernels (see cov_set_stage_events):
+// call number c uses ev[5*(c % rounds) .. 5*(c % rounds)+4].
 struct StageEvents {
-  cudaEvent_t ev[5];
+  cudaEvent_t *ev;
+  int rounds;
+  long long calls;
   bool on;
 };
 
 cudaError_t launch_recurrence(const RecParams &p, bool fp64, int num_sms, cudaStream_t s,
-                              const StageEvents *events);
+                              StageEvents *events);
+
+// The four kernels of the combination path (rec_products.cu, rec_fringe.cu,
+// rec_reduce.cu). `pdl`: launch with programmatic stream serialization.
+cudaError_t launch_products_any(const RecParams &p, const CUtensorMap &tmap, bool fp64, int num_sms,
+                                cudaStream_t s);
+cudaError_t launch_fringe(const RecParams &p, bool fp64, cudaStream_t s, bool pdl);
+cudaError_t launch_reduce(const RecParams &p, bool fp64, cudaStream_t s, bool pdl);
+cudaError_t launch_walk(const RecParams &p, bool fp64, cudaStream_t s, bool pdl);
 cudaError_t launch_direct(const DirectParams &p, bool c128, cudaStream_t s);
 
 }  // namespace cov

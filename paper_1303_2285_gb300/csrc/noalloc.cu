@@ -86,6 +86,7 @@ extern "C" cov_status cov_estimate_noalloc(const void *A, cov_dtype dtype, int64
   p.status = (unsigned *)w;
   p.core_part = w + ws.core_off;
   p.colsum_part = w + ws.colsum_off;
+  p.sin_part = w + ws.sin_off;
   p.rowval = w + ws.rowval_off;
   p.colval = w + ws.colval_off;
   // The status word must start at zero; every other scratch region is fully

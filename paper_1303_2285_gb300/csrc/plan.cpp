@@ -29,15 +29,16 @@ bool recurrence_ok(long long N, long long M, int P, int Q) {
          M >= 2LL * Q - 1 && N < (1LL << 30) && M < (1LL << 30);
 }
 
-int choose_group(int P, int Q) {
+int choose_group(int P, int Q, int elem) {
   const int cand[3] = {16, 8, 4};
+  const int first = elem > 8 ? 1 : 0;  // FP64: at most 8 lags (registers)
   const double uc = (double)n_unique_combinations(P, Q);
   double waste[3], best = 1e30;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = first; k < 3; ++k) {
     waste[k] = (double)n_groups(P, Q, cand[k]) * cand[k] / uc - 1.0;
     if (waste[k] < best) best = waste[k];
   }
-  for (int k = 0; k < 3; ++k)
+  for (int k = first; k < 3; ++k)
     if (waste[k] <= best + 0.02) return cand[k];
   return 4;
 }
@@ -52,43 +53,38 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.lda = lda;
   p.K = n_positions(N, M, P, Q);
   p.n_uc = (int)n_unique_combinations(P, Q);
-  p.G = choose_group(P, Q);
+  p.G = choose_group(P, Q, elem);
   p.ngroups = n_groups(P, Q, p.G);
   p.inner_lo = P - 1;
   p.n_inner = (int)(N - 2LL * P + 2);
   p.d_lo = group_lag_lo(P, Q);
   p.d_hi = group_lag_hi(P, Q, p.G);
   const int span = p.d_hi - p.d_lo;
-  p.TC = M >= 64 ? 64 : 32;
-  p.CBT = p.TC / 32;
-  p.STC = p.TC + Q - 1;
-  p.STC += p.STC & 1;
+  // Tiles: 64 columns, smem pitch 80 (Q <= 17) or 96 (Q <= 33) complex
+  // elements; two buffers of STR rows each within the 227 KB of a CTA.
+  p.TC = 64;
+  p.CBT = 2;
+  p.PITCH = Q <= 17 ? 80 : 96;
   p.n_cb = (int)((M + 31) / 32);
   p.n_ct = (int)((M + p.TC - 1) / p.TC);
-  // Tile rows: two buffers of at most `budget` bytes each; prefer a budget
-  // that leaves room for two CTAs per SM when the tile is not too short.
-  const int R = 8;
-  const long long row_bytes = (long long)p.STC * elem;
-  long long budget = 56 * 1024;
-  long long tr_max = budget / row_bytes - span;
-  if (tr_max < 48) {
-    budget = 110 * 1024;
-    tr_max = budget / row_bytes - span;
-  }
-  if (tr_max < R) tr_max = R;  // shapes this large in Q are rejected earlier
-  if (tr_max > 128) tr_max = 128;
-  int n_rt = (int)((p.n_inner + tr_max - 1) / tr_max);
-  if (n_rt < 1) n_rt = 1;
-  int TR = 0;
-  for (;; ++n_rt) {
-    const int per = (p.n_inner + n_rt - 1) / n_rt;
-    TR = ((per + R - 1) / R) * R;
-    if (TR <= tr_max || TR <= R) break;
-  }
-  p.TR = TR;
-  p.n_rt = (p.n_inner + TR - 1) / TR;
-  p.STR = TR + span;
-  p.tasks_per_tile = (long long)p.ngroups * p.CBT;
+  const long long buf_bytes = (232448LL - 1024) / 2;
+  long long rows_max = buf_bytes / ((long long)p.PITCH * elem);
+  if (rows_max > 256) rows_max = 256;  // TMA box height
+  long long tr_max = rows_max - span;
+  if (tr_max < 8) tr_max = 8;
+  int TRB = tr_max >= 48 ? 48 : (int)(tr_max / 8) * 8;
+  if (TRB < 8) TRB = 8;
+  int TPT = (int)(tr_max / TRB);
+  if (TPT > 4) TPT = 4;
+  if (TPT < 1) TPT = 1;
+  p.TRB = TRB;
+  p.n_rb = (p.n_inner + TRB - 1) / TRB;
+  if (TPT > p.n_rb) TPT = p.n_rb;
+  p.TPT = TPT;
+  p.TR = TRB * TPT;
+  p.n_rt = (p.n_rb + TPT - 1) / TPT;
+  p.STR = p.TR + span;
+  p.tasks_per_tile = (long long)p.ngroups * p.CBT * p.TPT;
   p.n_tasks = (long long)p.n_rt * p.n_ct * p.tasks_per_tile;
   // fringe rows
   p.NFR = 2 * (P - 1);
@@ -97,14 +93,20 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.RB = 4;
   p.ngroups_f = n_groups(P, Q, p.GF);
   p.nrb = (P - 1 + p.RB - 1) / p.RB;
+  p.CWF = 32;
+  p.NCH = (int)((M - 2LL * Q + 2 + p.CWF - 1) / p.CWF);
+  p.QMAXF = Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
+  p.FPITCH = ((p.CWF + p.QMAXF - 1 + 14) / 16) * 16 + 1;  // >= CWF+QMAXF-1, = 1 mod 16
   p.L = 8;
   p.div_double = (elem == 8 && p.K > (1LL << 24)) ? 1 : 0;
   // workspace
   size_t off = kWsHeader;
   ws.core_off = off;
-  off = align256(off + (size_t)p.n_uc * p.n_rt * p.n_cb * elem);
+  off = align256(off + (size_t)p.n_uc * p.n_rb * p.n_cb * elem);
   ws.colsum_off = off;
-  off = align256(off + (size_t)p.n_uc * p.NFC * p.n_rt * elem);
+  off = align256(off + (size_t)p.n_uc * p.NFC * p.n_rb * elem);
+  ws.sin_off = off;
+  off = align256(off + (size_t)p.n_uc * p.NFR * p.NCH * elem);
   ws.rowval_off = off;
   off = align256(off + (size_t)p.n_uc * Q * p.NFR * elem);
   ws.colval_off = off;

@@ -10,7 +10,7 @@
 namespace cov {
 
 struct WsLayout {
-  size_t core_off, colsum_off, rowval_off, colval_off, total;
+  size_t core_off, colsum_off, sin_off, rowval_off, colval_off, total;
 };
 
 // Number of window positions, |UC| and UM for an N x M input, P x Q window
@@ -23,9 +23,9 @@ long long distinct_products(long long N, long long M, int P, int Q);
 // 1 <= P, Q <= kMaxPQ).
 bool recurrence_ok(long long N, long long M, int P, int Q);
 
-// Lags per group: the largest of 16, 8, 4 whose unused slots stay within 2%
-// of the fewest.
-int choose_group(int P, int Q);
+// Lags per group: the largest of 16, 8, 4 (8, 4 for FP64) whose unused
+// slots stay within 2% of the fewest.
+int choose_group(int P, int Q, int elem);
 
 // Fills every field of p that depends on the shape only (not the pointers);
 // returns the workspace layout. elem = bytes of one complex number.
