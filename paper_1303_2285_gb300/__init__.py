@@ -170,6 +170,45 @@ def estimate(A, P: int, Q: int, algo: str = "auto", norm: str = "mean", workspac
     return estimate_into(A, R, P, Q, algo, norm, workspace, stream)
 
 
+class BatchedPlan:
+    """Many matrices of uneven shapes in one persistent launch (cov_batched_*).
+
+    ``items``: sequence of (A, R, P, Q) with A an N x M complex64 CUDA tensor
+    (unit column stride) and R a contiguous PQ x PQ complex64 CUDA tensor. The
+    plan keeps the device pointers: the tensors must outlive it.
+    """
+
+    def __init__(self, items, norm: str = "mean"):
+        lib = load()
+        n = len(items)
+        arr = (CovDesc * n)()
+        for k, (A, R, P, Q) in enumerate(items):
+            if not (A.is_cuda and R.is_cuda) or A.stride(1) != 1 or not R.is_contiguous():
+                raise ValueError("A and R must be CUDA tensors (A unit column stride, R contiguous)")
+            arr[k] = CovDesc(A.data_ptr(), R.data_ptr(), A.stride(0), A.shape[0], A.shape[1], P, Q)
+        ptr = ctypes.c_void_p()
+        _check(lib.cov_batched_plan_create(arr, n, DTYPES["c64"], ALGOS["auto"], NORMS[norm],
+                                           ctypes.byref(ptr)), "cov_batched_plan_create")
+        self._lib = lib
+        self.ptr = ptr
+        out = ctypes.c_size_t(0)
+        _check(lib.cov_batched_workspace_size(ptr, ctypes.byref(out)), "cov_batched_workspace_size")
+        self.workspace_bytes = int(out.value)
+
+    def upload(self, workspace, stream=None) -> None:
+        _check(self._lib.cov_batched_upload(self.ptr, workspace.data_ptr(), workspace.numel(),
+                                            _stream_ptr(stream)), "cov_batched_upload")
+
+    def run(self, workspace, stream=None) -> None:
+        _check(self._lib.cov_estimate_batched(self.ptr, workspace.data_ptr(), workspace.numel(),
+                                              _stream_ptr(stream)), "cov_estimate_batched")
+
+    def __del__(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            self._lib.cov_batched_plan_destroy(self.ptr)
+            self.ptr = None
+
+
 def set_stage_events(events) -> None:
     """Instrumentation: record the given torch.cuda.Events (5, created) around
     the four kernels of each following recurrence call; None switches off."""

@@ -218,32 +218,7 @@ cov_status cov_check_device_status(void *workspace, cov_stream_t stream) {
   return COV_EDEVICE;
 }
 
-// ---- not yet available: batched, backward -------------------------------
-struct cov_batched_plan {
-  int dummy;
-};
-
-cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype,
-                                   cov_algo algo, cov_norm norm, cov_batched_plan **plan) {
-  (void)descs; (void)count; (void)dtype; (void)algo; (void)norm; (void)plan;
-  return COV_EUNSUPPORTED;
-}
-cov_status cov_batched_workspace_size(const cov_batched_plan *plan, size_t *bytes) {
-  (void)plan; (void)bytes;
-  return COV_EUNSUPPORTED;
-}
-cov_status cov_batched_upload(const cov_batched_plan *plan, void *workspace, size_t ws_bytes,
-                              cov_stream_t stream) {
-  (void)plan; (void)workspace; (void)ws_bytes; (void)stream;
-  return COV_EUNSUPPORTED;
-}
-cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, size_t ws_bytes,
-                                cov_stream_t stream) {
-  (void)plan; (void)workspace; (void)ws_bytes; (void)stream;
-  return COV_EUNSUPPORTED;
-}
-void cov_batched_plan_destroy(cov_batched_plan *plan) { (void)plan; }
-
+// ---- not yet available: backward -----------------------------------------
 cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
                                        size_t *bytes) {
   (void)dtype; (void)N; (void)M; (void)P; (void)Q; (void)bytes;

@@ -1,0 +1,440 @@
+// Many input matrices of uneven N, M, P, Q in one persistent launch
+// (Section 5.1: computing several covariance matrices concurrently keeps every
+// core busy where one matrix has too few combinations).
+//
+// Each CTA owns whole matrices, taken from a schedule the host builds once by
+// longest-processing-time-first assignment (cost = distinct products, Eq. 3.6,
+// plus a per-combination overhead). A CTA never waits on another CTA, so the
+// launch is one kernel and can be captured in a CUDA graph.
+//
+// Per matrix, the CTA goes through the column lags dc = 0..Q-1; for one dc it
+// handles the combinations (dr, dc) of Eq. 3.3 together:
+//   A. products over the inner rows [P-1, N-P] (every box holds them): warp
+//      tasks (lag group of 8, 32 columns, row range), lanes own a column and
+//      register-block 8 rows x 8 lags; inner-column lanes are summed over the
+//      warp, fringe-column lanes keep their column sums;
+//   B. products of the fringe rows with the inner columns: warp tasks (4 rows,
+//      8 lags), lanes stride over the columns, one transpose reduction;
+//   C. per combination: the inner-row part CV[j] of the box sum at column
+//      offset j, and for each fringe row the box-row sums RV[j] (its own
+//      fringe-column products formed once, warp scans);
+//   D. per diagonal segment: seed with the direct sum over the box, walk down
+//      the diagonal (subtract the leaving top row, add the entering bottom
+//      row; compensated), divide by K, write R and its conjugate mirror.
+// Every element of R is written by one thread; partial sums are combined in a
+// fixed order in shared memory (no atomics).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <queue>
+#include <vector>
+
+#include "../../include/cov.h"
+#include "cov_device.cuh"
+#include "cov_internal.h"
+#include "plan.h"
+
+namespace cov {
+
+constexpr int kBMaxPQ = 16;      // P, Q <= 16
+constexpr int kBMaxM = 512;      // M <= 512 (16 column blocks)
+constexpr int kBMaxD = 2 * kBMaxPQ - 1;   // combinations per dc
+constexpr int kBMaxF = 2 * (kBMaxPQ - 1); // fringe rows / columns
+constexpr int kBMaxCB = kBMaxM / 32;
+constexpr int kBMaxRS = 4;       // row ranges of phase A
+constexpr int kBWarps = 16;
+constexpr int kBG = 8;           // lags per group
+
+struct BDesc {
+  const float2 *A;
+  float2 *R;
+  long long lda;
+  int N, M, P, Q;
+};
+
+struct BSmem {
+  float2 core[kBMaxD][kBMaxCB][kBMaxRS];
+  float2 cs[kBMaxD][kBMaxF][kBMaxRS];
+  float2 sin[kBMaxD][kBMaxF];
+  float2 cv[kBMaxD][kBMaxPQ];
+  float2 rv[kBMaxD][kBMaxPQ][kBMaxF];
+};
+
+__device__ __forceinline__ float2 ld2(const float2 *p) { return __ldg(p); }
+
+__global__ void __launch_bounds__(kBWarps * 32, 1)
+    k_batched(const BDesc *descs, const int *order, const int *cta_begin, int mean) {
+  extern __shared__ __align__(16) unsigned char smem_b[];
+  BSmem &S = *(BSmem *)smem_b;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int mi = cta_begin[blockIdx.x]; mi < cta_begin[blockIdx.x + 1]; ++mi) {
+    const BDesc d = descs[order[mi]];
+    const int N = d.N, M = d.M, P = d.P, Q = d.Q;
+    const long long lda = d.lda;
+    const float2 *A = d.A;
+    const int inner_lo = P - 1, n_inner = N - 2 * P + 2;
+    const int n_cb = (M + 31) / 32, NFR = 2 * (P - 1), NFC = 2 * (Q - 1), W = M - Q + 1;
+    const long long K = (long long)(N - P + 1) * (M - Q + 1);
+    const long long DD = (long long)P * Q;
+    for (int dc = 0; dc < Q; ++dc) {
+      const int dr_lo = dc ? -(P - 1) : 0;
+      const int nD = P - dr_lo, ng = (nD + kBG - 1) / kBG;
+      int RS = 1;
+      while (RS < kBMaxRS && ng * n_cb * RS < 2 * kBWarps && n_inner >= 16 * RS * 2) RS *= 2;
+      // ---- A: products over inner rows -------------------------------------
+      const int nA = ng * n_cb * RS;
+      for (int t = warp; t < nA; t += kBWarps) {
+        const int rs = t % RS, cb = (t / RS) % n_cb, g = t / (RS * n_cb);
+        const int d0 = dr_lo + g * kBG;
+        const int cnt = min(kBG, P - d0);
+        const int r_beg = inner_lo + (int)((long long)n_inner * rs / RS);
+        const int r_end = inner_lo + (int)((long long)n_inner * (rs + 1) / RS);
+        const int m = cb * 32 + lane;
+        const bool mok = m < M, bok = m + dc < M;
+        float2 acc[kBG];
+#pragma unroll
+        for (int k = 0; k < kBG; ++k) acc[k] = make_float2(0.f, 0.f);
+        for (int n = r_beg; n < r_end; n += 8) {
+          float2 a[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            a[r] = (mok && n + r < r_end) ? ld2(A + (long long)(n + r) * lda + m) : make_float2(0.f, 0.f);
+          float2 bv[8 + kBG - 1];
+#pragma unroll
+          for (int k = 0; k < 8 + kBG - 1; ++k) {
+            const int row = n + d0 + k;
+            bv[k] = (bok && row >= 0 && row < N) ? ld2(A + (long long)row * lda + m + dc)
+                                                  : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int k = 0; k < 8 + kBG - 1; ++k)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              const int gg = k - r;
+              if (gg >= 0 && gg < kBG) cmac_conj(acc[gg], a[r], bv[k]);
+            }
+        }
+        const bool inner = m >= Q - 1 && m <= M - Q;
+        if (mok && !inner) {
+          const int fc = m < Q - 1 ? m : m - (M - 2 * Q + 2);
+#pragma unroll
+          for (int k = 0; k < kBG; ++k)
+            if (k < cnt) S.cs[d0 + k - dr_lo][fc][rs] = acc[k];
+        }
+        float v[2 * kBG];
+#pragma unroll
+        for (int k = 0; k < kBG; ++k) {
+          v[2 * k] = inner ? acc[k].x : 0.f;
+          v[2 * k + 1] = inner ? acc[k].y : 0.f;
+        }
+        warp_transpose_reduce<2 * kBG>(v, lane);  // lane holds value index lane >> 1
+        if ((lane & 1) == 0) {
+          const int k = lane >> 2, comp = (lane >> 1) & 1;
+          if (k < cnt) ((float *)&S.core[d0 + k - dr_lo][cb][rs])[comp] = v[0];
+        }
+      }
+      // ---- B: fringe rows x inner columns ---------------------------------
+      const int nrb = (P - 1 + 3) / 4;
+      const int nB = 2 * nrb * ng;
+      for (int t = warp; t < nB; t += kBWarps) {
+        const int g = t % ng, rb = (t / ng) % nrb, side = t / (ng * nrb);
+        const int d0 = dr_lo + g * kBG, cnt = min(kBG, P - d0);
+        const int fr0 = rb * 4, nrows = min(4, P - 1 - fr0);
+        const int nbase = side == 0 ? fr0 : (N - P + 1) + fr0;
+        float2 acc[4][kBG];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int k = 0; k < kBG; ++k) acc[r][k] = make_float2(0.f, 0.f);
+        for (int m = Q - 1 + lane; m <= M - Q; m += 32) {
+          float2 a[4], bv[4 + kBG - 1];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            a[r] = r < nrows ? ld2(A + (long long)(nbase + r) * lda + m) : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < 4 + kBG - 1; ++k) {
+            const int row = nbase + d0 + k;
+            bv[k] = (row >= 0 && row < N) ? ld2(A + (long long)row * lda + m + dc) : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int k = 0; k < 4 + kBG - 1; ++k)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int gg = k - r;
+              if (gg >= 0 && gg < kBG) cmac_conj(acc[r][gg], a[r], bv[k]);
+            }
+        }
+        float v[2 * 4 * kBG];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int k = 0; k < kBG; ++k) {
+            v[2 * (r * kBG + k)] = acc[r][k].x;
+            v[2 * (r * kBG + k) + 1] = acc[r][k].y;
+          }
+        warp_transpose_reduce<2 * 4 * kBG>(v, lane);  // lane holds complex index lane
+        const int r = lane / kBG, k = lane % kBG;
+        if (r < nrows && k < cnt) S.sin[d0 + k - dr_lo][side * (P - 1) + fr0 + r] = make_float2(v[0], v[1]);
+      }
+      __syncthreads();
+      // ---- C: CV per combination, RV per (combination, fringe row) ---------
+      const int nC = nD * (1 + NFR);
+      for (int t = warp; t < nC; t += kBWarps) {
+        const int dl = t % nD, kind = t / nD;  // kind 0: CV, kind 1+fr: RV of fringe row fr
+        const int dr = dl + dr_lo, J = Q - dc;
+        if (kind == 0) {
+          Neu<float> cr, ci;
+          for (int k = lane; k < n_cb * RS; k += 32) {
+            const float2 x = S.core[dl][k / RS][k % RS];
+            cr.add(x.x);
+            ci.add(x.y);
+          }
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) {
+            const float s1 = __shfl_xor_sync(0xffffffffu, cr.s, o), c1 = __shfl_xor_sync(0xffffffffu, cr.c, o);
+            const float s2 = __shfl_xor_sync(0xffffffffu, ci.s, o), c2 = __shfl_xor_sync(0xffffffffu, ci.c, o);
+            cr.merge(s1, c1);
+            ci.merge(s2, c2);
+          }
+          float lr = 0.f, li = 0.f, rr = 0.f, ri = 0.f;
+          if (lane < Q - 1) {
+            for (int rs = 0; rs < RS; ++rs) {
+              lr += S.cs[dl][lane][rs].x;
+              li += S.cs[dl][lane][rs].y;
+              rr += S.cs[dl][Q - 1 + lane][rs].x;
+              ri += S.cs[dl][Q - 1 + lane][rs].y;
+            }
+          }
+          // suffix sums over the left fringe columns, prefix over the right
+          float lsr = lr, lsi = li, rpr = rr, rpi = ri;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float a1 = __shfl_down_sync(0xffffffffu, lsr, o), a2 = __shfl_down_sync(0xffffffffu, lsi, o);
+            const float b1 = __shfl_up_sync(0xffffffffu, rpr, o), b2 = __shfl_up_sync(0xffffffffu, rpi, o);
+            if (lane + o < 32) { lsr += a1; lsi += a2; }
+            if (lane >= o) { rpr += b1; rpi += b2; }
+          }
+          rpr = __shfl_up_sync(0xffffffffu, rpr, 1);
+          rpi = __shfl_up_sync(0xffffffffu, rpi, 1);
+          if (lane == 0) rpr = rpi = 0.f;
+          if (lane < J) {
+            Neu<float> vr = cr, vi = ci;
+            vr.add(lane < Q - 1 ? lsr : 0.f);
+            vi.add(lane < Q - 1 ? lsi : 0.f);
+            vr.add(rpr);
+            vi.add(rpi);
+            S.cv[dl][lane] = make_float2(vr.value(), vi.value());
+          }
+        } else {
+          const int fr = kind - 1;
+          const int n = fr < P - 1 ? fr : (N - P + 1) + (fr - (P - 1));
+          const bool rowok = n + dr >= 0 && n + dr < N;
+          float2 lft = make_float2(0.f, 0.f), rgt = make_float2(0.f, 0.f);
+          if (rowok && lane < Q - 1) {
+            const float2 *An = A + (long long)n * lda;
+            const float2 *Ab = A + (long long)(n + dr) * lda + dc;
+            cmac_conj(lft, ld2(An + lane), ld2(Ab + lane));
+            if (W + lane + dc < M) cmac_conj(rgt, ld2(An + W + lane), ld2(Ab + W + lane));
+          }
+          float lsr = lft.x, lsi = lft.y, rpr = rgt.x, rpi = rgt.y;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float a1 = __shfl_down_sync(0xffffffffu, lsr, o), a2 = __shfl_down_sync(0xffffffffu, lsi, o);
+            const float b1 = __shfl_up_sync(0xffffffffu, rpr, o), b2 = __shfl_up_sync(0xffffffffu, rpi, o);
+            if (lane + o < 32) { lsr += a1; lsi += a2; }
+            if (lane >= o) { rpr += b1; rpi += b2; }
+          }
+          rpr = __shfl_up_sync(0xffffffffu, rpr, 1);
+          rpi = __shfl_up_sync(0xffffffffu, rpi, 1);
+          if (lane == 0) rpr = rpi = 0.f;
+          const float2 si = rowok ? S.sin[dl][fr] : make_float2(0.f, 0.f);
+          if (lane < J)
+            S.rv[dl][lane][fr] = make_float2(si.x + (lane < Q - 1 ? lsr : 0.f) + rpr,
+                                             si.y + (lane < Q - 1 ? lsi : 0.f) + rpi);
+        }
+      }
+      __syncthreads();
+      // ---- D: seed, walk, write -------------------------------------------
+      const int J = Q - dc;
+      for (int t = threadIdx.x; t < nD * J; t += blockDim.x) {
+        const int dl = t % nD, j = t / nD;
+        const int dr = dl + dr_lo;
+        const int adr = dr < 0 ? -dr : dr;
+        const int i0 = dr < 0 ? -dr : 0, I = P - adr;
+        Neu<float> orr, oii;
+        orr.add(S.cv[dl][j].x);
+        oii.add(S.cv[dl][j].y);
+        for (int n = i0; n <= P - 2; ++n) {
+          orr.add(S.rv[dl][j][n].x);
+          oii.add(S.rv[dl][j][n].y);
+        }
+        for (int k = 0; k < i0; ++k) {
+          orr.add(S.rv[dl][j][P - 1 + k].x);
+          oii.add(S.rv[dl][j][P - 1 + k].y);
+        }
+        for (int i = i0; i < i0 + I; ++i) {
+          float re = orr.value(), im = oii.value();
+          if (mean) {
+            if (K <= (1LL << 24)) {  // K exact in FP32: one IEEE division
+              re = re / (float)K;
+              im = im / (float)K;
+            } else {
+              re = (float)((double)re / (double)K);
+              im = (float)((double)im / (double)K);
+            }
+          }
+          if (dr == 0 && dc == 0) im = 0.f;
+          const long long a = i + (long long)P * j, b = (i + dr) + (long long)P * (j + dc);
+          d.R[a * DD + b] = make_float2(re, im);
+          if (a != b) d.R[b * DD + a] = make_float2(re, -im);
+          if (i + 1 < i0 + I) {  // walk: row i leaves the box, row i+N-P+1 enters
+            orr.add(-S.rv[dl][j][i].x);
+            oii.add(-S.rv[dl][j][i].y);
+            orr.add(S.rv[dl][j][P - 1 + i].x);
+            oii.add(S.rv[dl][j][P - 1 + i].y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace cov
+
+// ---------------------------------------------------------------------------
+// Host side: plan (validation + LPT schedule), upload, launch.
+// ---------------------------------------------------------------------------
+struct cov_batched_plan {
+  std::vector<cov::BDesc> descs;
+  std::vector<int> order;      // matrix indices, CTA by CTA
+  std::vector<int> cta_begin;  // grid + 1 offsets into order
+  int grid;
+  int mean;
+  size_t off_desc, off_order, off_begin, total;
+};
+
+namespace {
+
+bool batched_shape_ok(const cov_desc &d) {
+  return d.A && d.R && d.N >= 1 && d.M >= 1 && d.P >= 1 && d.Q >= 1 && d.P <= cov::kBMaxPQ &&
+         d.Q <= cov::kBMaxPQ && d.N >= 2 * d.P - 1 && d.M >= 2 * d.Q - 1 && d.M <= cov::kBMaxM &&
+         d.lda >= d.M && (((uintptr_t)d.A) & 7) == 0 && (((uintptr_t)d.R) & 7) == 0;
+}
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype, cov_algo algo,
+                                   cov_norm norm, cov_batched_plan **plan) {
+  if (!descs || count < 1 || !plan || (norm != COV_MEAN && norm != COV_SUM)) return COV_EINVAL;
+  if (dtype != COV_C64 || (algo != COV_AUTO && algo != COV_RECURRENCE)) return COV_EUNSUPPORTED;
+  for (int i = 0; i < count; ++i)
+    if (!batched_shape_ok(descs[i])) return COV_EINVAL;
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 148;  // no device visible: plan for a typical SM count
+  }
+  cov_batched_plan *pl = new cov_batched_plan();
+  pl->mean = norm == COV_MEAN ? 1 : 0;
+  pl->descs.resize(count);
+  std::vector<std::pair<long long, int>> cost(count);
+  for (int i = 0; i < count; ++i) {
+    const cov_desc &d = descs[i];
+    pl->descs[i] = {(const float2 *)d.A, (float2 *)d.R, d.lda, d.N, d.M, d.P, d.Q};
+    const long long um = cov::distinct_products(d.N, d.M, d.P, d.Q);
+    const long long nuc = cov::n_unique_combinations(d.P, d.Q);
+    cost[i] = {um + 2000LL * nuc + 20000, i};
+  }
+  const int grid = std::min(sms, count);
+  // longest processing time first: largest matrix to the least-loaded CTA
+  std::sort(cost.begin(), cost.end(), [](const std::pair<long long, int> &a,
+                                         const std::pair<long long, int> &b) {
+    return a.first > b.first || (a.first == b.first && a.second < b.second);
+  });
+  std::priority_queue<std::pair<long long, int>, std::vector<std::pair<long long, int>>,
+                      std::greater<std::pair<long long, int>>> load;
+  for (int c = 0; c < grid; ++c) load.push({0, c});
+  std::vector<std::vector<int>> per(grid);
+  for (const auto &ci : cost) {
+    auto top = load.top();
+    load.pop();
+    per[top.second].push_back(ci.second);
+    load.push({top.first + ci.first, top.second});
+  }
+  pl->grid = grid;
+  pl->cta_begin.assign(grid + 1, 0);
+  for (int c = 0; c < grid; ++c) {
+    pl->cta_begin[c + 1] = pl->cta_begin[c] + (int)per[c].size();
+    for (int i : per[c]) pl->order.push_back(i);
+  }
+  size_t off = cov::kWsHeader;
+  pl->off_desc = off;
+  off = al256(off + sizeof(cov::BDesc) * count);
+  pl->off_order = off;
+  off = al256(off + sizeof(int) * count);
+  pl->off_begin = off;
+  off = al256(off + sizeof(int) * (grid + 1));
+  pl->total = off;
+  *plan = pl;
+  return COV_OK;
+}
+
+cov_status cov_batched_workspace_size(const cov_batched_plan *plan, size_t *bytes) {
+  if (!plan || !bytes) return COV_EINVAL;
+  *bytes = plan->total;
+  return COV_OK;
+}
+
+cov_status cov_batched_upload(const cov_batched_plan *plan, void *workspace, size_t ws_bytes,
+                              cov_stream_t stream) {
+  if (!plan || !workspace) return COV_EINVAL;
+  if (ws_bytes < plan->total || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char *w = (char *)workspace;
+  if (cudaMemcpyAsync(w + plan->off_desc, plan->descs.data(), sizeof(cov::BDesc) * plan->descs.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(w + plan->off_order, plan->order.data(), sizeof(int) * plan->order.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(w + plan->off_begin, plan->cta_begin.data(), sizeof(int) * plan->cta_begin.size(),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return COV_ECUDA;
+  // pageable host memory: make sure the copies have read it before returning
+  if (cudaStreamSynchronize(s) != cudaSuccess) return COV_ECUDA;
+  return COV_OK;
+}
+
+cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, size_t ws_bytes,
+                                cov_stream_t stream) {
+  if (!plan || !workspace) return COV_EINVAL;
+  if (ws_bytes < plan->total || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  char *w = (char *)workspace;
+  const size_t smem = sizeof(cov::BSmem);
+  static bool attr_done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return COV_ECUDA;
+  if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+    if (cudaFuncSetAttribute(cov::k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return COV_ECUDA;
+    if (dev >= 0 && dev < 64) attr_done[dev] = true;
+  }
+  if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  cov::k_batched<<<plan->grid, cov::kBWarps * 32, smem, s>>>(
+      (const cov::BDesc *)(w + plan->off_desc), (const int *)(w + plan->off_order),
+      (const int *)(w + plan->off_begin), plan->mean);
+  return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
+}
+
+void cov_batched_plan_destroy(cov_batched_plan *plan) { delete plan; }
+
+}  // extern "C"

@@ -94,3 +94,28 @@ def test_argument_checks_fail_before_cuda():
     info = cov.PlanInfo()
     assert lib.cov_plan_info(0, 5, 1, 1, ctypes.byref(info)) == 1
     assert lib.cov_plan_info(5, 5, 1, 1, None) == 1
+
+
+def test_batched_plan_validation_host_only():
+    lib = cov.load()
+    fake = 0x1000
+
+    def plan(shapes):
+        arr = (cov.CovDesc * len(shapes))()
+        for k, (N, M, P, Q) in enumerate(shapes):
+            arr[k] = cov.CovDesc(fake, fake, M, N, M, P, Q)
+        ptr = ctypes.c_void_p()
+        code = lib.cov_batched_plan_create(arr, len(shapes), 0, 0, 0, ctypes.byref(ptr))
+        return code, ptr
+
+    code, ptr = plan([(64, 64, 8, 8), (33, 40, 16, 2), (200, 512, 3, 16)])
+    assert code == 0
+    n = ctypes.c_size_t(0)
+    assert lib.cov_batched_workspace_size(ptr, ctypes.byref(n)) == 0 and n.value > 256
+    lib.cov_batched_plan_destroy(ptr)
+    for bad in ([(64, 64, 17, 8)], [(30, 64, 16, 2)], [(64, 513, 2, 2)], [(8, 8, 0, 1)]):
+        assert plan(bad)[0] == 1, bad
+    arr = (cov.CovDesc * 1)(cov.CovDesc(fake, fake, 8, 8, 8, 2, 2))
+    ptr = ctypes.c_void_p()
+    assert lib.cov_batched_plan_create(arr, 1, 1, 0, 0, ctypes.byref(ptr)) == 5  # c128
+    assert lib.cov_batched_plan_create(arr, 1, 0, 2, 0, ctypes.byref(ptr)) == 5  # gemm algo

@@ -1,0 +1,91 @@
+"""Parity of the batched persistent launch (many uneven matrices, one kernel)
+with the CPU oracle, through the C ABI; and its capture in a CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+import cov_workloads as wl
+import paper_1303_2285_gb300 as cov
+
+pytestmark = pytest.mark.gpu
+
+from gpu_util import oracle_R, rel_fro  # noqa: E402
+
+F32_TOL = 1e-5
+
+
+def random_shapes(count, seed, nm=(8, 70), pq_max=16):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        N, M = (int(x) for x in rng.integers(nm[0], nm[1] + 1, 2))
+        P = int(rng.integers(1, min(pq_max, (N + 1) // 2) + 1))
+        Q = int(rng.integers(1, min(pq_max, (M + 1) // 2) + 1))
+        out.append((N, M, P, Q))
+    return out
+
+
+def make_batch(shapes, kind, seed):
+    items, host = [], []
+    for k, (N, M, P, Q) in enumerate(shapes):
+        if kind == "int":
+            A = wl.integer_valued((N, M), seed + k, dtype="c64")
+        else:
+            A = wl.complex_normal((N, M), seed + k, dtype="c64")
+        At = torch.from_numpy(A).cuda()
+        Rt = torch.full((P * Q, P * Q), complex(np.nan, np.nan), dtype=torch.complex64, device="cuda")
+        items.append((At, Rt, P, Q))
+        host.append(A)
+    return items, host
+
+
+def run_plan(items, norm="mean"):
+    plan = cov.BatchedPlan(items, norm=norm)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    plan.run(ws)
+    torch.cuda.synchronize()
+    cov.check_device_status(ws)
+    return plan, ws
+
+
+def test_batched_gaussian(oracle_mod):
+    shapes = random_shapes(40, 1) + [(256, 256, 16, 16), (31, 200, 16, 2), (200, 33, 3, 16),
+                                     (32, 32, 16, 16), (5, 9, 1, 1)]
+    items, host = make_batch(shapes, "cn", 100)
+    run_plan(items)
+    for (At, Rt, P, Q), A in zip(items, host):
+        got = Rt.cpu().numpy()
+        want = oracle_R(oracle_mod, A, P, Q)
+        assert rel_fro(got, want) < F32_TOL, (A.shape, P, Q)
+        assert np.array_equal(got, got.conj().T)
+
+
+def test_batched_integer_exact(oracle_mod):
+    shapes = random_shapes(25, 2, nm=(8, 60))
+    items, host = make_batch(shapes, "int", 300)
+    run_plan(items, norm="sum")
+    for (At, Rt, P, Q), A in zip(items, host):
+        N, M = A.shape
+        S = oracle_R(oracle_mod, A, P, Q, mean=False)
+        assert np.array_equal(Rt.cpu().numpy(), S.astype(np.complex64)), (N, M, P, Q)
+
+
+def test_batched_graph_capture(oracle_mod):
+    shapes = random_shapes(16, 3)
+    items, host = make_batch(shapes, "cn", 500)
+    plan = cov.BatchedPlan(items)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(ws, stream=s)
+    for _ in range(2):
+        for _, Rt, _, _ in items:
+            Rt.fill_(complex(np.nan, np.nan))
+        g.replay()
+        torch.cuda.synchronize()
+        for (At, Rt, P, Q), A in zip(items, host):
+            assert rel_fro(Rt.cpu().numpy(), oracle_R(oracle_mod, A, P, Q)) < F32_TOL
