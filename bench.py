@@ -460,6 +460,8 @@ def bench_ours(args, rank, world, local):
         line["rows"] = extras(args, cov, torch, np, wl, mk_events, stream)
         line["rows"]["batched_4096_uneven_f32"] = bench_batched(cov, torch, np, wl, mk_events, stream,
                                                                 fp32_peak)
+        line["rows"]["diff_b64_256x256_w12_f32"] = bench_adjoint(cov, torch, np, wl, mk_events, stream,
+                                                                 fp32_peak)
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()
@@ -508,6 +510,53 @@ def bench_batched(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
             "fp32_fma_frac": 8.0 * um / (ms * 1e-3) / fp32_peak,
             "input_bytes": sum(N * M * 8 for N, M, _, _ in shapes),
             "err_vs_fp64_direct_rel_fro_max_of_8": max(errs), "graph_captured": True}
+
+
+def bench_adjoint(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
+    """Differentiation workload: batch of 64 A (256 x 256, window 12 x 12);
+    forward through the batched launch, adjoint dL/dA per member for
+    L = ||R - R_target||_F^2 (G = 2 (R - R_target) formed once, untimed)."""
+    w = wl.WORKLOADS["diff_b64_256x256_w12_f32"]
+    P, Q, N, M, B = w.P, w.Q, w.N, w.M, w.batch
+    As = [torch.from_numpy(wl.complex_normal((N, M), w.seed + k, "c64")).cuda() for k in range(B)]
+    Rs = [torch.empty((P * Q, P * Q), dtype=torch.complex64, device="cuda") for _ in range(B)]
+    T = cov.estimate(torch.from_numpy(wl.complex_normal((N, M), 5000, "c64")).cuda(), P, Q)
+    plan = cov.BatchedPlan([(A, R, P, Q) for A, R in zip(As, Rs)])
+    wsf = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.upload(wsf)
+    plan.run(wsf)
+    torch.cuda.synchronize()
+    Gs = [(2.0 * (R - T)).contiguous() for R in Rs]
+    wsb = torch.empty(cov.backward_workspace_size(N, M, P, Q), dtype=torch.uint8, device="cuda")
+    dAs = [torch.empty_like(A) for A in As]
+    lib = cov.load()
+    sp = stream.cuda_stream
+
+    def backward_all():
+        for A, G, dA in zip(As, Gs, dAs):
+            lib.cov_estimate_backward(A.data_ptr(), G.data_ptr(), 0, N, M, P, Q, 0, dA.data_ptr(),
+                                      wsb.data_ptr(), wsb.numel(), sp)
+
+    backward_all()
+    torch.cuda.synchronize()
+    n = 3
+    ev = mk_events(3 * n)
+    for k in range(n):
+        ev[3 * k].record(stream)
+        plan.run(wsf)
+        ev[3 * k + 1].record(stream)
+        backward_all()
+        ev[3 * k + 2].record(stream)
+    torch.cuda.synchronize()
+    fwd = sum(ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(n)) / n
+    bwd = sum(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(n)) / n
+    D = P * Q
+    KW = (N - P + 1) * (M - Q + 1)
+    hx_flops = 8.0 * D * D * KW * B  # complex MACs of Y = H X
+    return {"batch": B, "forward_ms": fwd, "backward_ms": bwd, "forward_plus_backward_ms": fwd + bwd,
+            "backward_hx_tflops": hx_flops / (bwd * 1e-3) / 1e12,
+            "backward_fp32_fma_frac": hx_flops / (bwd * 1e-3) / fp32_peak,
+            "workspace_bytes_backward": wsb.numel()}
 
 
 def extras(args, cov, torch, np, wl, mk_events, stream) -> dict:

@@ -170,6 +170,67 @@ def estimate(A, P: int, Q: int, algo: str = "auto", norm: str = "mean", workspac
     return estimate_into(A, R, P, Q, algo, norm, workspace, stream)
 
 
+def backward_workspace_size(N: int, M: int, P: int, Q: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().cov_backward_workspace_size(DTYPES["c64"], N, M, P, Q, ctypes.byref(out)),
+           "cov_backward_workspace_size")
+    return int(out.value)
+
+
+def estimate_backward(A, G, P: int, Q: int, norm: str = "mean", workspace=None, stream=None):
+    """dL/dA for G = dL/dR (complex64 CUDA tensors; dL/dRe + i dL/dIm convention)."""
+    torch = _torch()
+    if not (A.is_cuda and G.is_cuda) or A.dtype != torch.complex64 or G.dtype != torch.complex64:
+        raise ValueError("A and G must be complex64 CUDA tensors")
+    A = A.contiguous()
+    G = G.contiguous()
+    N, M = A.shape
+    if tuple(G.shape) != (P * Q, P * Q):
+        raise ValueError("G must be PQ x PQ")
+    need = backward_workspace_size(N, M, P, Q)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=A.device)
+    dA = torch.empty_like(A)
+    _check(load().cov_estimate_backward(A.data_ptr(), G.data_ptr(), DTYPES["c64"], N, M, P, Q,
+                                        NORMS[norm], dA.data_ptr(), workspace.data_ptr(),
+                                        workspace.numel(), _stream_ptr(stream)),
+           "cov_estimate_backward")
+    return dA
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class CovarianceEstimate(torch.autograd.Function):
+        """R = estimate(A) with the library's adjoint kernels as backward."""
+
+        @staticmethod
+        def forward(ctx, A, P, Q, norm):
+            ctx.save_for_backward(A)
+            ctx.P, ctx.Q, ctx.norm = P, Q, norm
+            return estimate(A.detach().contiguous(), P, Q, algo="auto", norm=norm)
+
+        @staticmethod
+        def backward(ctx, G):
+            (A,) = ctx.saved_tensors
+            dA = estimate_backward(A.detach(), G.contiguous(), ctx.P, ctx.Q, ctx.norm)
+            return dA, None, None, None
+
+    return CovarianceEstimate
+
+
+_autograd_fn = None
+
+
+def covariance(A, P: int, Q: int, norm: str = "mean"):
+    """Differentiable estimate: R = covariance(A, P, Q); backward runs the
+    library's adjoint ((G + G^H) X, gather col2im). complex64 CUDA tensors."""
+    global _autograd_fn
+    if _autograd_fn is None:
+        _autograd_fn = _make_autograd()
+    return _autograd_fn.apply(A, P, Q, norm)
+
+
 class BatchedPlan:
     """Many matrices of uneven shapes in one persistent launch (cov_batched_*).
 

@@ -1,0 +1,186 @@
+// Adjoint of the estimate (not in the paper; the derivative of Eq. 2.2).
+//
+// With G = dL/dR and dA in the convention dL/dRe + i dL/dIm:
+//   dL/dx_w = H x_w,  H = (G + G^H) / K   (G + G^H for the plain sum),
+//   dA[n][m] = sum over windows w = (p, q) that hold (n, m) of (H x_w)[a],
+//   a = (n - p) + P (m - q).
+// Kernel 1 forms Y = H X for tiles of windows: X (PQ x K, column w = the
+// window's column stack) is never stored; each CTA gathers its windows' values
+// from a staged patch of A. Kernel 2 is the col2im in gather form: one thread
+// per element of dA sums the entries of Y that belong to it, so every element
+// of dA has one writer and no atomics are needed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cov.h"
+#include "cov_device.cuh"
+#include "cov_internal.h"
+#include "plan.h"
+
+namespace cov {
+
+constexpr int kAdjTA = 48;   // rows a of Y per CTA
+constexpr int kAdjTW = 128;  // windows per CTA (one window row p, consecutive q)
+constexpr int kAdjPQMax = 1024;
+
+struct AdjParams {
+  const float2 *A;
+  const float2 *G;
+  float2 *Y;   // [PQ][KW], window index w = p * W + q
+  float2 *dA;  // N x M, leading dimension M
+  long long lda;
+  int N, M, P, Q, W, Hn;  // W = M-Q+1 window columns, Hn = N-P+1 window rows
+  long long KW;           // number of windows
+  int mean;
+};
+
+// Y[a][w] for a in [a0, a0+48), w = p*W + q, q in [q0, q0+128).
+// Thread (ta, tw) of a 16 x 16 grid: a = a0 + ta + 16k (k < 3),
+// q = q0 + tw + 16l (l < 8): 24 complex accumulators.
+__global__ void __launch_bounds__(256) k_adj_hx(const AdjParams p) {
+  extern __shared__ __align__(16) unsigned char smem_adj[];
+  const int D = p.P * p.Q;
+  float2 *Hs = (float2 *)smem_adj;                // [48][D]
+  float2 *As = Hs + kAdjTA * D;                   // [P][128 + Q - 1]
+  const int AP = kAdjTW + p.Q - 1;
+  const int nqc = (p.W + kAdjTW - 1) / kAdjTW;
+  int bid = blockIdx.x;
+  const int qc = bid % nqc;
+  bid /= nqc;
+  const int pw = bid % p.Hn;
+  const int a0 = (bid / p.Hn) * kAdjTA;
+  const int q0 = qc * kAdjTW;
+  // H rows a0..a0+47: H[a][b] = (G[a][b] + conj(G[b][a])) / K
+  for (int e = threadIdx.x; e < kAdjTA * D; e += blockDim.x) {
+    const int ar = e / D, b = e - ar * D, a = a0 + ar;
+    float2 h = make_float2(0.f, 0.f);
+    if (a < D) {
+      const float2 g1 = p.G[(long long)a * D + b], g2 = p.G[(long long)b * D + a];
+      h.x = g1.x + g2.x;
+      h.y = g1.y - g2.y;
+      if (p.mean) {
+        h.x = h.x / (float)p.KW;
+        h.y = h.y / (float)p.KW;
+      }
+    }
+    Hs[e] = h;
+  }
+  // patch of A: rows pw..pw+P-1, columns q0..q0+127+Q-1 (zero outside A)
+  for (int e = threadIdx.x; e < p.P * AP; e += blockDim.x) {
+    const int r = e / AP, c = e - r * AP;
+    const int gc = q0 + c;
+    As[e] = gc < p.M ? p.A[(long long)(pw + r) * p.lda + gc] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int ta = threadIdx.x >> 4, tw = threadIdx.x & 15;
+  float2 acc[3][8];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int l = 0; l < 8; ++l) acc[k][l] = make_float2(0.f, 0.f);
+  for (int jb = 0, b = 0; jb < p.Q; ++jb)
+  for (int ib = 0; ib < p.P; ++ib, ++b) {
+    float2 h[3], x[8];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) h[k] = Hs[(ta + 16 * k) * D + b];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) x[l] = As[ib * AP + tw + 16 * l + jb];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {  // acc += h * x
+        acc[k][l].x = fma_rn(h[k].x, x[l].x, acc[k][l].x);
+        acc[k][l].x = fma_rn(-h[k].y, x[l].y, acc[k][l].x);
+        acc[k][l].y = fma_rn(h[k].x, x[l].y, acc[k][l].y);
+        acc[k][l].y = fma_rn(h[k].y, x[l].x, acc[k][l].y);
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int a = a0 + ta + 16 * k;
+    if (a >= D) continue;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int q = q0 + tw + 16 * l;
+      if (q < p.W) p.Y[(long long)a * p.KW + (long long)pw * p.W + q] = acc[k][l];
+    }
+  }
+}
+
+// dA[n][m] = sum over (i, j) with window (n-i, m-j) valid of Y[i + P j][(n-i) W + (m-j)].
+__global__ void __launch_bounds__(256) k_adj_col2im(const AdjParams p) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)p.N * p.M) return;
+  const int n = (int)(idx / p.M), m = (int)(idx - (long long)n * p.M);
+  const int i_lo = n - (p.Hn - 1) > 0 ? n - (p.Hn - 1) : 0, i_hi = n < p.P - 1 ? n : p.P - 1;
+  const int j_lo = m - (p.W - 1) > 0 ? m - (p.W - 1) : 0, j_hi = m < p.Q - 1 ? m : p.Q - 1;
+  float sr = 0.f, si = 0.f;
+  for (int j = j_lo; j <= j_hi; ++j)
+    for (int i = i_lo; i <= i_hi; ++i) {
+      const float2 y = p.Y[(long long)(i + p.P * j) * p.KW + (long long)(n - i) * p.W + (m - j)];
+      sr += y.x;
+      si += y.y;
+    }
+  p.dA[idx] = make_float2(sr, si);
+}
+
+}  // namespace cov
+
+extern "C" {
+
+cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                                       size_t *bytes) {
+  if (!bytes || N < 1 || M < 1 || P < 1 || Q < 1 || P > N || Q > M) return COV_EINVAL;
+  if (dtype != COV_C64 || (long long)P * Q > cov::kAdjPQMax) return COV_EUNSUPPORTED;
+  const long long KW = (N - P + 1) * (M - Q + 1);
+  *bytes = cov::kWsHeader + (((size_t)P * Q * KW * 8 + 255) & ~(size_t)255);
+  return COV_OK;
+}
+
+cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype, int64_t N, int64_t M,
+                                 int P, int Q, cov_norm norm, void *dA, void *workspace,
+                                 size_t ws_bytes, cov_stream_t stream) {
+  if (!A || !G || !dA || N < 1 || M < 1 || P < 1 || Q < 1 || P > N || Q > M ||
+      (norm != COV_MEAN && norm != COV_SUM) || N >= (1LL << 30) || M >= (1LL << 30))
+    return COV_EINVAL;
+  if (dtype != COV_C64 || (long long)P * Q > cov::kAdjPQMax) return COV_EUNSUPPORTED;
+  if ((((uintptr_t)A) & 7) || (((uintptr_t)G) & 7) || (((uintptr_t)dA) & 7)) return COV_EINVAL;
+  size_t need = 0;
+  cov_backward_workspace_size(dtype, N, M, P, Q, &need);
+  if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  cov::AdjParams p;
+  p.A = (const float2 *)A;
+  p.G = (const float2 *)G;
+  p.Y = (float2 *)((char *)workspace + cov::kWsHeader);
+  p.dA = (float2 *)dA;
+  p.lda = M;
+  p.N = (int)N;
+  p.M = (int)M;
+  p.P = P;
+  p.Q = Q;
+  p.W = (int)(M - Q + 1);
+  p.Hn = (int)(N - P + 1);
+  p.KW = (long long)p.W * p.Hn;
+  p.mean = norm == COV_MEAN ? 1 : 0;
+  const int D = P * Q;
+  const size_t smem = ((size_t)cov::kAdjTA * D + (size_t)P * (cov::kAdjTW + Q - 1)) * sizeof(float2);
+  if (smem > 227 * 1024) return COV_EUNSUPPORTED;
+  static size_t attr_done = 0;
+  if (smem > 48 * 1024 && smem > attr_done) {
+    if (cudaFuncSetAttribute(cov::k_adj_hx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return COV_ECUDA;
+    attr_done = smem;
+  }
+  if (cudaMemsetAsync(workspace, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  const long long nqc = (p.W + cov::kAdjTW - 1) / cov::kAdjTW;
+  const long long grid1 = nqc * p.Hn * ((D + cov::kAdjTA - 1) / cov::kAdjTA);
+  cov::k_adj_hx<<<(unsigned)grid1, 256, smem, s>>>(p);
+  if (cudaGetLastError() != cudaSuccess) return COV_ECUDA;
+  const long long grid2 = (N * M + 255) / 256;
+  cov::k_adj_col2im<<<(unsigned)grid2, 256, 0, s>>>(p);
+  return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
+}
+
+}  // extern "C"

@@ -218,18 +218,4 @@ cov_status cov_check_device_status(void *workspace, cov_stream_t stream) {
   return COV_EDEVICE;
 }
 
-// ---- not yet available: backward -----------------------------------------
-cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
-                                       size_t *bytes) {
-  (void)dtype; (void)N; (void)M; (void)P; (void)Q; (void)bytes;
-  return COV_EUNSUPPORTED;
-}
-cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype, int64_t N,
-                                 int64_t M, int P, int Q, cov_norm norm, void *dA,
-                                 void *workspace, size_t ws_bytes, cov_stream_t stream) {
-  (void)A; (void)G; (void)dtype; (void)N; (void)M; (void)P; (void)Q; (void)norm; (void)dA;
-  (void)workspace; (void)ws_bytes; (void)stream;
-  return COV_EUNSUPPORTED;
-}
-
 }  // extern "C"

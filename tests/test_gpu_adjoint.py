@@ -1,0 +1,72 @@
+"""Parity of the adjoint kernels (dL/dA) with the CPU oracle's gradient and
+with FP64 finite differences of the oracle's loss, through the C ABI and the
+torch.autograd.Function wrapper."""
+import numpy as np
+import pytest
+import torch
+
+import cov_workloads as wl
+import paper_1303_2285_gb300 as cov
+
+pytestmark = pytest.mark.gpu
+
+from gpu_util import rel_fro  # noqa: E402
+
+F32_TOL = 1e-5
+
+
+@pytest.mark.parametrize("N,M,P,Q", [(20, 17, 4, 3), (16, 16, 4, 4), (37, 50, 7, 5),
+                                     (9, 9, 9, 9), (30, 12, 1, 1), (64, 70, 12, 12)])
+@pytest.mark.parametrize("norm", ["mean", "sum"])
+def test_backward_matches_oracle(oracle_mod, N, M, P, Q, norm):
+    A = wl.complex_normal((N, M), 11 + N, dtype="c64")
+    G = wl.complex_normal((P * Q, P * Q), 12 + M, dtype="c64")
+    dA = cov.estimate_backward(torch.from_numpy(A).cuda(), torch.from_numpy(G).cuda(), P, Q, norm=norm)
+    want = oracle_mod.cov_backward(A.astype(np.complex128), G.astype(np.complex128), P, Q,
+                                   mean=(norm == "mean"))
+    assert rel_fro(dA.cpu().numpy(), want) < F32_TOL
+
+
+def test_autograd_against_fd_fp64(oracle_mod):
+    # loss = ||R - T||_F^2 with T from a second seed; A 16x16, window 4x4
+    N = M = 16
+    P = Q = 4
+    A = wl.complex_normal((N, M), 4, dtype="c128")
+    T = oracle_mod.cov_window(wl.complex_normal((N, M), 5000, dtype="c128"), P, Q)
+    At = torch.tensor(A.astype(np.complex64), device="cuda", requires_grad=True)
+    Tt = torch.tensor(T.astype(np.complex64), device="cuda")
+    R = cov.covariance(At, P, Q)
+    loss = (R - Tt).abs().pow(2).sum()
+    loss.backward()
+    got = At.grad.cpu().numpy()
+
+    def L(X):
+        return float(np.sum(np.abs(oracle_mod.cov_window(X, P, Q) - T) ** 2))
+
+    h = 1e-6
+    fd = np.zeros((N, M), np.complex128)
+    for n in range(N):
+        for m in range(M):
+            for unit in (1.0, 1j):
+                E = np.zeros((N, M), np.complex128)
+                E[n, m] = unit * h
+                d = (L(A + E) - L(A - E)) / (2 * h)
+                fd[n, m] += d * (1.0 if unit == 1.0 else 1j)
+    assert rel_fro(got, fd) < 1e-5
+
+
+def test_autograd_matches_oracle_gradient_workload_shape(oracle_mod):
+    # one member of the differentiation workload: 256 x 256, window 12 x 12
+    N = M = 256
+    P = Q = 12
+    A = wl.complex_normal((N, M), 4, dtype="c64")
+    T = wl.complex_normal((N, M), 5000, dtype="c64")
+    At = torch.tensor(A, device="cuda", requires_grad=True)
+    with torch.no_grad():
+        Tt = cov.estimate(torch.from_numpy(T).cuda(), P, Q)
+    R = cov.covariance(At, P, Q)
+    loss = (R - Tt).abs().pow(2).sum()
+    loss.backward()
+    G = 2.0 * (R.detach() - Tt).cpu().numpy().astype(np.complex128)
+    want = oracle_mod.cov_backward(A.astype(np.complex128), G, P, Q)
+    assert rel_fro(At.grad.cpu().numpy(), want) < F32_TOL
