@@ -113,6 +113,10 @@ cov_status cov_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int 
     case COV_DIRECT:
       *bytes = kWsHeader;
       return COV_OK;
+    case COV_GEMM_TF32X3:
+      if (dtype != COV_C64 || !gemm_shape_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+      *bytes = gemm_workspace_size(N, M, P, Q);
+      return COV_OK;
     default:
       return COV_EUNSUPPORTED;
   }
@@ -169,6 +173,16 @@ cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M,
       d.mean = norm == COV_MEAN ? 1 : 0;
       if (launch_direct(d, dtype == COV_C128, s) != cudaSuccess) return COV_ECUDA;
       return COV_OK;
+    }
+    case COV_GEMM_TF32X3: {
+      if (dtype != COV_C64 || !gemm_shape_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+      const int sms = device_sms();
+      if (sms <= 0) return COV_ECUDA;
+      bool ws_ok = false;
+      if (launch_gemm_tf32x3(A, N, M, lda, P, Q, R, norm == COV_MEAN ? 1 : 0, workspace, ws_bytes,
+                             sms, s, &ws_ok) != cudaSuccess)
+        return COV_ECUDA;
+      return ws_ok ? COV_OK : COV_EWORKSPACE;
     }
     default:
       return COV_EUNSUPPORTED;

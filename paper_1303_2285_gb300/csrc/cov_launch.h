@@ -39,4 +39,11 @@ cudaError_t launch_reduce(const RecParams &p, bool fp64, cudaStream_t s, bool pd
 cudaError_t launch_walk(const RecParams &p, bool fp64, cudaStream_t s, bool pdl);
 cudaError_t launch_direct(const DirectParams &p, bool c128, cudaStream_t s);
 
+// Dense form on tcgen05 (gemm_tc.cu); complex64 input and output.
+bool gemm_shape_ok(long long N, long long M, int P, int Q);
+size_t gemm_workspace_size(long long N, long long M, int P, int Q);
+cudaError_t launch_gemm_tf32x3(const void *A, long long N, long long M, long long lda, int P, int Q,
+                               void *R, int mean, void *workspace, size_t ws_bytes, int sms,
+                               cudaStream_t s, bool *ws_ok);
+
 }  // namespace cov
