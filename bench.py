@@ -269,6 +269,20 @@ def bench_ours(args, rank, world, local):
     R = torch.empty((D, D), dtype=dt, device="cuda")
     info = cov.plan_info(w.N, w.M, w.P, w.Q)
     um = info["distinct_products"]
+    tune_ms, source = None, "defaults"
+    if args.tuning_file and os.path.exists(args.tuning_file):
+        cov.tuning_load(args.tuning_file)
+        source = "file"
+    elif args.autotune:
+        # the library's tuner times its candidate knobs on this input and
+        # caches the fastest; planning below picks them up (untimed)
+        _, tune_ms = cov.autotune(A, w.P, w.Q, reps=5)
+        tune_ms, source = round(tune_ms, 5), "autotune"
+        if args.tuning_file:
+            cov.tuning_save(args.tuning_file)
+    knobs, cached = cov.tuning_get(w.dtype, w.N, w.M, w.P, w.Q)
+    tuning = dict(knobs, source=source if cached else "defaults", tuned_ms_per_call=tune_ms)
+    torch.cuda.synchronize()
     ws = torch.empty(max(256, cov.workspace_size(w.dtype, w.N, w.M, w.P, w.Q, "recurrence")),
                      dtype=torch.uint8, device="cuda")
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -437,7 +451,7 @@ def bench_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
-        "data": "synthetic", "config": _config(w),
+        "data": "synthetic", "config": dict(_config(w), tuning=tuning),
         "r_elements_per_s": D * D * K * world / total_s,
         "vs_plain_fp64_gpu": {"speedup": direct_ms / ms_per_step, "fp64_direct_ms": direct_ms},
         "err_vs_fp64": {"rel_fro": err_fro, "max_abs_rel_to_max": err_max,
@@ -651,6 +665,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extras", action="store_true", default=True)
     ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True)
+    ap.add_argument("--tuning-file", default=None,
+                    help="load the knobs from this file if it exists, else autotune and save them")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

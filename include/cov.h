@@ -31,8 +31,8 @@
  * - No entry point falls back to a CPU implementation: every result is
  *   computed by this library's CUDA kernels.
  * - Entry points that take (workspace, ws_bytes) never allocate device
- *   memory. cov_estimate and cov_estimate_backward_alloc allocate a
- *   stream-ordered workspace (cudaMallocAsync / cudaFreeAsync) on `stream`.
+ *   memory. cov_estimate allocates a stream-ordered workspace
+ *   (cudaMallocAsync / cudaFreeAsync) on `stream`.
  */
 #ifndef COV_H
 #define COV_H
@@ -170,6 +170,16 @@ cov_status cov_estimate_noalloc(const void *A, cov_dtype dtype, int64_t N, int64
  * COV_EDEVICE; COV_ECUDA if the copy itself fails. */
 cov_status cov_check_device_status(void *workspace, cov_stream_t stream);
 
+/* Failure-detection self-test (not in the paper). Launches one warp that
+ * waits, through the library's bounded mbarrier wait, on a barrier nothing
+ * completes; after limit_us microseconds (1 .. 1,000,000) the wait gives up,
+ * the kernel records COV_ETIMEOUT in the status word at the start of
+ * `workspace` (device, >= 4 bytes, 256-byte aligned) and returns normally,
+ * so cov_check_device_status then reports COV_ETIMEOUT and the context stays
+ * usable. COV_EINVAL for a limit out of range. */
+cov_status cov_selftest_timeout(void *workspace, size_t ws_bytes, uint32_t limit_us,
+                                cov_stream_t stream);
+
 /* Instrumentation (not in the paper). With events != NULL, following
  * cov_estimate_ex calls of COV_RECURRENCE record five events each on their
  * stream: before the first kernel and after each of the four kernels
@@ -180,6 +190,62 @@ cov_status cov_check_device_status(void *workspace, cov_stream_t stream);
  * events[5*(c mod n_events/5) ...]. NULL switches this off. Process-wide
  * host state; not thread safe. COV_EINVAL on a bad count or a null handle. */
 cov_status cov_set_stage_events(void *const *events, int n_events);
+
+/* ---------------------------------------------------------------------------
+ * Tuned knobs of COV_RECURRENCE (not in the paper, whose Section 5 fixes the
+ * work decomposition by hand). Three knobs change speed, never the set of
+ * products computed:
+ *   lag_group       lags (combinations) that share one pass over a tile:
+ *                   4, 8 or 16 (16 only for COV_C64);
+ *   rows_per_task   inner rows of one product task: a multiple of 8 in
+ *                   [8, 256] (clamped by the planner to what shared memory
+ *                   holds);
+ *   reseed_interval outputs walked from one direct seed along a diagonal,
+ *                   1..32 (1 = every output seeded directly).
+ * A process-wide host cache maps (dtype, N, M, P, Q, SM count of the current
+ * device) to knobs; planning (cov_workspace_size, cov_estimate_ex,
+ * cov_estimate, cov_estimate_noalloc) uses the cached knobs for that key, else
+ * the defaults. The workspace size can change with the knobs: query
+ * cov_workspace_size again after changing the cache. Cache calls are
+ * thread safe; host only; no device work except in cov_autotune.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t lag_group;
+  int32_t rows_per_task;
+  int32_t reseed_interval;
+} cov_tuning_t;
+
+/* Knobs planning would use for this shape now (*out); *cached (optional)
+ * = 1 if they come from the cache. COV_EUNSUPPORTED for shapes
+ * COV_RECURRENCE does not take. */
+cov_status cov_tuning_get(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                          cov_tuning_t *out, int *cached);
+/* Stores knobs (HOST struct, copied) for this shape; t == NULL removes the
+ * entry. COV_EINVAL for knobs outside the ranges above. */
+cov_status cov_tuning_set(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                          const cov_tuning_t *t);
+void cov_tuning_clear(void);
+/* Writes the cache to a text file (one line per entry: dtype-bytes N M P Q
+ * SMs knobs) / merges such a file into it (*n_loaded = entries read).
+ * COV_EINVAL if the file cannot be written or read or has a malformed line. */
+cov_status cov_tuning_save(const char *path);
+cov_status cov_tuning_load(const char *path, int *n_loaded);
+/* Upper bound of the workspace any cov_autotune candidate for this shape
+ * needs; a smaller workspace makes cov_autotune skip the candidates that do
+ * not fit. */
+cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                                       size_t *bytes);
+/* Times COV_RECURRENCE candidates on the caller's data with CUDA events on
+ * `stream` (one warm-up and `reps` timed calls each, 1 <= reps <= 1000):
+ * first lag_group x rows_per_task, then reseed_interval at the best of
+ * those; stores the fastest in the cache and returns it in *best (optional)
+ * with its mean milliseconds per call in *best_ms (optional). Overwrites R
+ * (with the correct mean-normalised estimate) and the workspace; synchronises
+ * `stream`; not capturable. A candidate whose device status word reports a
+ * failure ends the search with that status. */
+cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, int64_t lda,
+                        int P, int Q, void *R, void *workspace, size_t ws_bytes, int reps,
+                        cov_stream_t stream, cov_tuning_t *best, float *best_ms);
 
 /* ---------------------------------------------------------------------------
  * Many input matrices of uneven N, M, P, Q in one launch sequence

@@ -20,7 +20,8 @@ from typing import Optional
 from . import _build
 
 __all__ = ["load", "estimate", "estimate_into", "workspace_size", "plan_info",
-           "check_device_status", "CovError", "ALGOS", "STATUS"]
+           "check_device_status", "CovError", "ALGOS", "STATUS", "autotune", "tuning_get",
+           "tuning_set", "tuning_clear", "tuning_save", "tuning_load"]
 
 ALGOS = {"auto": 0, "recurrence": 1, "gemm_tf32x3": 2, "gemm_bf16x3": 3, "direct": 4}
 NORMS = {"mean": 0, "sum": 1}
@@ -41,6 +42,16 @@ class PlanInfo(ctypes.Structure):
                 ("naive_macs", ctypes.c_int64), ("recurrence_ok", ctypes.c_int32),
                 ("n_groups", ctypes.c_int32), ("n_tasks", ctypes.c_int64),
                 ("products_inner", ctypes.c_int64), ("products_fringe", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    """Knobs of the combination path: lags per group, rows per product task,
+    walk re-seed interval (cov_tuning_t)."""
+    _fields_ = [("lag_group", ctypes.c_int32), ("rows_per_task", ctypes.c_int32),
+                ("reseed_interval", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class CovDesc(ctypes.Structure):
@@ -72,6 +83,16 @@ SIGNATURES = [
     ("cov_batched_plan_destroy", None, [_VP]),
     ("cov_backward_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
     ("cov_estimate_backward", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _VP, _VP, _SZ, _VP]),
+    ("cov_selftest_timeout", _I, [_VP, _SZ, ctypes.c_uint32, _VP]),
+    ("cov_tuning_get", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(Tuning),
+                            ctypes.POINTER(ctypes.c_int)]),
+    ("cov_tuning_set", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(Tuning)]),
+    ("cov_tuning_clear", None, []),
+    ("cov_tuning_save", _I, [ctypes.c_char_p]),
+    ("cov_tuning_load", _I, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
+    ("cov_autotune_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
+    ("cov_autotune", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _VP, _VP, _SZ, _I, _VP,
+                          ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_float)]),
 ]
 
 
@@ -279,6 +300,61 @@ def set_stage_events(events) -> None:
         return
     arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
     _check(lib.cov_set_stage_events(arr, len(events)), "cov_set_stage_events")
+
+
+def tuning_get(dtype: str, N: int, M: int, P: int, Q: int):
+    """(knobs planning uses now, whether they come from the tuning cache)."""
+    t, cached = Tuning(), ctypes.c_int(0)
+    _check(load().cov_tuning_get(DTYPES[dtype], N, M, P, Q, ctypes.byref(t), ctypes.byref(cached)),
+           "cov_tuning_get")
+    return t.as_dict(), bool(cached.value)
+
+
+def tuning_set(dtype: str, N: int, M: int, P: int, Q: int, knobs: Optional[dict]) -> None:
+    """Stores knobs for the shape in the tuning cache; None removes the entry."""
+    t = None if knobs is None else ctypes.byref(Tuning(**knobs))
+    _check(load().cov_tuning_set(DTYPES[dtype], N, M, P, Q, t), "cov_tuning_set")
+
+
+def tuning_clear() -> None:
+    load().cov_tuning_clear()
+
+
+def tuning_save(path: str) -> None:
+    _check(load().cov_tuning_save(os.fsencode(path)), "cov_tuning_save")
+
+
+def tuning_load(path: str) -> int:
+    n = ctypes.c_int(0)
+    _check(load().cov_tuning_load(os.fsencode(path), ctypes.byref(n)), "cov_tuning_load")
+    return int(n.value)
+
+
+def autotune(A, P: int, Q: int, reps: int = 5, stream=None):
+    """Times the combination path's candidate knobs on the device tensor A,
+    caches the fastest for A's shape and returns (knobs, ms per call)."""
+    torch = _torch()
+    if not A.is_cuda or A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a 2-D CUDA tensor with unit column stride")
+    dt = _dtype_of(A)
+    N, M = A.shape
+    need = ctypes.c_size_t(0)
+    _check(load().cov_autotune_workspace_size(DTYPES[dt], N, M, P, Q, ctypes.byref(need)),
+           "cov_autotune_workspace_size")
+    ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=A.device)
+    R = torch.empty((P * Q, P * Q), dtype=A.dtype, device=A.device)
+    best, ms = Tuning(), ctypes.c_float(0)
+    _check(load().cov_autotune(A.data_ptr(), DTYPES[dt], N, M, A.stride(0), P, Q, R.data_ptr(),
+                               ws.data_ptr(), ws.numel(), reps, _stream_ptr(stream),
+                               ctypes.byref(best), ctypes.byref(ms)), "cov_autotune")
+    return best.as_dict(), float(ms.value)
+
+
+def selftest_timeout(workspace, limit_us: int = 20000, stream=None) -> None:
+    """Queues the bounded-wait self-test kernel; its timeout is reported by the
+    next check_device_status on the same workspace."""
+    _check(load().cov_selftest_timeout(workspace.data_ptr(), workspace.numel(), limit_us,
+                                       _stream_ptr(stream)), "cov_selftest_timeout")
 
 
 def check_device_status(workspace, stream=None) -> None:

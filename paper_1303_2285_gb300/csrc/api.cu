@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <vector>
+
 #include "../../include/cov.h"
 #include "cov_internal.h"
 #include "cov_launch.h"
@@ -32,6 +34,31 @@ bool shape_ok(int64_t N, int64_t M, int P, int Q) {
 
 StageEvents g_stage_events = {nullptr, 0, 0, false};
 cudaEvent_t g_stage_store[5 * 4096];
+
+// Plans (cached tuning unless `tune` is given) and launches the combination
+// path on the caller's workspace.
+cov_status run_recurrence(const void *A, int elem, int64_t N, int64_t M, int64_t lda, int P, int Q,
+                          void *R, cov_norm norm, void *workspace, size_t ws_bytes, int sms,
+                          cudaStream_t s, const Tuning *tune, StageEvents *marks) {
+  RecParams p;
+  WsLayout ws;
+  plan_recurrence(N, M, lda, P, Q, elem, sms, p, ws, tune);
+  if (!workspace || ws_bytes < ws.total || ((uintptr_t)workspace & 255) != 0)
+    return COV_EWORKSPACE;
+  char *w = (char *)workspace;
+  p.A = A;
+  p.R = R;
+  p.mean = norm == COV_MEAN ? 1 : 0;
+  p.status = (unsigned *)w;
+  p.core_part = w + ws.core_off;
+  p.colsum_part = w + ws.colsum_off;
+  p.sin_part = w + ws.sin_off;
+  p.rowval = w + ws.rowval_off;
+  p.colval = w + ws.colval_off;
+  if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  if (launch_recurrence(p, elem == 16, sms, s, marks) != cudaSuccess) return COV_ECUDA;
+  return COV_OK;
+}
 
 cov_algo resolve_algo(cov_algo algo, int64_t N, int64_t M, int P, int Q) {
   if (algo != COV_AUTO) return algo;
@@ -70,7 +97,7 @@ cov_status cov_plan_info(int64_t N, int64_t M, int P, int Q, cov_plan_info_t *ou
   if (out->recurrence_ok) {
     RecParams p;
     WsLayout ws;
-    plan_recurrence(N, M, M, P, Q, 8, p, ws);
+    plan_recurrence(N, M, M, P, Q, 8, device_sms(), p, ws);
     out->n_groups = p.ngroups;
     out->n_tasks = p.n_tasks;
     // products of the inner-row kernel: inner rows x all columns, valid lags
@@ -106,7 +133,7 @@ cov_status cov_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int 
       if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
       RecParams p;
       WsLayout ws;
-      plan_recurrence(N, M, M, P, Q, dtype == COV_C128 ? 16 : 8, p, ws);
+      plan_recurrence(N, M, M, P, Q, dtype == COV_C128 ? 16 : 8, device_sms(), p, ws);
       *bytes = ws.total;
       return COV_OK;
     }
@@ -136,27 +163,11 @@ cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M,
   switch (algo) {
     case COV_RECURRENCE: {
       if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
-      RecParams p;
-      WsLayout ws;
-      plan_recurrence(N, M, lda, P, Q, elem, p, ws);
-      if (!workspace || ws_bytes < ws.total || ((uintptr_t)workspace & 255) != 0)
-        return COV_EWORKSPACE;
-      char *w = (char *)workspace;
-      p.A = A;
-      p.R = R;
-      p.mean = norm == COV_MEAN ? 1 : 0;
-      p.status = (unsigned *)w;
-      p.core_part = w + ws.core_off;
-      p.colsum_part = w + ws.colsum_off;
-      p.sin_part = w + ws.sin_off;
-      p.rowval = w + ws.rowval_off;
-      p.colval = w + ws.colval_off;
+      if (!workspace || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
       const int sms = device_sms();
       if (sms <= 0) return COV_ECUDA;
-      if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
-      if (launch_recurrence(p, dtype == COV_C128, sms, s, &g_stage_events) != cudaSuccess)
-        return COV_ECUDA;
-      return COV_OK;
+      return run_recurrence(A, elem, N, M, lda, P, Q, R, norm, workspace, ws_bytes, sms, s,
+                            nullptr, &g_stage_events);
     }
     case COV_DIRECT: {
       if (workspace && ((uintptr_t)workspace & 255) == 0 && ws_bytes >= 4)
@@ -230,6 +241,172 @@ cov_status cov_check_device_status(void *workspace, cov_stream_t stream) {
   if (word == kDevOk) return COV_OK;
   if (word == kDevTimeout) return COV_ETIMEOUT;
   return COV_EDEVICE;
+}
+
+// autotune candidates
+static const int kTuneG[3] = {4, 8, 16};
+static const int kTuneTRB[7] = {16, 24, 32, 48, 64, 96, 128};
+static const int kTuneL[5] = {2, 4, 8, 16, 32};
+
+cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                                       size_t *bytes) {
+  if (!bytes || !shape_ok(N, M, P, Q) || (dtype != COV_C64 && dtype != COV_C128)) return COV_EINVAL;
+  if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+  const int elem = dtype == COV_C128 ? 16 : 8;
+  const int sms = device_sms();
+  RecParams p;
+  WsLayout ws;
+  plan_recurrence(N, M, M, P, Q, elem, sms, p, ws, nullptr);
+  size_t mx = ws.total;
+  for (int gi = 0; gi < 3; ++gi)
+    for (int ti = 0; ti < 7; ++ti) {
+      const Tuning c = {kTuneG[gi], kTuneTRB[ti], 8};
+      plan_recurrence(N, M, M, P, Q, elem, sms, p, ws, &c);
+      if (ws.total > mx) mx = ws.total;
+    }
+  *bytes = mx;
+  return COV_OK;
+}
+
+static bool tuning_valid(const cov_tuning_t &t, int elem) {
+  const bool g_ok = t.lag_group == 4 || t.lag_group == 8 || (t.lag_group == 16 && elem == 8);
+  return g_ok && t.rows_per_task >= 8 && t.rows_per_task <= 256 && t.rows_per_task % 8 == 0 &&
+         t.reseed_interval >= 1 && t.reseed_interval <= kMaxPQ;
+}
+
+cov_status cov_tuning_get(cov_dtype dtype, int64_t N, int64_t M, int P, int Q, cov_tuning_t *out,
+                          int *cached) {
+  if (!out || !shape_ok(N, M, P, Q) || (dtype != COV_C64 && dtype != COV_C128)) return COV_EINVAL;
+  if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+  const int elem = dtype == COV_C128 ? 16 : 8;
+  const int sms = device_sms();
+  Tuning t;
+  if (cached) *cached = lookup_tuning(elem, N, M, P, Q, sms, t) ? 1 : 0;
+  RecParams p;
+  WsLayout ws;
+  plan_recurrence(N, M, M, P, Q, elem, sms, p, ws);
+  out->lag_group = p.G;
+  out->rows_per_task = p.TRB;
+  out->reseed_interval = p.L;
+  return COV_OK;
+}
+
+cov_status cov_tuning_set(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                          const cov_tuning_t *t) {
+  if (!shape_ok(N, M, P, Q) || (dtype != COV_C64 && dtype != COV_C128)) return COV_EINVAL;
+  if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+  const int elem = dtype == COV_C128 ? 16 : 8;
+  if (t && !tuning_valid(*t, elem)) return COV_EINVAL;
+  if (t) {
+    const Tuning k = {t->lag_group, t->rows_per_task, t->reseed_interval};
+    store_tuning(elem, N, M, P, Q, device_sms(), &k);
+  } else {
+    store_tuning(elem, N, M, P, Q, device_sms(), nullptr);
+  }
+  return COV_OK;
+}
+
+void cov_tuning_clear(void) { clear_tuning(); }
+
+cov_status cov_tuning_save(const char *path) {
+  if (!path) return COV_EINVAL;
+  return save_tuning(path) == 0 ? COV_OK : COV_EINVAL;
+}
+
+cov_status cov_tuning_load(const char *path, int *n_loaded) {
+  if (!path) return COV_EINVAL;
+  const int n = load_tuning(path);
+  if (n_loaded) *n_loaded = n < 0 ? 0 : n;
+  return n < 0 ? COV_EINVAL : COV_OK;
+}
+
+cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, int64_t lda, int P,
+                        int Q, void *R, void *workspace, size_t ws_bytes, int reps,
+                        cov_stream_t stream, cov_tuning_t *best, float *best_ms) {
+  if (!A || !R || !shape_ok(N, M, P, Q) || lda < M || (dtype != COV_C64 && dtype != COV_C128) ||
+      reps < 1 || reps > 1000)
+    return COV_EINVAL;
+  if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+  const int elem = dtype == COV_C128 ? 16 : 8;
+  if (((uintptr_t)A % (uintptr_t)(elem / 2)) != 0 || ((uintptr_t)R % (uintptr_t)(elem / 2)) != 0)
+    return COV_EINVAL;
+  if (!workspace || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  const int sms = device_sms();
+  if (sms <= 0) return COV_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return COV_ECUDA;
+  }
+  // Times one candidate; returns its mean milliseconds per call, or a negative
+  // value when it does not fit the workspace or repeats a planned config.
+  std::vector<Tuning> seen;
+  cov_status err = COV_OK;
+  auto time_one = [&](const Tuning &cand) -> float {
+    RecParams p;
+    WsLayout ws;
+    plan_recurrence(N, M, lda, P, Q, elem, sms, p, ws, &cand);
+    if (ws.total > ws_bytes) return -1.f;
+    const Tuning eff = {p.G, p.TRB, p.L};
+    for (const Tuning &k : seen)
+      if (k.G == eff.G && k.TRB == eff.TRB && k.L == eff.L) return -1.f;
+    seen.push_back(eff);
+    cov_status st = run_recurrence(A, elem, N, M, lda, P, Q, R, COV_MEAN, workspace, ws_bytes,
+                                   sms, s, &eff, nullptr);
+    if (st == COV_OK && cudaEventRecord(e0, s) != cudaSuccess) st = COV_ECUDA;
+    for (int r = 0; r < reps && st == COV_OK; ++r)
+      st = run_recurrence(A, elem, N, M, lda, P, Q, R, COV_MEAN, workspace, ws_bytes, sms, s,
+                          &eff, nullptr);
+    if (st == COV_OK && cudaEventRecord(e1, s) != cudaSuccess) st = COV_ECUDA;
+    if (st == COV_OK && cudaEventSynchronize(e1) != cudaSuccess) st = COV_ECUDA;
+    float ms = 0.f;
+    if (st == COV_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = COV_ECUDA;
+    if (st == COV_OK) st = cov_check_device_status(workspace, stream);
+    if (st != COV_OK) {
+      err = st;
+      return -1.f;
+    }
+    return ms / (float)reps;
+  };
+  RecParams p0;
+  WsLayout ws0;
+  plan_recurrence(N, M, lda, P, Q, elem, sms, p0, ws0, nullptr);
+  Tuning bestt = {0, 0, 0};
+  float bestv = -1.f;
+  // stage 1: lags per group and rows per task (the product kernel)
+  for (int gi = 0; gi < 3 && err == COV_OK; ++gi) {
+    if (kTuneG[gi] == 16 && elem == 16) continue;
+    for (int ti = 0; ti < 7 && err == COV_OK; ++ti) {
+      const Tuning c = {kTuneG[gi], kTuneTRB[ti], p0.L};
+      const float v = time_one(c);
+      if (v > 0.f && (bestv < 0.f || v < bestv)) {
+        bestv = v;
+        bestt = seen.back();
+      }
+    }
+  }
+  // stage 2: the walk's re-seed interval at the best stage-1 knobs
+  for (int li = 0; li < 5 && err == COV_OK && bestv > 0.f; ++li) {
+    const Tuning c = {bestt.G, bestt.TRB, kTuneL[li]};
+    const float v = time_one(c);
+    if (v > 0.f && v < bestv) {
+      bestv = v;
+      bestt = seen.back();
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != COV_OK) return err;
+  if (bestv < 0.f) return COV_EWORKSPACE;  // no candidate fits the workspace
+  store_tuning(elem, N, M, P, Q, sms, &bestt);
+  if (best) {
+    best->lag_group = bestt.G;
+    best->rows_per_task = bestt.TRB;
+    best->reseed_interval = bestt.L;
+  }
+  if (best_ms) *best_ms = bestv;
+  return COV_OK;
 }
 
 }  // extern "C"

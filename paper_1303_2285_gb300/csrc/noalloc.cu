@@ -70,14 +70,14 @@ extern "C" cov_status cov_estimate_noalloc(const void *A, cov_dtype dtype, int64
   const int elem = dtype == COV_C128 ? 16 : 8;
   if (((uintptr_t)A % (uintptr_t)(elem / 2)) != 0 || ((uintptr_t)R % (uintptr_t)(elem / 2)) != 0)
     return COV_EINVAL;
-  RecParams p;
-  WsLayout ws;
-  plan_recurrence(N, M, lda, P, Q, elem, p, ws);
-  if (ws.total > kNoAllocScratchBytes) return COV_EWORKSPACE;  // beyond the static maximum
   void *base = nullptr;
   int sms = 0;
   const cov_status st = scratch_for_current_device(&base, &sms);
   if (st != COV_OK) return st;
+  RecParams p;
+  WsLayout ws;
+  plan_recurrence(N, M, lda, P, Q, elem, sms, p, ws);
+  if (ws.total > kNoAllocScratchBytes) return COV_EWORKSPACE;  // beyond the static maximum
   cudaStream_t s = (cudaStream_t)stream;
   char *w = (char *)base;
   p.A = A;

@@ -1,7 +1,11 @@
 // Host plan layer of the combination path (integer arithmetic only).
 #include "plan.h"
 
+#include <stdio.h>
 #include <string.h>
+
+#include <mutex>
+#include <vector>
 
 namespace cov {
 
@@ -43,8 +47,11 @@ int choose_group(int P, int Q, int elem) {
   return 4;
 }
 
-void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int elem,
-                     RecParams &p, WsLayout &ws) {
+void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int elem, int sms,
+                     RecParams &p, WsLayout &ws, const Tuning *tune) {
+  Tuning t = {0, 0, 0};
+  if (tune) t = *tune;
+  else lookup_tuning(elem, N, M, P, Q, sms, t);
   memset(&p, 0, sizeof(p));
   p.N = (int)N;
   p.M = (int)M;
@@ -54,6 +61,7 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.K = n_positions(N, M, P, Q);
   p.n_uc = (int)n_unique_combinations(P, Q);
   p.G = choose_group(P, Q, elem);
+  if (t.G == 4 || t.G == 8 || (t.G == 16 && elem == 8)) p.G = t.G;
   p.ngroups = n_groups(P, Q, p.G);
   p.inner_lo = P - 1;
   p.n_inner = (int)(N - 2LL * P + 2);
@@ -73,6 +81,7 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   long long tr_max = rows_max - span;
   if (tr_max < 8) tr_max = 8;
   int TRB = tr_max >= 48 ? 48 : (int)(tr_max / 8) * 8;
+  if (t.TRB >= 8 && t.TRB % 8 == 0 && t.TRB <= tr_max) TRB = t.TRB;
   if (TRB < 8) TRB = 8;
   int TPT = (int)(tr_max / TRB);
   if (TPT > 4) TPT = 4;
@@ -97,7 +106,7 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.NCH = (int)((M - 2LL * Q + 2 + p.CWF - 1) / p.CWF);
   p.QMAXF = Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
   p.FPITCH = ((p.CWF + p.QMAXF - 1 + 14) / 16) * 16 + 1;  // >= CWF+QMAXF-1, = 1 mod 16
-  p.L = 8;
+  p.L = (t.L >= 1 && t.L <= kMaxPQ) ? t.L : 8;
   p.div_double = (elem == 8 && p.K > (1LL << 24)) ? 1 : 0;
   // workspace
   size_t off = kWsHeader;
@@ -112,6 +121,80 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   ws.colval_off = off;
   off = align256(off + (size_t)p.n_uc * Q * elem);
   ws.total = off;
+}
+
+// ---- tuned knobs: process-wide cache ---------------------------------------
+namespace {
+struct TuneEntry {
+  int elem;
+  long long N, M;
+  int P, Q, sms;
+  Tuning t;
+};
+std::mutex g_tune_mutex;
+std::vector<TuneEntry> g_tune;
+}  // namespace
+
+bool lookup_tuning(int elem, long long N, long long M, int P, int Q, int sms, Tuning &out) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  for (const TuneEntry &e : g_tune)
+    if (e.elem == elem && e.N == N && e.M == M && e.P == P && e.Q == Q && e.sms == sms) {
+      out = e.t;
+      return true;
+    }
+  return false;
+}
+
+void store_tuning(int elem, long long N, long long M, int P, int Q, int sms, const Tuning *t) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  for (size_t k = 0; k < g_tune.size(); ++k) {
+    TuneEntry &e = g_tune[k];
+    if (e.elem == elem && e.N == N && e.M == M && e.P == P && e.Q == Q && e.sms == sms) {
+      if (t) e.t = *t;
+      else g_tune.erase(g_tune.begin() + (long)k);
+      return;
+    }
+  }
+  if (t) g_tune.push_back({elem, N, M, P, Q, sms, *t});
+}
+
+void clear_tuning() {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune.clear();
+}
+
+int save_tuning(const char *path) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  FILE *f = fopen(path, "w");
+  if (!f) return -1;
+  fprintf(f, "# elem N M P Q sms G TRB L\n");
+  for (const TuneEntry &e : g_tune)
+    fprintf(f, "%d %lld %lld %d %d %d %d %d %d\n", e.elem, e.N, e.M, e.P, e.Q, e.sms, e.t.G,
+            e.t.TRB, e.t.L);
+  return fclose(f) == 0 ? 0 : -1;
+}
+
+int load_tuning(const char *path) {
+  FILE *f = fopen(path, "r");
+  if (!f) return -1;
+  char line[256];
+  int n = 0;
+  while (fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    int elem, P, Q, sms, G, TRB, L;
+    long long N, M;
+    if (sscanf(line, "%d %lld %lld %d %d %d %d %d %d", &elem, &N, &M, &P, &Q, &sms, &G, &TRB, &L) ==
+        9) {
+      const Tuning t = {G, TRB, L};
+      store_tuning(elem, N, M, P, Q, sms, &t);
+      ++n;
+    } else {
+      n = -1;
+      break;
+    }
+  }
+  fclose(f);
+  return n;
 }
 
 }  // namespace cov

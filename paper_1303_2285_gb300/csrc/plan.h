@@ -27,9 +27,25 @@ bool recurrence_ok(long long N, long long M, int P, int Q);
 // slots stay within 2% of the fewest.
 int choose_group(int P, int Q, int elem);
 
+// Tuned knobs of the combination path (0 = the plan's default): lags per
+// group G, rows per product task TRB, walk re-seed interval L.
+struct Tuning {
+  int G, TRB, L;
+};
+
 // Fills every field of p that depends on the shape only (not the pointers);
-// returns the workspace layout. elem = bytes of one complex number.
-void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int elem,
-                     RecParams &p, WsLayout &ws);
+// returns the workspace layout. elem = bytes of one complex number. `tune`
+// overrides the knobs; when null, the cached tuning for (elem, shape, sms),
+// if any, is used, else the defaults.
+void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int elem, int sms,
+                     RecParams &p, WsLayout &ws, const Tuning *tune = nullptr);
+
+// Process-wide cache of tuned knobs, keyed by (elem, N, M, P, Q, SM count).
+bool lookup_tuning(int elem, long long N, long long M, int P, int Q, int sms, Tuning &out);
+void store_tuning(int elem, long long N, long long M, int P, int Q, int sms,
+                  const Tuning *t);  // t == null removes the entry
+void clear_tuning();
+int save_tuning(const char *path);  // 0 on success, -1 on error
+int load_tuning(const char *path);  // entries read, -1 on a malformed file
 
 }  // namespace cov
