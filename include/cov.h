@@ -295,6 +295,49 @@ cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype,
                                  void *dA, void *workspace, size_t ws_bytes,
                                  cov_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Sharding across GPUs (one process per GPU). Section 4.2 gives every
+ * combination Delta = (dr, dc) its own set of outputs of R (Eq. 3.7-3.8), so
+ * disjoint sets of combinations write disjoint parts of R and need no
+ * reduction; Section 5.1 balances the work by the combinations' costs. The
+ * shard unit here is a column lag dc: all combinations (dr, dc) of that dc,
+ * which own exactly the P x P blocks (a, b) of R with |b - a| = dc (block
+ * (a, b) = rows a*P .. a*P+P-1, columns b*P .. b*P+P-1). Every rank needs the
+ * whole of A. Host-only planning; the data exchange (gathering the blocks) is
+ * the caller's.
+ * ------------------------------------------------------------------------- */
+
+/* Splits the column lags [0, Q) into n_ranks contiguous ranges: rank r owns
+ * [dc_begin[r], dc_begin[r+1]) (dc_begin: HOST array of n_ranks + 1 entries;
+ * empty ranges when n_ranks > Q). The split minimises the largest rank cost,
+ * cost = distinct products of the rank's combinations plus a fixed share per
+ * combination; rank_cost (HOST, n_ranks, optional) receives them.
+ * COV_EUNSUPPORTED for shapes COV_RECURRENCE does not take. */
+cov_status cov_partition_lags(int64_t N, int64_t M, int P, int Q, int n_ranks, int32_t *dc_begin,
+                              int64_t *rank_cost);
+/* COV_RECURRENCE restricted to the column lags [dc_lo, dc_hi): writes exactly
+ * the blocks (a, b) of R with dc_lo <= |b - a| < dc_hi (both triangles, same
+ * values as cov_estimate_ex) and leaves every other element of R untouched.
+ * Same workspace as cov_estimate_ex with COV_RECURRENCE; an empty range queues
+ * nothing but the status-word reset. */
+cov_status cov_estimate_shard(const void *A, cov_dtype dtype, int64_t N, int64_t M, int64_t lda,
+                              int P, int Q, int dc_lo, int dc_hi, void *R, cov_norm norm,
+                              void *workspace, size_t ws_bytes, cov_stream_t stream);
+/* Batched workload (Section 5.1, several matrices at once): assigns each of
+ * `count` matrices (HOST descriptors; only the sizes are read) to one of
+ * n_ranks ranks, longest processing time first by the same cost the batched
+ * plan uses; rank_of (HOST, count) and rank_cost (HOST, n_ranks, optional). */
+cov_status cov_partition_matrices(const cov_desc *descs, int count, int n_ranks, int32_t *rank_of,
+                                  int64_t *rank_cost);
+/* Adjoint: rank r owns the rows [row_begin[r], row_begin[r+1]) of dA (equal
+ * bands; row_begin HOST, n_ranks + 1 entries) and needs the rows
+ * [halo_lo[r], halo_hi[r]) of A (the band widened by P - 1 rows each way,
+ * clipped; HOST, n_ranks each, optional). Because dA is linear in G, the band
+ * equals those rows of cov_estimate_backward on that sub-image with COV_SUM
+ * and G scaled by 1/K of the full image (COV_MEAN) or unscaled (COV_SUM). */
+cov_status cov_partition_rows(int64_t N, int P, int n_ranks, int64_t *row_begin, int64_t *halo_lo,
+                              int64_t *halo_hi);
+
 #ifdef __cplusplus
 }
 #endif

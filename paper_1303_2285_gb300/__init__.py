@@ -84,6 +84,15 @@ SIGNATURES = [
     ("cov_backward_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
     ("cov_estimate_backward", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _VP, _VP, _SZ, _VP]),
     ("cov_selftest_timeout", _I, [_VP, _SZ, ctypes.c_uint32, _VP]),
+    ("cov_partition_lags", _I, [_I64, _I64, _I, _I, _I, ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_int64)]),
+    ("cov_estimate_shard", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _I, _I, _VP, _I, _VP, _SZ,
+                                _VP]),
+    ("cov_partition_matrices", _I, [ctypes.POINTER(CovDesc), _I, _I,
+                                    ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int64)]),
+    ("cov_partition_rows", _I, [_I64, _I, _I, ctypes.POINTER(ctypes.c_int64),
+                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("cov_tuning_get", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(Tuning),
                             ctypes.POINTER(ctypes.c_int)]),
     ("cov_tuning_set", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(Tuning)]),

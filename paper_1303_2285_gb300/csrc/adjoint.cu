@@ -128,6 +128,19 @@ __global__ void __launch_bounds__(256) k_adj_col2im(const AdjParams p) {
 
 extern "C" {
 
+cov_status cov_partition_rows(int64_t N, int P, int n_ranks, int64_t *row_begin, int64_t *halo_lo,
+                              int64_t *halo_hi) {
+  if (!row_begin || N < 1 || P < 1 || P > N || n_ranks < 1 || n_ranks > 65536) return COV_EINVAL;
+  for (int r = 0; r <= n_ranks; ++r) row_begin[r] = (int64_t)((__int128)N * r / n_ranks);
+  for (int r = 0; r < n_ranks; ++r) {
+    // rows of every window that covers a row of the band
+    const int64_t lo = row_begin[r] - (P - 1), hi = row_begin[r + 1] + (P - 1);
+    if (halo_lo) halo_lo[r] = lo < 0 ? 0 : lo;
+    if (halo_hi) halo_hi[r] = hi > N ? N : hi;
+  }
+  return COV_OK;
+}
+
 cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
                                        size_t *bytes) {
   if (!bytes || N < 1 || M < 1 || P < 1 || Q < 1 || P > N || Q > M) return COV_EINVAL;

@@ -39,10 +39,12 @@ cudaEvent_t g_stage_store[5 * 4096];
 // path on the caller's workspace.
 cov_status run_recurrence(const void *A, int elem, int64_t N, int64_t M, int64_t lda, int P, int Q,
                           void *R, cov_norm norm, void *workspace, size_t ws_bytes, int sms,
-                          cudaStream_t s, const Tuning *tune, StageEvents *marks) {
+                          cudaStream_t s, const Tuning *tune, StageEvents *marks, int dc_lo = 0,
+                          int dc_hi = -1) {
   RecParams p;
   WsLayout ws;
   plan_recurrence(N, M, lda, P, Q, elem, sms, p, ws, tune);
+  if (dc_hi >= 0) restrict_to_lags(p, dc_lo, dc_hi);
   if (!workspace || ws_bytes < ws.total || ((uintptr_t)workspace & 255) != 0)
     return COV_EWORKSPACE;
   char *w = (char *)workspace;
@@ -56,6 +58,7 @@ cov_status run_recurrence(const void *A, int elem, int64_t N, int64_t M, int64_t
   p.rowval = w + ws.rowval_off;
   p.colval = w + ws.colval_off;
   if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  if (p.dc_lo >= p.dc_hi) return COV_OK;  // empty shard
   if (launch_recurrence(p, elem == 16, sms, s, marks) != cudaSuccess) return COV_ECUDA;
   return COV_OK;
 }
@@ -241,6 +244,36 @@ cov_status cov_check_device_status(void *workspace, cov_stream_t stream) {
   if (word == kDevOk) return COV_OK;
   if (word == kDevTimeout) return COV_ETIMEOUT;
   return COV_EDEVICE;
+}
+
+cov_status cov_partition_lags(int64_t N, int64_t M, int P, int Q, int n_ranks, int32_t *dc_begin,
+                              int64_t *rank_cost) {
+  if (!dc_begin || !shape_ok(N, M, P, Q) || n_ranks < 1 || n_ranks > 65536) return COV_EINVAL;
+  if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+  std::vector<int> b(n_ranks + 1);
+  std::vector<long long> c(n_ranks);
+  partition_lags(N, M, P, Q, n_ranks, b.data(), c.data());
+  for (int r = 0; r <= n_ranks; ++r) dc_begin[r] = b[r];
+  if (rank_cost)
+    for (int r = 0; r < n_ranks; ++r) rank_cost[r] = c[r];
+  return COV_OK;
+}
+
+cov_status cov_estimate_shard(const void *A, cov_dtype dtype, int64_t N, int64_t M, int64_t lda,
+                              int P, int Q, int dc_lo, int dc_hi, void *R, cov_norm norm,
+                              void *workspace, size_t ws_bytes, cov_stream_t stream) {
+  if (!A || !R || !shape_ok(N, M, P, Q) || lda < M || (dtype != COV_C64 && dtype != COV_C128) ||
+      (norm != COV_MEAN && norm != COV_SUM) || dc_lo < 0 || dc_hi < dc_lo || dc_hi > Q)
+    return COV_EINVAL;
+  if (!recurrence_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+  const int elem = dtype == COV_C128 ? 16 : 8;
+  if (((uintptr_t)A % (uintptr_t)(elem / 2)) != 0 || ((uintptr_t)R % (uintptr_t)(elem / 2)) != 0)
+    return COV_EINVAL;
+  if (!workspace || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  const int sms = device_sms();
+  if (sms <= 0) return COV_ECUDA;
+  return run_recurrence(A, elem, N, M, lda, P, Q, R, norm, workspace, ws_bytes, sms,
+                        (cudaStream_t)stream, nullptr, nullptr, dc_lo, dc_hi);
 }
 
 // autotune candidates

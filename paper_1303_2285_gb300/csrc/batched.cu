@@ -331,6 +331,24 @@ size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 extern "C" {
 
+cov_status cov_partition_matrices(const cov_desc *descs, int count, int n_ranks, int32_t *rank_of,
+                                  int64_t *rank_cost) {
+  if (!descs || count < 1 || n_ranks < 1 || n_ranks > 65536 || !rank_of) return COV_EINVAL;
+  std::vector<long long> cost(count);
+  for (int i = 0; i < count; ++i) {
+    const cov_desc &d = descs[i];
+    if (d.N < 1 || d.M < 1 || d.P < 1 || d.Q < 1 || d.P > d.N || d.Q > d.M) return COV_EINVAL;
+    cost[i] = cov::matrix_cost(d.N, d.M, d.P, d.Q);
+  }
+  std::vector<int> bin(count);
+  std::vector<long long> load(n_ranks);
+  cov::lpt_assign(cost.data(), count, n_ranks, bin.data(), load.data());
+  for (int i = 0; i < count; ++i) rank_of[i] = bin[i];
+  if (rank_cost)
+    for (int r = 0; r < n_ranks; ++r) rank_cost[r] = load[r];
+  return COV_OK;
+}
+
 cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype, cov_algo algo,
                                    cov_norm norm, cov_batched_plan **plan) {
   if (!descs || count < 1 || !plan || (norm != COV_MEAN && norm != COV_SUM)) return COV_EINVAL;
@@ -346,30 +364,23 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   cov_batched_plan *pl = new cov_batched_plan();
   pl->mean = norm == COV_MEAN ? 1 : 0;
   pl->descs.resize(count);
-  std::vector<std::pair<long long, int>> cost(count);
+  std::vector<long long> cost(count);
   for (int i = 0; i < count; ++i) {
     const cov_desc &d = descs[i];
     pl->descs[i] = {(const float2 *)d.A, (float2 *)d.R, d.lda, d.N, d.M, d.P, d.Q};
-    const long long um = cov::distinct_products(d.N, d.M, d.P, d.Q);
-    const long long nuc = cov::n_unique_combinations(d.P, d.Q);
-    cost[i] = {um + 2000LL * nuc + 20000, i};
+    cost[i] = cov::matrix_cost(d.N, d.M, d.P, d.Q);
   }
   const int grid = std::min(sms, count);
-  // longest processing time first: largest matrix to the least-loaded CTA
-  std::sort(cost.begin(), cost.end(), [](const std::pair<long long, int> &a,
-                                         const std::pair<long long, int> &b) {
-    return a.first > b.first || (a.first == b.first && a.second < b.second);
+  std::vector<int> bin(count);
+  cov::lpt_assign(cost.data(), count, grid, bin.data(), nullptr);
+  // each CTA's matrices in decreasing cost order (the order LPT placed them)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return cost[a] > cost[b] || (cost[a] == cost[b] && a < b);
   });
-  std::priority_queue<std::pair<long long, int>, std::vector<std::pair<long long, int>>,
-                      std::greater<std::pair<long long, int>>> load;
-  for (int c = 0; c < grid; ++c) load.push({0, c});
   std::vector<std::vector<int>> per(grid);
-  for (const auto &ci : cost) {
-    auto top = load.top();
-    load.pop();
-    per[top.second].push_back(ci.second);
-    load.push({top.first + ci.first, top.second});
-  }
+  for (int i : order) per[bin[i]].push_back(i);
   pl->grid = grid;
   pl->cta_begin.assign(grid + 1, 0);
   for (int c = 0; c < grid; ++c) {

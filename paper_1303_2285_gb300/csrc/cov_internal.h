@@ -87,6 +87,12 @@ COV_HD void group_of(int P, int G, int g, int &dc, int &d0, int &cnt) {
   const int c = P - d0;  // lags up to dr = P-1
   cnt = c < G ? c : G;
 }
+// First lag group and first combination of column lag dc (dc <= Q gives the
+// end of the range).
+COV_HD int first_group(int P, int G, int dc) {
+  return dc == 0 ? 0 : groups_dc0(P, G) + (dc - 1) * groups_per_dc(P, G);
+}
+COV_HD int first_combo(int P, int dc) { return dc == 0 ? 0 : P + (dc - 1) * (2 * P - 1); }
 // Largest lag (including unused slots) over all groups.
 COV_HD int group_lag_hi(int P, int Q, int G) {
   int hi = groups_dc0(P, G) * G - 1;
@@ -130,6 +136,10 @@ struct RecParams {
   int QMAXF, FPITCH;    // its column-lag register count (>= Q) and smem pitch
   // walk
   int L;                // re-seed interval along the diagonal
+  // shard: the column lags dc in [dc_lo, dc_hi) (the R blocks (a, b) with
+  // |b - a| in that range); lag groups [g_lo, g_lo + ngroups) and
+  // combinations [u_lo, u_hi) are theirs. The full problem is [0, Q).
+  int dc_lo, dc_hi, g_lo, u_lo, u_hi;
   // workspace
   unsigned *status;
   void *core_part;      // [n_uc][n_rb][n_cb]

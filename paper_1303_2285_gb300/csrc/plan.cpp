@@ -4,7 +4,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <functional>
 #include <mutex>
+#include <queue>
+#include <utility>
 #include <vector>
 
 namespace cov {
@@ -107,6 +111,11 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.QMAXF = Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
   p.FPITCH = ((p.CWF + p.QMAXF - 1 + 14) / 16) * 16 + 1;  // >= CWF+QMAXF-1, = 1 mod 16
   p.L = (t.L >= 1 && t.L <= kMaxPQ) ? t.L : 8;
+  p.dc_lo = 0;
+  p.dc_hi = Q;
+  p.g_lo = 0;
+  p.u_lo = 0;
+  p.u_hi = p.n_uc;
   p.div_double = (elem == 8 && p.K > (1LL << 24)) ? 1 : 0;
   // workspace
   size_t off = kWsHeader;
@@ -121,6 +130,89 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   ws.colval_off = off;
   off = align256(off + (size_t)p.n_uc * Q * elem);
   ws.total = off;
+}
+
+void restrict_to_lags(RecParams &p, int dc_lo, int dc_hi) {
+  p.dc_lo = dc_lo;
+  p.dc_hi = dc_hi;
+  p.g_lo = first_group(p.P, p.G, dc_lo);
+  p.ngroups = first_group(p.P, p.G, dc_hi) - p.g_lo;
+  p.u_lo = first_combo(p.P, dc_lo);
+  p.u_hi = first_combo(p.P, dc_hi);
+  p.tasks_per_tile = (long long)p.ngroups * p.CBT * p.TPT;
+  p.n_tasks = (long long)p.n_rt * p.n_ct * p.tasks_per_tile;
+}
+
+// cost of the combinations of column lag dc: their distinct products plus a
+// per-combination share of the reduction and walk
+static long long lag_cost(long long N, long long M, int P, int dc) {
+  long long c = 0;
+  const int lo = dc == 0 ? 0 : -(P - 1);
+  for (int dr = lo; dr <= P - 1; ++dr) c += (N - (dr < 0 ? -dr : dr)) * (M - dc) + 2000;
+  return c;
+}
+
+void partition_lags(long long N, long long M, int P, int Q, int n_ranks, int *dc_begin,
+                    long long *rank_cost) {
+  // contiguous ranges of dc minimising the largest rank cost (exact DP over
+  // the Q lags; ties go to the earlier split)
+  std::vector<long long> pre(Q + 1, 0);
+  for (int dc = 0; dc < Q; ++dc) pre[dc + 1] = pre[dc] + lag_cost(N, M, P, dc);
+  const int R = n_ranks;
+  const long long INF = (long long)1 << 62;
+  // best[r][k]: smallest max cost placing lags [0, k) on ranks [0, r)
+  std::vector<long long> best((size_t)(R + 1) * (Q + 1), INF);
+  std::vector<int> cut((size_t)(R + 1) * (Q + 1), 0);
+  best[0] = 0;
+  for (int r = 1; r <= R; ++r)
+    for (int k = 0; k <= Q; ++k)
+      for (int j = 0; j <= k; ++j) {
+        const long long prev = best[(size_t)(r - 1) * (Q + 1) + j];
+        if (prev >= INF) continue;
+        const long long seg = pre[k] - pre[j];
+        const long long v = prev > seg ? prev : seg;
+        if (v < best[(size_t)r * (Q + 1) + k]) {
+          best[(size_t)r * (Q + 1) + k] = v;
+          cut[(size_t)r * (Q + 1) + k] = j;
+        }
+      }
+  dc_begin[R] = Q;
+  int k = Q;
+  for (int r = R; r >= 1; --r) {
+    const int j = cut[(size_t)r * (Q + 1) + k];
+    dc_begin[r - 1] = j;
+    k = j;
+  }
+  dc_begin[0] = 0;
+  if (rank_cost)
+    for (int r = 0; r < R; ++r) rank_cost[r] = pre[dc_begin[r + 1]] - pre[dc_begin[r]];
+}
+
+long long matrix_cost(long long N, long long M, int P, int Q) {
+  return distinct_products(N, M, P, Q) + 2000LL * n_unique_combinations(P, Q) + 20000;
+}
+
+void lpt_assign(const long long *cost, int count, int n_bins, int *bin, long long *load) {
+  // longest processing time first: the costliest item to the least-loaded
+  // bin (ties: lower item index first, lower bin index first)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return cost[a] > cost[b] || (cost[a] == cost[b] && a < b);
+  });
+  std::priority_queue<std::pair<long long, int>, std::vector<std::pair<long long, int>>,
+                      std::greater<std::pair<long long, int>>> q;
+  for (int c = 0; c < n_bins; ++c) q.push({0, c});
+  std::vector<long long> l(n_bins, 0);
+  for (int i : order) {
+    const auto top = q.top();
+    q.pop();
+    bin[i] = top.second;
+    l[top.second] = top.first + cost[i];
+    q.push({l[top.second], top.second});
+  }
+  if (load)
+    for (int c = 0; c < n_bins; ++c) load[c] = l[c];
 }
 
 // ---- tuned knobs: process-wide cache ---------------------------------------

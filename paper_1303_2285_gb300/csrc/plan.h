@@ -40,6 +40,21 @@ struct Tuning {
 void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int elem, int sms,
                      RecParams &p, WsLayout &ws, const Tuning *tune = nullptr);
 
+// Restricts a plan to the column lags [dc_lo, dc_hi) (one shard).
+void restrict_to_lags(RecParams &p, int dc_lo, int dc_hi);
+
+// Splits the column lags [0, Q) into n_ranks contiguous ranges (dc_begin has
+// n_ranks + 1 entries) minimising the largest per-rank cost; rank_cost
+// (optional) receives each rank's cost.
+void partition_lags(long long N, long long M, int P, int Q, int n_ranks, int *dc_begin,
+                    long long *rank_cost);
+
+// Scheduling cost of one matrix (distinct products plus per-combination and
+// per-matrix overheads) and the longest-processing-time-first assignment of
+// `count` items to `n_bins` bins (bin[i] per item; load per bin, optional).
+long long matrix_cost(long long N, long long M, int P, int Q);
+void lpt_assign(const long long *cost, int count, int n_bins, int *bin, long long *load);
+
 // Process-wide cache of tuned knobs, keyed by (elem, N, M, P, Q, SM count).
 bool lookup_tuning(int elem, long long N, long long M, int P, int Q, int sms, Tuning &out);
 void store_tuning(int elem, long long N, long long M, int P, int Q, int sms,

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) k_fringe_rows(const RecParams p) {
     C2 *out = (C2 *)p.sin_part;
 #pragma unroll
     for (int dc = 0; dc < QMAX; ++dc) {
-      if (dc >= Q || (dc == 0 && dr < 0)) continue;
+      if (dc < p.dc_lo || dc >= p.dc_hi || (dc == 0 && dr < 0)) continue;
       const int D = combo_index(P, dr, dc);
       out[((long long)D * p.NFR + fr) * p.NCH + cc] = acc[dc];
     }

@@ -127,7 +127,7 @@ __device__ __forceinline__ void product_task(const RecParams &p, long long tile,
   const int rb = rt * p.TPT + sub;
   if (cbg >= p.n_cb || rb >= p.n_rb) return;
   int dc, d0, cnt;
-  group_of(p.P, G, g, dc, d0, cnt);
+  group_of(p.P, G, p.g_lo + g, dc, d0, cnt);
   const int n0 = p.inner_lo + rb * p.TRB;
   const int rem = p.inner_lo + p.n_inner - n0;
   const int rows = rem < p.TRB ? rem : p.TRB;

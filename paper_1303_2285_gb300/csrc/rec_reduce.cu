@@ -51,9 +51,10 @@ __global__ void __launch_bounds__(128) k_reduce(const RecParams p) {
   pdl_wait();  // the product and fringe-row kernels' partials
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int Q = p.Q, P = p.P, W = p.M - p.Q + 1;
-  if ((int)blockIdx.x < p.n_uc) {
+  const int n_own = p.u_hi - p.u_lo;
+  if ((int)blockIdx.x < n_own) {
     // ---- one CTA per combination: core, fringe-column sums, CV ----------
-    const int D = blockIdx.x;
+    const int D = p.u_lo + (int)blockIdx.x;
     int dr, dc;
     combo_of(P, D, dr, dc);
     Neu<T> cr, ci;
@@ -152,9 +153,9 @@ __global__ void __launch_bounds__(128) k_reduce(const RecParams p) {
     return;
   }
   // ---- one warp per (combination, fringe row): RV ------------------------
-  const long long w2 = ((long long)blockIdx.x - p.n_uc) * 4 + wib;
-  if (w2 >= (long long)p.n_uc * p.NFR) return;
-  const int D = (int)(w2 / p.NFR), fr = (int)(w2 % p.NFR);
+  const long long w2 = ((long long)blockIdx.x - n_own) * 4 + wib;
+  if (w2 >= (long long)n_own * p.NFR) return;
+  const int D = p.u_lo + (int)(w2 / p.NFR), fr = (int)(w2 % p.NFR);
   int dr, dc;
   combo_of(P, D, dr, dc);
   const int n = fr < P - 1 ? fr : (p.N - P + 1) + (fr - (P - 1));
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(256) k_walk_write(const RecParams p) {
   C2 *B = (C2 *)smem_k4;                 // [P][P+1]
   C2 *RVs = B + P * PP;                  // [2P-1][NFR]
   C2 *CVs = RVs + D2 * NFR;              // [2P-1]
-  int b = blockIdx.x, dc = 0;
+  int b = blockIdx.x, dc = p.dc_lo;
   while (b >= p.Q - dc) {
     b -= p.Q - dc;
     ++dc;
@@ -339,9 +340,10 @@ __global__ void __launch_bounds__(256) k_walk_write(const RecParams p) {
 
 template <typename T>
 static cudaError_t launch_reduce_t(const RecParams &p, cudaStream_t s, bool pdl) {
-  // blocks [0, n_uc): one per combination; then 4 (combination, fringe row)
+  // one block per combination of the shard; then 4 (combination, fringe row)
   // pairs per block
-  const long long blocks = (long long)p.n_uc + ((long long)p.n_uc * p.NFR + 3) / 4;
+  const long long n_own = p.u_hi - p.u_lo;
+  const long long blocks = n_own + (n_own * p.NFR + 3) / 4;
   const cudaError_t e = ensure_smem_attr(k_reduce<T>, 0);
   if (e != cudaSuccess) return e;
   return launch_k(k_reduce<T>, dim3((unsigned)blocks), dim3(128), 0, s, pdl, p);
@@ -349,7 +351,8 @@ static cudaError_t launch_reduce_t(const RecParams &p, cudaStream_t s, bool pdl)
 
 template <typename T>
 static cudaError_t launch_walk_t(const RecParams &p, cudaStream_t s, bool pdl) {
-  const int nblk = p.Q * (p.Q + 1) / 2;
+  int nblk = 0;  // blocks (bj, bj + dc) of the shard's column lags
+  for (int dc = p.dc_lo; dc < p.dc_hi; ++dc) nblk += p.Q - dc;
   const size_t smem = ((size_t)p.P * (p.P + 1) + (size_t)(2 * p.P - 1) * (p.NFR + 1)) *
                       sizeof(typename C2t<T>::type);
   auto kern = k_walk_write<T>;
