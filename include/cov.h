@@ -201,7 +201,12 @@ cov_status cov_set_stage_events(void *const *events, int n_events);
  *                   [8, 256] (clamped by the planner to what shared memory
  *                   holds);
  *   reseed_interval outputs walked from one direct seed along a diagonal,
- *                   1..32 (1 = every output seeded directly).
+ *                   1..32 (1 = every output seeded directly);
+ *   kernels         1 = the four stages in one cooperative kernel with grid
+ *                   barriers (COV_C64 only), 4 = four kernels chained by
+ *                   programmatic dependent launch (the only form for
+ *                   COV_C128), 0 = the default (COV_C64: 1 while
+ *                   |UC| * 2(P-1) <= 32768, else 4).
  * A process-wide host cache maps (dtype, N, M, P, Q, SM count of the current
  * device) to knobs; planning (cov_workspace_size, cov_estimate_ex,
  * cov_estimate, cov_estimate_noalloc) uses the cached knobs for that key, else
@@ -213,6 +218,7 @@ typedef struct {
   int32_t lag_group;
   int32_t rows_per_task;
   int32_t reseed_interval;
+  int32_t kernels;
 } cov_tuning_t;
 
 /* Knobs planning would use for this shape now (*out); *cached (optional)
@@ -226,7 +232,7 @@ cov_status cov_tuning_set(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
                           const cov_tuning_t *t);
 void cov_tuning_clear(void);
 /* Writes the cache to a text file (one line per entry: dtype-bytes N M P Q
- * SMs knobs) / merges such a file into it (*n_loaded = entries read).
+ * SMs and the four knobs) / merges such a file into it (*n_loaded = entries read).
  * COV_EINVAL if the file cannot be written or read or has a malformed line. */
 cov_status cov_tuning_save(const char *path);
 cov_status cov_tuning_load(const char *path, int *n_loaded);
@@ -238,7 +244,7 @@ cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, in
 /* Times COV_RECURRENCE candidates on the caller's data with CUDA events on
  * `stream` (one warm-up and `reps` timed calls each, 1 <= reps <= 1000):
  * first lag_group x rows_per_task, then reseed_interval at the best of
- * those; stores the fastest in the cache and returns it in *best (optional)
+ * those, then (COV_C64) one kernel against four; stores the fastest in the cache and returns it in *best (optional)
  * with its mean milliseconds per call in *best_ms (optional). Overwrites R
  * (with the correct mean-normalised estimate) and the workspace; synchronises
  * `stream`; not capturable. A candidate whose device status word reports a

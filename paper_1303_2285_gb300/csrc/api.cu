@@ -57,7 +57,8 @@ cov_status run_recurrence(const void *A, int elem, int64_t N, int64_t M, int64_t
   p.sin_part = w + ws.sin_off;
   p.rowval = w + ws.rowval_off;
   p.colval = w + ws.colval_off;
-  if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  // status word and the fused kernel's barrier and task counters start at 0
+  if (cudaMemsetAsync(w, 0, 16, s) != cudaSuccess) return COV_ECUDA;
   if (p.dc_lo >= p.dc_hi) return COV_OK;  // empty shard
   if (launch_recurrence(p, elem == 16, sms, s, marks) != cudaSuccess) return COV_ECUDA;
   return COV_OK;
@@ -293,7 +294,7 @@ cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, in
   size_t mx = ws.total;
   for (int gi = 0; gi < 3; ++gi)
     for (int ti = 0; ti < 7; ++ti) {
-      const Tuning c = {kTuneG[gi], kTuneTRB[ti], 8};
+      const Tuning c = {kTuneG[gi], kTuneTRB[ti], 8, 0};
       plan_recurrence(N, M, M, P, Q, elem, sms, p, ws, &c);
       if (ws.total > mx) mx = ws.total;
     }
@@ -303,8 +304,9 @@ cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, in
 
 static bool tuning_valid(const cov_tuning_t &t, int elem) {
   const bool g_ok = t.lag_group == 4 || t.lag_group == 8 || (t.lag_group == 16 && elem == 8);
-  return g_ok && t.rows_per_task >= 8 && t.rows_per_task <= 256 && t.rows_per_task % 8 == 0 &&
-         t.reseed_interval >= 1 && t.reseed_interval <= kMaxPQ;
+  const bool k_ok = t.kernels == 0 || t.kernels == 4 || (t.kernels == 1 && elem == 8);
+  return g_ok && k_ok && t.rows_per_task >= 8 && t.rows_per_task <= 256 &&
+         t.rows_per_task % 8 == 0 && t.reseed_interval >= 1 && t.reseed_interval <= kMaxPQ;
 }
 
 cov_status cov_tuning_get(cov_dtype dtype, int64_t N, int64_t M, int P, int Q, cov_tuning_t *out,
@@ -321,6 +323,7 @@ cov_status cov_tuning_get(cov_dtype dtype, int64_t N, int64_t M, int P, int Q, c
   out->lag_group = p.G;
   out->rows_per_task = p.TRB;
   out->reseed_interval = p.L;
+  out->kernels = p.fused ? 1 : 4;
   return COV_OK;
 }
 
@@ -331,7 +334,7 @@ cov_status cov_tuning_set(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
   const int elem = dtype == COV_C128 ? 16 : 8;
   if (t && !tuning_valid(*t, elem)) return COV_EINVAL;
   if (t) {
-    const Tuning k = {t->lag_group, t->rows_per_task, t->reseed_interval};
+    const Tuning k = {t->lag_group, t->rows_per_task, t->reseed_interval, t->kernels};
     store_tuning(elem, N, M, P, Q, device_sms(), &k);
   } else {
     store_tuning(elem, N, M, P, Q, device_sms(), nullptr);
@@ -381,9 +384,9 @@ cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
     WsLayout ws;
     plan_recurrence(N, M, lda, P, Q, elem, sms, p, ws, &cand);
     if (ws.total > ws_bytes) return -1.f;
-    const Tuning eff = {p.G, p.TRB, p.L};
+    const Tuning eff = {p.G, p.TRB, p.L, p.fused ? 1 : 4};
     for (const Tuning &k : seen)
-      if (k.G == eff.G && k.TRB == eff.TRB && k.L == eff.L) return -1.f;
+      if (k.G == eff.G && k.TRB == eff.TRB && k.L == eff.L && k.K == eff.K) return -1.f;
     seen.push_back(eff);
     cov_status st = run_recurrence(A, elem, N, M, lda, P, Q, R, COV_MEAN, workspace, ws_bytes,
                                    sms, s, &eff, nullptr);
@@ -405,13 +408,13 @@ cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
   RecParams p0;
   WsLayout ws0;
   plan_recurrence(N, M, lda, P, Q, elem, sms, p0, ws0, nullptr);
-  Tuning bestt = {0, 0, 0};
+  Tuning bestt = {0, 0, 0, 0};
   float bestv = -1.f;
   // stage 1: lags per group and rows per task (the product kernel)
   for (int gi = 0; gi < 3 && err == COV_OK; ++gi) {
     if (kTuneG[gi] == 16 && elem == 16) continue;
     for (int ti = 0; ti < 7 && err == COV_OK; ++ti) {
-      const Tuning c = {kTuneG[gi], kTuneTRB[ti], p0.L};
+      const Tuning c = {kTuneG[gi], kTuneTRB[ti], p0.L, 0};
       const float v = time_one(c);
       if (v > 0.f && (bestv < 0.f || v < bestv)) {
         bestv = v;
@@ -421,7 +424,16 @@ cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
   }
   // stage 2: the walk's re-seed interval at the best stage-1 knobs
   for (int li = 0; li < 5 && err == COV_OK && bestv > 0.f; ++li) {
-    const Tuning c = {bestt.G, bestt.TRB, kTuneL[li]};
+    const Tuning c = {bestt.G, bestt.TRB, kTuneL[li], bestt.K};
+    const float v = time_one(c);
+    if (v > 0.f && v < bestv) {
+      bestv = v;
+      bestt = seen.back();
+    }
+  }
+  // stage 3: the other kernel form (FP32 only)
+  if (err == COV_OK && bestv > 0.f && elem == 8) {
+    const Tuning c = {bestt.G, bestt.TRB, bestt.L, bestt.K == 1 ? 4 : 1};
     const float v = time_one(c);
     if (v > 0.f && v < bestv) {
       bestv = v;
@@ -437,6 +449,7 @@ cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
     best->lag_group = bestt.G;
     best->rows_per_task = bestt.TRB;
     best->reseed_interval = bestt.L;
+    best->kernels = bestt.K;
   }
   if (best_ms) *best_ms = bestv;
   return COV_OK;

@@ -133,9 +133,11 @@ struct RecParams {
   int NFR, NFC;         // 2(P-1), 2(Q-1)
   int GF, ngroups_f, RB, nrb;
   int CWF, NCH;         // inner-column chunk width and count of the fringe-row kernel
+  int FPB;              // its (fringe row, row lag) pairs per CTA (= threads)
   int QMAXF, FPITCH;    // its column-lag register count (>= Q) and smem pitch
   // walk
   int L;                // re-seed interval along the diagonal
+  int fused;            // FP32: run the four stages as one cooperative kernel
   // shard: the column lags dc in [dc_lo, dc_hi) (the R blocks (a, b) with
   // |b - a| in that range); lag groups [g_lo, g_lo + ngroups) and
   // combinations [u_lo, u_hi) are theirs. The full problem is [0, Q).

@@ -39,6 +39,11 @@ cudaError_t launch_reduce(const RecParams &p, bool fp64, cudaStream_t s, bool pd
 cudaError_t launch_walk(const RecParams &p, bool fp64, cudaStream_t s, bool pdl);
 cudaError_t launch_direct(const DirectParams &p, bool c128, cudaStream_t s);
 
+// The same four stages as one cooperative kernel (rec_fused.cu, FP32).
+// cudaErrorNotSupported when it cannot run here (then use the four kernels).
+bool fused_supported(const RecParams &p, bool fp64);
+cudaError_t launch_fused(const RecParams &p, const CUtensorMap &tmap, int num_sms, cudaStream_t s);
+
 // Dense form on tcgen05 (gemm_tc.cu); complex64 input and output.
 bool gemm_shape_ok(long long N, long long M, int P, int Q);
 size_t gemm_workspace_size(long long N, long long M, int P, int Q);

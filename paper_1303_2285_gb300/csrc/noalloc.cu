@@ -89,9 +89,10 @@ extern "C" cov_status cov_estimate_noalloc(const void *A, cov_dtype dtype, int64
   p.sin_part = w + ws.sin_off;
   p.rowval = w + ws.rowval_off;
   p.colval = w + ws.colval_off;
-  // The status word must start at zero; every other scratch region is fully
+  // The status word and the fused kernel's barrier and task counters (the
+  // first 16 bytes) must start at zero; every other scratch region is fully
   // written by the kernels before it is read.
-  if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  if (cudaMemsetAsync(w, 0, 16, s) != cudaSuccess) return COV_ECUDA;
   if (launch_recurrence(p, dtype == COV_C128, sms, s, nullptr) != cudaSuccess) return COV_ECUDA;
   return COV_OK;
 }

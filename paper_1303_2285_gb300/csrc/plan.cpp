@@ -53,7 +53,7 @@ int choose_group(int P, int Q, int elem) {
 
 void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int elem, int sms,
                      RecParams &p, WsLayout &ws, const Tuning *tune) {
-  Tuning t = {0, 0, 0};
+  Tuning t = {0, 0, 0, 0};
   if (tune) t = *tune;
   else lookup_tuning(elem, N, M, P, Q, sms, t);
   memset(&p, 0, sizeof(p));
@@ -85,6 +85,13 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   long long tr_max = rows_max - span;
   if (tr_max < 8) tr_max = 8;
   int TRB = tr_max >= 48 ? 48 : (int)(tr_max / 8) * 8;
+  if (elem == 16 && sms > 0) {
+    // FP64: one SM's FP64 pipe is slow, so shorten the row blocks until the
+    // tasks (about row blocks x column blocks x lag groups) cover twice the
+    // SMs
+    const long long per_rb = (long long)((M + 31) / 32) * p.ngroups;
+    while (TRB > 8 && (long long)((p.n_inner + TRB - 1) / TRB) * per_rb < 2LL * sms) TRB -= 8;
+  }
   if (t.TRB >= 8 && t.TRB % 8 == 0 && t.TRB <= tr_max) TRB = t.TRB;
   if (TRB < 8) TRB = 8;
   int TPT = (int)(tr_max / TRB);
@@ -106,11 +113,15 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.RB = 4;
   p.ngroups_f = n_groups(P, Q, p.GF);
   p.nrb = (P - 1 + p.RB - 1) / p.RB;
-  p.CWF = 32;
+  p.CWF = elem == 16 ? 8 : 16;
+  p.FPB = elem == 16 ? 32 : 256;
   p.NCH = (int)((M - 2LL * Q + 2 + p.CWF - 1) / p.CWF);
   p.QMAXF = Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
   p.FPITCH = ((p.CWF + p.QMAXF - 1 + 14) / 16) * 16 + 1;  // >= CWF+QMAXF-1, = 1 mod 16
   p.L = (t.L >= 1 && t.L <= kMaxPQ) ? t.L : 8;
+  // FP32: one fused kernel by default where the reductions are small (they
+  // run with one CTA per SM there); four kernels otherwise
+  p.fused = elem == 8 && (t.K == 1 || (t.K == 0 && (long long)p.n_uc * p.NFR <= 32768)) ? 1 : 0;
   p.dc_lo = 0;
   p.dc_hi = Q;
   p.g_lo = 0;
@@ -259,10 +270,10 @@ int save_tuning(const char *path) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   FILE *f = fopen(path, "w");
   if (!f) return -1;
-  fprintf(f, "# elem N M P Q sms G TRB L\n");
+  fprintf(f, "# elem N M P Q sms G TRB L K\n");
   for (const TuneEntry &e : g_tune)
-    fprintf(f, "%d %lld %lld %d %d %d %d %d %d\n", e.elem, e.N, e.M, e.P, e.Q, e.sms, e.t.G,
-            e.t.TRB, e.t.L);
+    fprintf(f, "%d %lld %lld %d %d %d %d %d %d %d\n", e.elem, e.N, e.M, e.P, e.Q, e.sms, e.t.G,
+            e.t.TRB, e.t.L, e.t.K);
   return fclose(f) == 0 ? 0 : -1;
 }
 
@@ -273,11 +284,11 @@ int load_tuning(const char *path) {
   int n = 0;
   while (fgets(line, sizeof(line), f)) {
     if (line[0] == '#') continue;
-    int elem, P, Q, sms, G, TRB, L;
+    int elem, P, Q, sms, G, TRB, L, K;
     long long N, M;
-    if (sscanf(line, "%d %lld %lld %d %d %d %d %d %d", &elem, &N, &M, &P, &Q, &sms, &G, &TRB, &L) ==
-        9) {
-      const Tuning t = {G, TRB, L};
+    if (sscanf(line, "%d %lld %lld %d %d %d %d %d %d %d", &elem, &N, &M, &P, &Q, &sms, &G, &TRB, &L,
+               &K) == 10) {
+      const Tuning t = {G, TRB, L, K};
       store_tuning(elem, N, M, P, Q, sms, &t);
       ++n;
     } else {

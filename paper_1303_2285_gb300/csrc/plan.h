@@ -28,9 +28,10 @@ bool recurrence_ok(long long N, long long M, int P, int Q);
 int choose_group(int P, int Q, int elem);
 
 // Tuned knobs of the combination path (0 = the plan's default): lags per
-// group G, rows per product task TRB, walk re-seed interval L.
+// group G, rows per product task TRB, walk re-seed interval L, kernels per
+// call K (1 = the fused cooperative kernel, FP32 only; 4 = four kernels).
 struct Tuning {
-  int G, TRB, L;
+  int G, TRB, L, K;
 };
 
 // Fills every field of p that depends on the shape only (not the pointers);

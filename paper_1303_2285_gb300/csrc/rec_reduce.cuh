@@ -1,0 +1,352 @@
+// Device code of the reduction and walk stages of the combination path (see
+// cov_internal.h), shared by the stand-alone kernels and the fused kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rec_common.cuh"
+
+namespace cov {
+
+// ---------------------------------------------------------------------------
+// Reductions that finish the box sums, one warp per task.
+//  - per combination D: core = sum of the core partials, the fringe-column
+//    sums CS over inner rows, and CV[D][j] = core + the fringe-column sums
+//    inside the box of column offset j (suffix scan over the left fringe
+//    columns, prefix scan over the right ones);
+//  - per (D, fringe row fr): S_in = sum of the row's partials, the row's own
+//    fringe-column products (one per lane, each formed once) and the box-row
+//    sums RV[D][j][fr] = S_in + the fringe-column products inside the box.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+// inclusive scan over lanes k <= lane
+template <typename T> __device__ __forceinline__ T scan_incl(T x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+// inclusive scan over lanes k >= lane
+template <typename T> __device__ __forceinline__ T scan_suffix(T x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = __shfl_down_sync(0xffffffffu, x, o);
+    if (lane + o < 32) x += y;
+  }
+  return x;
+}
+
+// Warp task: CV[D][j] for every column offset j of combination D = the sum
+// of its core partials plus the fringe-column sums (over the inner rows)
+// inside the box of column offset j (suffix scan over the left fringe
+// columns, prefix scan over the right ones).
+template <typename T>
+__device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int lane) {
+  using C2 = typename C2t<T>::type;
+  const int P = p.P, Q = p.Q;
+  int dr, dc;
+  combo_of(P, D, dr, dc);
+  Neu<T> cr, ci;
+  const long long nparts = (long long)p.n_rb * p.n_cb;
+  const C2 *cp = (const C2 *)p.core_part + (long long)D * nparts;
+  for (long long k0 = lane; k0 < nparts; k0 += 8 * 32) {
+    C2 x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = (k0 + 32 * u < nparts) ? cp[k0 + 32 * u] : czero<C2>();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      cr.add(x[u].x);
+      ci.add(x[u].y);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const T s1 = __shfl_xor_sync(0xffffffffu, cr.s, o), c1 = __shfl_xor_sync(0xffffffffu, cr.c, o);
+    const T s2 = __shfl_xor_sync(0xffffffffu, ci.s, o), c2 = __shfl_xor_sync(0xffffffffu, ci.c, o);
+    cr.merge(s1, c1);
+    ci.merge(s2, c2);
+  }
+  // lane k < Q-1: fringe columns m = k (left) and m = W + k (right), each
+  // summed over the row blocks
+  T lr = 0, li = 0, rr = 0, ri = 0;
+  if (lane < Q - 1) {
+    const C2 *csl = (const C2 *)p.colsum_part + ((long long)D * p.NFC + lane) * p.n_rb;
+    const C2 *csr = csl + (long long)(Q - 1) * p.n_rb;
+    Neu<T> a, b, c, d;
+    for (int rb0 = 0; rb0 < p.n_rb; rb0 += 4) {
+      C2 x[4], y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        x[u] = rb0 + u < p.n_rb ? csl[rb0 + u] : czero<C2>();
+        y[u] = rb0 + u < p.n_rb ? csr[rb0 + u] : czero<C2>();
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a.add(x[u].x);
+        b.add(x[u].y);
+        c.add(y[u].x);
+        d.add(y[u].y);
+      }
+    }
+    lr = a.value();
+    li = b.value();
+    rr = c.value();
+    ri = d.value();
+  }
+  const T lsr = scan_suffix(lr, lane), lsi = scan_suffix(li, lane);
+  T rpr = scan_incl(rr, lane), rpi = scan_incl(ri, lane);
+  rpr = __shfl_up_sync(0xffffffffu, rpr, 1);  // exclusive
+  rpi = __shfl_up_sync(0xffffffffu, rpi, 1);
+  if (lane == 0) rpr = rpi = T(0);
+  const int J = Q - dc;
+  if (lane < J) {
+    Neu<T> vr = cr, vi = ci;
+    vr.add(lane < Q - 1 ? lsr : T(0));
+    vi.add(lane < Q - 1 ? lsi : T(0));
+    vr.add(rpr);
+    vi.add(rpi);
+    C2 o;
+    o.x = vr.value();
+    o.y = vi.value();
+    ((C2 *)p.colval)[(long long)D * Q + lane] = o;
+  }
+}
+
+// Rows of fringe rows per RV warp task (their loads are issued together).
+constexpr int kRowsPerTask = 4;
+
+// Warp task: the box-row sums RV[D][j][fr] of the fringe rows
+// fr0 .. fr0+kRowsPerTask-1 (those < NFR) for every column offset j: S_in
+// from the chunk partials plus each row's own fringe-column products (each
+// formed once), with prefix and suffix scans over the fringe columns.
+template <typename T>
+__device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int fr0, int lane) {
+  using C2 = typename C2t<T>::type;
+  constexpr int RF = kRowsPerTask;
+  const int P = p.P, Q = p.Q, W = p.M - p.Q + 1, NFR = p.NFR;
+  int dr, dc;
+  combo_of(P, D, dr, dc);
+  const C2 *A = (const C2 *)p.A;
+  C2 a0[RF], b0[RF], a1[RF], b1[RF];
+  bool has_r[RF];
+  T sr[RF], si[RF];
+  // all loads of the RF rows first
+#pragma unroll
+  for (int f = 0; f < RF; ++f) {
+    const int fr = fr0 + f;
+    const int n = fr < P - 1 ? fr : (p.N - P + 1) + (fr - (P - 1));
+    const bool rowok = fr < NFR && n + dr >= 0 && n + dr < p.N;
+    a0[f] = b0[f] = a1[f] = b1[f] = czero<C2>();
+    has_r[f] = rowok && lane < Q - 1 && W + lane + dc < p.M;
+    if (rowok && lane < Q - 1) {
+      const C2 *An = A + (long long)n * p.lda;
+      const C2 *Ab = A + (long long)(n + dr) * p.lda + dc;
+      a0[f] = __ldg(An + lane);
+      b0[f] = __ldg(Ab + lane);
+      if (has_r[f]) {
+        a1[f] = __ldg(An + W + lane);
+        b1[f] = __ldg(Ab + W + lane);
+      }
+    }
+    sr[f] = si[f] = T(0);
+    if (fr < NFR) {
+      const C2 *sp = (const C2 *)p.sin_part + ((long long)D * NFR + fr) * p.NCH;
+      for (int cc = lane; cc < p.NCH; cc += 32) {
+        const C2 x = sp[cc];
+        sr[f] += x.x;
+        si[f] += x.y;
+      }
+    }
+  }
+  const int J = Q - dc;
+#pragma unroll
+  for (int f = 0; f < RF; ++f) {
+    const int fr = fr0 + f;
+    C2 lft = czero<C2>(), rgt = czero<C2>();
+    cmac_conj(lft, a0[f], b0[f]);
+    if (has_r[f]) cmac_conj(rgt, a1[f], b1[f]);
+    const T s_r = warp_sum(sr[f]), s_i = warp_sum(si[f]);
+    const T lsr = scan_suffix(lft.x, lane), lsi = scan_suffix(lft.y, lane);
+    T rpr = scan_incl(rgt.x, lane), rpi = scan_incl(rgt.y, lane);
+    rpr = __shfl_up_sync(0xffffffffu, rpr, 1);
+    rpi = __shfl_up_sync(0xffffffffu, rpi, 1);
+    if (lane == 0) rpr = rpi = T(0);
+    if (fr < NFR && lane < J) {
+      C2 o;
+      o.x = s_r + (lane < Q - 1 ? lsr : T(0)) + rpr;
+      o.y = s_i + (lane < Q - 1 ? lsi : T(0)) + rpi;
+      ((C2 *)p.rowval)[((long long)D * Q + lane) * NFR + fr] = o;
+    }
+  }
+}
+
+// Reduction warp task w of the shard: [0, n_own) the combinations (CV), then
+// (combination, block of kRowsPerTask fringe rows) pairs (RV).
+__host__ __device__ __forceinline__ long long reduce_tasks(const RecParams &p) {
+  const long long n_own = p.u_hi - p.u_lo;
+  return n_own * (1 + (p.NFR + kRowsPerTask - 1) / kRowsPerTask);
+}
+template <typename T>
+__device__ __forceinline__ void reduce_task(const RecParams &p, long long w, int lane) {
+  const long long n_own = p.u_hi - p.u_lo;
+  if (w < n_own) {
+    reduce_combo_warp<T>(p, p.u_lo + (int)w, lane);
+  } else {
+    const int nb = (p.NFR + kRowsPerTask - 1) / kRowsPerTask;
+    const long long w2 = w - n_own;
+    reduce_rows_warp<T>(p, p.u_lo + (int)(w2 / nb), (int)(w2 % nb) * kRowsPerTask, lane);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block task: the P x P block (bj, bj+dc) of R, which the combinations
+// (dr, dc) own entirely (Fig. 3). The block's box-row sums RV and column
+// values CV are first staged in shared memory. A thread then takes one
+// diagonal segment of one combination (L outputs at most): it seeds with the
+// direct sum over the box, walks down the diagonal (subtract the leaving top
+// fringe row, add the entering bottom fringe row; compensated), divides by K
+// and stages the block; the block and its conjugate mirror are then written
+// row by row (coalesced).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, unsigned char *smem) {
+  using C2 = typename C2t<T>::type;
+  const int P = p.P, D2 = 2 * P - 1, PP = P + 1, NFR = p.NFR;
+  C2 *B = (C2 *)smem;                    // [P][P+1]
+  C2 *RVs = B + P * PP;                  // [2P-1][NFR]
+  C2 *CVs = RVs + D2 * NFR;              // [2P-1]
+  const C2 *rowval = (const C2 *)p.rowval;
+  const C2 *colval = (const C2 *)p.colval;
+  // stage: every thread issues all of its loads before storing any
+  {
+    constexpr int U = 16;  // (2P-1)(2P-2) <= 63*62 < 16*256 <= U*blockDim
+    C2 v[U];
+    const int total = D2 * NFR;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = threadIdx.x + u * (int)blockDim.x;
+      v[u] = czero<C2>();
+      if (idx < total) {
+        const int di = idx / NFR, f = idx - di * NFR, dr = di - (P - 1);
+        if (!(dc == 0 && dr < 0))
+          v[u] = rowval[((long long)combo_index(P, dr, dc) * p.Q + bj) * NFR + f];
+      }
+    }
+    C2 cvv = czero<C2>();
+    if (threadIdx.x < D2) {
+      const int dr = threadIdx.x - (P - 1);
+      if (!(dc == 0 && dr < 0)) cvv = colval[(long long)combo_index(P, dr, dc) * p.Q + bj];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = threadIdx.x + u * (int)blockDim.x;
+      if (idx < total) RVs[idx] = v[u];
+    }
+    if (threadIdx.x < D2) CVs[threadIdx.x] = cvv;
+  }
+  __syncthreads();
+  const int nchunk = (P + p.L - 1) / p.L;
+  for (int t = threadIdx.x; t < D2 * nchunk; t += blockDim.x) {
+    const int dr = t % D2 - (P - 1), c = t / D2;
+    if (dc == 0 && dr < 0) continue;
+    const int adr = dr < 0 ? -dr : dr;
+    const int I = P - adr, i0 = dr < 0 ? -dr : 0;
+    const int is = i0 + c * p.L;
+    if (is >= i0 + I) continue;
+    const int ie = (i0 + I) < (is + p.L) ? (i0 + I) : (is + p.L);
+    const C2 *RV = RVs + (dr + P - 1) * NFR;
+    const C2 cv = CVs[dr + P - 1];
+    // seed: the direct sum over the box of output (is, bj): the top fringe
+    // rows n in [is, P-2] and the bottom fringe rows N-P+1+k, k < is
+    Neu<T> orr, oii;
+    orr.add(cv.x);
+    oii.add(cv.y);
+#pragma unroll
+    for (int n = 0; n < kMaxPQ - 1; ++n)
+      if (n >= is && n <= P - 2) {
+        orr.add(RV[n].x);
+        oii.add(RV[n].y);
+      }
+#pragma unroll
+    for (int k = 0; k < kMaxPQ - 1; ++k)
+      if (k < is) {
+        orr.add(RV[P - 1 + k].x);
+        oii.add(RV[P - 1 + k].y);
+      }
+    for (int i = is; i < ie; ++i) {
+      T re = orr.value(), im = oii.value();
+      if (p.mean) {
+        if (p.div_double) {
+          re = (T)((double)re / (double)p.K);
+          im = (T)((double)im / (double)p.K);
+        } else {
+          re = re / (T)p.K;
+          im = im / (T)p.K;
+        }
+      }
+      if (dr == 0 && dc == 0) im = T(0);
+      C2 o;
+      o.x = re;
+      o.y = im;
+      B[i * PP + i + dr] = o;
+      if (i + 1 < ie) {  // walk: row i leaves the box, row i+N-P+1 enters
+        orr.add(-RV[i].x);
+        oii.add(-RV[i].y);
+        orr.add(RV[P - 1 + i].x);
+        oii.add(RV[P - 1 + i].y);
+      }
+    }
+  }
+  __syncthreads();
+  const long long DD = (long long)P * p.Q;
+  C2 *R = (C2 *)p.R;
+  const long long ra = (long long)P * bj, cb = (long long)P * (bj + dc);
+  if (dc > 0) {
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+      const int i = e / P, ii = e - i * P;
+      R[(ra + i) * DD + cb + ii] = B[i * PP + ii];
+    }
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+      const int ii = e / P, i = e - ii * P;
+      C2 v = B[i * PP + ii];
+      v.y = -v.y;
+      R[(cb + ii) * DD + ra + i] = v;
+    }
+  } else {
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+      const int i = e / P, ii = e - i * P;
+      C2 v;
+      if (ii >= i) {
+        v = B[i * PP + ii];
+      } else {
+        v = B[ii * PP + i];
+        v.y = -v.y;
+      }
+      if (i == ii) v.y = T(0);
+      R[(ra + i) * DD + ra + ii] = v;
+    }
+  }
+}
+
+// Blocks (bj, bj + dc) of the shard's column lags, in launch order.
+__device__ __forceinline__ void walk_block_of(const RecParams &p, int b, int &dc, int &bj) {
+  dc = p.dc_lo;
+  while (b >= p.Q - dc) {
+    b -= p.Q - dc;
+    ++dc;
+  }
+  bj = b;
+}
+
+// Size of walk_block's shared memory.
+template <typename T> __host__ __device__ constexpr size_t walk_smem_bytes(int P, int NFR) {
+  return ((size_t)P * (P + 1) + (size_t)(2 * P - 1) * (NFR + 1)) * sizeof(typename C2t<T>::type);
+}
+
+}  // namespace cov

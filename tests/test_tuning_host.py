@@ -22,7 +22,7 @@ def test_defaults_not_cached():
 
 
 def test_set_get_remove():
-    k = {"lag_group": 4, "rows_per_task": 24, "reseed_interval": 4}
+    k = {"lag_group": 4, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4}
     cov.tuning_set("c64", 300, 200, 8, 6, k)
     got, cached = cov.tuning_get("c64", 300, 200, 8, 6)
     assert cached and got == k
@@ -34,12 +34,12 @@ def test_set_get_remove():
 
 
 @pytest.mark.parametrize("bad", [
-    {"lag_group": 5, "rows_per_task": 24, "reseed_interval": 4},
-    {"lag_group": 8, "rows_per_task": 20, "reseed_interval": 4},
-    {"lag_group": 8, "rows_per_task": 0, "reseed_interval": 4},
-    {"lag_group": 8, "rows_per_task": 264, "reseed_interval": 4},
-    {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 0},
-    {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 33},
+    {"lag_group": 5, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4},
+    {"lag_group": 8, "rows_per_task": 20, "reseed_interval": 4, "kernels": 4},
+    {"lag_group": 8, "rows_per_task": 0, "reseed_interval": 4, "kernels": 4},
+    {"lag_group": 8, "rows_per_task": 264, "reseed_interval": 4, "kernels": 4},
+    {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 0, "kernels": 4},
+    {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 33, "kernels": 4},
 ])
 def test_invalid_knobs_rejected(bad):
     with pytest.raises(cov.CovError) as e:
@@ -47,18 +47,32 @@ def test_invalid_knobs_rejected(bad):
     assert e.value.code == 1
 
 
+def test_kernels_knob():
+    with pytest.raises(cov.CovError):
+        cov.tuning_set("c64", 300, 200, 8, 6,
+                       {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 4, "kernels": 2})
+    with pytest.raises(cov.CovError):  # the fused kernel is FP32 only
+        cov.tuning_set("c128", 300, 200, 8, 6,
+                       {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 4, "kernels": 1})
+    cov.tuning_set("c64", 300, 200, 8, 6,
+                   {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 4, "kernels": 0})
+    assert cov.tuning_get("c64", 300, 200, 8, 6)[0]["kernels"] == 1  # default: fused
+    assert cov.tuning_get("c64", 2048, 512, 32, 32)[0]["kernels"] == 4  # large reductions
+    assert cov.tuning_get("c128", 300, 200, 8, 6)[0]["kernels"] == 4
+
+
 def test_fp64_lag_group_16_rejected():
     with pytest.raises(cov.CovError):
         cov.tuning_set("c128", 300, 200, 8, 6,
-                       {"lag_group": 16, "rows_per_task": 24, "reseed_interval": 4})
+                       {"lag_group": 16, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4})
     cov.tuning_set("c64", 300, 200, 8, 6,
-                   {"lag_group": 16, "rows_per_task": 24, "reseed_interval": 4})
+                   {"lag_group": 16, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4})
 
 
 def test_unsupported_shape():
     with pytest.raises(cov.CovError) as e:
         cov.tuning_set("c64", 10, 10, 8, 8,
-                       {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 4})
+                       {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4})
     assert e.value.code == 5
 
 
@@ -67,13 +81,13 @@ def test_planner_honours_rows_per_task():
     # so fewer rows per task means a larger workspace
     base = cov.workspace_size("c64", 1024, 1024, 16, 16, "recurrence")
     cov.tuning_set("c64", 1024, 1024, 16, 16,
-                   {"lag_group": 8, "rows_per_task": 16, "reseed_interval": 8})
+                   {"lag_group": 8, "rows_per_task": 16, "reseed_interval": 8, "kernels": 1})
     small = cov.workspace_size("c64", 1024, 1024, 16, 16, "recurrence")
     assert small > base
     assert cov.tuning_get("c64", 1024, 1024, 16, 16)[0]["rows_per_task"] == 16
     # the planner clamps rows_per_task to what a shared-memory tile holds
     cov.tuning_set("c64", 1024, 1024, 32, 32,
-                   {"lag_group": 8, "rows_per_task": 256, "reseed_interval": 8})
+                   {"lag_group": 8, "rows_per_task": 256, "reseed_interval": 8, "kernels": 1})
     assert cov.tuning_get("c64", 1024, 1024, 32, 32)[0]["rows_per_task"] < 256
 
 
@@ -87,8 +101,8 @@ def test_autotune_workspace_bound():
 
 
 def test_save_load_round_trip(tmp_path):
-    a = {"lag_group": 4, "rows_per_task": 32, "reseed_interval": 2}
-    b = {"lag_group": 8, "rows_per_task": 64, "reseed_interval": 16}
+    a = {"lag_group": 4, "rows_per_task": 32, "reseed_interval": 2, "kernels": 1}
+    b = {"lag_group": 8, "rows_per_task": 64, "reseed_interval": 16, "kernels": 4}
     cov.tuning_set("c64", 512, 256, 12, 10, a)
     cov.tuning_set("c128", 100, 90, 5, 7, b)
     f = tmp_path / "tune.txt"
