@@ -85,6 +85,12 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
       int RS = 1;
       while (RS < kBMaxRS && ng * n_cb * RS < 2 * kBWarps && n_inner >= 16 * RS * 2) RS *= 2;
       // ---- A: products over inner rows -------------------------------------
+      // Packed FP32x2 FMA with direct and cross accumulator pairs (as the
+      // single-matrix product kernel). Loads use clamped addresses instead of
+      // predicates: a lane past the last column reads column M-1 and its sums
+      // are dropped; a lane whose partner column m+dc is past M zeroes its a
+      // values (no valid product); partner rows past N-1 occur only for the
+      // unused lag slots of the last group, whose sums are dropped.
       const int nA = ng * n_cb * RS;
       for (int t = warp; t < nA; t += kBWarps) {
         const int rs = t % RS, cb = (t / RS) % n_cb, g = t / (RS * n_cb);
@@ -94,28 +100,42 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
         const int r_end = inner_lo + (int)((long long)n_inner * (rs + 1) / RS);
         const int m = cb * 32 + lane;
         const bool mok = m < M, bok = m + dc < M;
-        float2 acc[kBG];
+        const int ma = mok ? m : M - 1, mb = bok ? m + dc : M - 1;
+        const unsigned long long amask = bok ? ~0ull : 0ull;
+        const unsigned long long *ua = (const unsigned long long *)A;
+        unsigned long long accd[kBG], accx[kBG];
 #pragma unroll
-        for (int k = 0; k < kBG; ++k) acc[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < kBG; ++k) accd[k] = accx[k] = 0ull;
         for (int n = r_beg; n < r_end; n += 8) {
-          float2 a[8];
+          const int nv = r_end - n;  // valid a rows of this chunk (>= 8 except the last)
+          unsigned long long a[8], as[8];
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
-            a[r] = (mok && n + r < r_end) ? ld2(A + (long long)(n + r) * lda + m) : make_float2(0.f, 0.f);
-          float2 bv[8 + kBG - 1];
+          for (int r = 0; r < 8; ++r) {
+            const int row = n + r < r_end ? n + r : r_end - 1;
+            a[r] = (r < nv ? __ldg(ua + (long long)row * lda + ma) : 0ull) & amask;
+            as[r] = swap2(a[r]);
+          }
+          const int b0 = n + d0;
+          const bool clamp = b0 + 8 + kBG - 1 > N;
 #pragma unroll
           for (int k = 0; k < 8 + kBG - 1; ++k) {
-            const int row = n + d0 + k;
-            bv[k] = (bok && row >= 0 && row < N) ? ld2(A + (long long)row * lda + m + dc)
-                                                  : make_float2(0.f, 0.f);
-          }
-#pragma unroll
-          for (int k = 0; k < 8 + kBG - 1; ++k)
+            const int row = clamp ? min(b0 + k, N - 1) : b0 + k;
+            const unsigned long long b = __ldg(ua + (long long)row * lda + mb);
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
               const int gg = k - r;
-              if (gg >= 0 && gg < kBG) cmac_conj(acc[gg], a[r], bv[k]);
+              if (gg >= 0 && gg < kBG) {
+                ffma2(accd[gg], a[r], b);
+                ffma2(accx[gg], as[r], b);
+              }
             }
+          }
+        }
+        float2 acc[kBG];
+#pragma unroll
+        for (int k = 0; k < kBG; ++k) {
+          const float2 dd = upk2(accd[k]), xx = upk2(accx[k]);
+          acc[k] = make_float2(dd.x + dd.y, xx.x - xx.y);
         }
         const bool inner = m >= Q - 1 && m <= M - Q;
         if (mok && !inner) {
@@ -181,79 +201,69 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
       }
       __syncthreads();
       // ---- C: CV per combination, RV per (combination, fringe row) ---------
+      // one thread per value set: suffix sums over the left fringe columns,
+      // prefix sums over the right ones, as running sums
       const int nC = nD * (1 + NFR);
-      for (int t = warp; t < nC; t += kBWarps) {
+      for (int t = threadIdx.x; t < nC; t += blockDim.x) {
         const int dl = t % nD, kind = t / nD;  // kind 0: CV, kind 1+fr: RV of fringe row fr
         const int dr = dl + dr_lo, J = Q - dc;
         if (kind == 0) {
           Neu<float> cr, ci;
-          for (int k = lane; k < n_cb * RS; k += 32) {
+          for (int k = 0; k < n_cb * RS; ++k) {
             const float2 x = S.core[dl][k / RS][k % RS];
             cr.add(x.x);
             ci.add(x.y);
           }
-#pragma unroll
-          for (int o = 16; o >= 1; o >>= 1) {
-            const float s1 = __shfl_xor_sync(0xffffffffu, cr.s, o), c1 = __shfl_xor_sync(0xffffffffu, cr.c, o);
-            const float s2 = __shfl_xor_sync(0xffffffffu, ci.s, o), c2 = __shfl_xor_sync(0xffffffffu, ci.c, o);
-            cr.merge(s1, c1);
-            ci.merge(s2, c2);
-          }
-          float lr = 0.f, li = 0.f, rr = 0.f, ri = 0.f;
-          if (lane < Q - 1) {
+          // left fringe columns k = Q-2 .. j (suffix), then right ones k < j
+          float2 suf = make_float2(0.f, 0.f);
+          for (int k = Q - 2; k >= 0; --k) {
+            float2 l = make_float2(0.f, 0.f);
             for (int rs = 0; rs < RS; ++rs) {
-              lr += S.cs[dl][lane][rs].x;
-              li += S.cs[dl][lane][rs].y;
-              rr += S.cs[dl][Q - 1 + lane][rs].x;
-              ri += S.cs[dl][Q - 1 + lane][rs].y;
+              l.x += S.cs[dl][k][rs].x;
+              l.y += S.cs[dl][k][rs].y;
             }
+            suf.x += l.x;
+            suf.y += l.y;
+            if (k < J) S.cv[dl][k] = suf;
           }
-          // suffix sums over the left fringe columns, prefix over the right
-          float lsr = lr, lsi = li, rpr = rr, rpi = ri;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const float a1 = __shfl_down_sync(0xffffffffu, lsr, o), a2 = __shfl_down_sync(0xffffffffu, lsi, o);
-            const float b1 = __shfl_up_sync(0xffffffffu, rpr, o), b2 = __shfl_up_sync(0xffffffffu, rpi, o);
-            if (lane + o < 32) { lsr += a1; lsi += a2; }
-            if (lane >= o) { rpr += b1; rpi += b2; }
-          }
-          rpr = __shfl_up_sync(0xffffffffu, rpr, 1);
-          rpi = __shfl_up_sync(0xffffffffu, rpi, 1);
-          if (lane == 0) rpr = rpi = 0.f;
-          if (lane < J) {
+          if (Q - 1 < J) S.cv[dl][Q - 1] = make_float2(0.f, 0.f);
+          float2 pre = make_float2(0.f, 0.f);
+          for (int j = 0; j < J; ++j) {
             Neu<float> vr = cr, vi = ci;
-            vr.add(lane < Q - 1 ? lsr : 0.f);
-            vi.add(lane < Q - 1 ? lsi : 0.f);
-            vr.add(rpr);
-            vi.add(rpi);
-            S.cv[dl][lane] = make_float2(vr.value(), vi.value());
+            vr.add(S.cv[dl][j].x);
+            vi.add(S.cv[dl][j].y);
+            vr.add(pre.x);
+            vi.add(pre.y);
+            S.cv[dl][j] = make_float2(vr.value(), vi.value());
+            if (j < Q - 1) {
+              for (int rs = 0; rs < RS; ++rs) {
+                pre.x += S.cs[dl][Q - 1 + j][rs].x;
+                pre.y += S.cs[dl][Q - 1 + j][rs].y;
+              }
+            }
           }
         } else {
           const int fr = kind - 1;
           const int n = fr < P - 1 ? fr : (N - P + 1) + (fr - (P - 1));
           const bool rowok = n + dr >= 0 && n + dr < N;
-          float2 lft = make_float2(0.f, 0.f), rgt = make_float2(0.f, 0.f);
-          if (rowok && lane < Q - 1) {
-            const float2 *An = A + (long long)n * lda;
-            const float2 *Ab = A + (long long)(n + dr) * lda + dc;
-            cmac_conj(lft, ld2(An + lane), ld2(Ab + lane));
-            if (W + lane + dc < M) cmac_conj(rgt, ld2(An + W + lane), ld2(Ab + W + lane));
-          }
-          float lsr = lft.x, lsi = lft.y, rpr = rgt.x, rpi = rgt.y;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const float a1 = __shfl_down_sync(0xffffffffu, lsr, o), a2 = __shfl_down_sync(0xffffffffu, lsi, o);
-            const float b1 = __shfl_up_sync(0xffffffffu, rpr, o), b2 = __shfl_up_sync(0xffffffffu, rpi, o);
-            if (lane + o < 32) { lsr += a1; lsi += a2; }
-            if (lane >= o) { rpr += b1; rpi += b2; }
-          }
-          rpr = __shfl_up_sync(0xffffffffu, rpr, 1);
-          rpi = __shfl_up_sync(0xffffffffu, rpi, 1);
-          if (lane == 0) rpr = rpi = 0.f;
           const float2 si = rowok ? S.sin[dl][fr] : make_float2(0.f, 0.f);
-          if (lane < J)
-            S.rv[dl][lane][fr] = make_float2(si.x + (lane < Q - 1 ? lsr : 0.f) + rpr,
-                                             si.y + (lane < Q - 1 ? lsi : 0.f) + rpi);
+          const float2 *An = A + (long long)n * lda;
+          const float2 *Ab = A + (long long)(rowok ? n + dr : 0) * lda + dc;
+          // own left fringe-column products, suffix sums
+          float2 suf = make_float2(0.f, 0.f);
+          for (int k = Q - 2; k >= 0; --k) {
+            if (rowok) cmac_conj(suf, ld2(An + k), ld2(Ab + k));
+            if (k < J) S.rv[dl][k][fr] = make_float2(si.x + suf.x, si.y + suf.y);
+          }
+          if (Q - 1 < J) S.rv[dl][Q - 1][fr] = si;
+          // own right fringe-column products, prefix sums
+          float2 pre = make_float2(0.f, 0.f);
+          for (int j = 1; j < J; ++j) {
+            const int k = j - 1;
+            if (rowok && W + k + dc < M) cmac_conj(pre, ld2(An + W + k), ld2(Ab + W + k));
+            S.rv[dl][j][fr].x += pre.x;
+            S.rv[dl][j][fr].y += pre.y;
+          }
         }
       }
       __syncthreads();

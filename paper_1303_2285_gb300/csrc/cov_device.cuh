@@ -29,6 +29,28 @@ __device__ __forceinline__ void cmac_conj(C2 &acc, const C2 &a, const C2 &b) {
   acc.y = fma_rn(-a.x, b.y, acc.y);
 }
 
+// Packed FP32x2: two floats in one 64-bit register pair, and the paired FMA
+// (fma.rn.f32x2: both halves rounded as two fma.rn.f32).
+__device__ __forceinline__ unsigned long long pk2(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ void ffma2(unsigned long long &acc, unsigned long long a,
+                                      unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+// (ar, ai) -> (ai, ar)
+__device__ __forceinline__ unsigned long long swap2(unsigned long long a) {
+  const float2 v = upk2(a);
+  return pk2(v.y, v.x);
+}
+
 // Compensated (Neumaier) running sum: the error of each addition is kept in c.
 template <typename T> struct Neu {
   T s, c;

@@ -80,20 +80,6 @@ __device__ __forceinline__ void product_chunk(const typename C2t<T>::type *sa,
 // so that a * conj(b) summed over the rows is (d.x + d.y, x.x - x.y). b is
 // used exactly as it sits in shared memory (no repacking per load); only a's
 // swapped pair is formed, once per row for all G lags.
-__device__ __forceinline__ unsigned long long pk2(float x, float y) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-  return r;
-}
-__device__ __forceinline__ float2 upk2(unsigned long long r) {
-  float2 v;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-  return v;
-}
-__device__ __forceinline__ void ffma2(unsigned long long &acc, unsigned long long a,
-                                      unsigned long long b) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
 
 template <int G, int R, int PITCH, bool MASKED>
 __device__ __forceinline__ void product_chunk_f2(const float2 *sa, const float2 *sb, int valid,
@@ -105,8 +91,7 @@ __device__ __forceinline__ void product_chunk_f2(const float2 *sa, const float2 
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     a[r] = (!MASKED || r < valid) ? ua[r * PITCH] : 0ull;
-    const float2 v = upk2(a[r]);
-    as[r] = pk2(v.y, v.x);
+    as[r] = swap2(a[r]);
   }
 #pragma unroll
   for (int k = 0; k < R + G - 1; ++k) {

@@ -105,10 +105,18 @@ cudaError_t launch_recurrence(const RecParams &p, bool fp64, int num_sms, cudaSt
   };
   const bool pdl = !inst;
   cudaError_t e;
-  if (!inst && q.fused && fused_supported(q, fp64)) {
+  if (q.fused && fused_supported(q, fp64)) {
+    // one kernel: with stage events, event 0 before it and events 1-4 after
+    if ((e = mark(0)) != cudaSuccess) return e;
     e = launch_fused(q, tmap, num_sms, s);
-    if (e != cudaErrorNotSupported) return e;
-    cudaGetLastError();  // not co-residentable here: the four kernels below
+    if (e != cudaErrorNotSupported) {
+      if (e != cudaSuccess) return e;
+      for (int k = 1; k <= 4; ++k)
+        if ((e = mark(k)) != cudaSuccess) return e;
+      if (inst) ++ev->calls;
+      return cudaSuccess;
+    }
+    cudaGetLastError();  // not co-resident here: the four kernels below
   }
   if ((e = mark(0)) != cudaSuccess) return e;
   if (q.n_inner > 0 && q.n_tasks > 0 && (e = launch_products_any(q, tmap, fp64, num_sms, s)) != cudaSuccess)
