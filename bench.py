@@ -488,6 +488,8 @@ def bench_ours(args, rank, world, local):
         line["rows"] = extras(args, cov, torch, np, wl, mk_events, stream)
         line["rows"]["batched_4096_uneven_f32"] = bench_batched(cov, torch, np, wl, mk_events, stream,
                                                                 fp32_peak)
+        line["rows"]["apertures_100x100_of_25x25_w10_f32"] = bench_apertures(
+            cov, torch, np, wl, mk_events, stream, fp32_peak)
         line["rows"]["diff_b64_256x256_w12_f32"] = bench_adjoint(cov, torch, np, wl, mk_events, stream,
                                                                  fp32_peak)
         line["rows"]["gemm_tf32x3_" + DEFAULT_WORKLOAD] = bench_gemm(cov, torch, np, wl, mk_events, stream)
@@ -539,6 +541,37 @@ def bench_batched(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
             "fp32_fma_frac": 8.0 * um / (ms * 1e-3) / fp32_peak,
             "input_bytes": sum(N * M * 8 for N, M, _, _ in shapes),
             "err_vs_fp64_direct_rel_fro_max_of_8": max(errs), "graph_captured": True}
+
+
+def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
+    """Every 25 x 25 aperture at stride 10 of a 1015 x 1015 image (100 x 100
+    apertures), 10 x 10 window, read in place by one graph-captured launch."""
+    H = W = 1015
+    img = torch.from_numpy(wl.complex_normal((H, W), 77, "c64")).cuda()
+    plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        plan.run(ws, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(ws, stream=s)
+    torch.cuda.synchronize()
+    n = 10
+    ev = mk_events(2 * n)
+    for k in range(n):
+        ev[2 * k].record(stream)
+        g.replay()
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    cov.check_device_status(ws)
+    ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n)) / n
+    um = R.shape[0] * cov.plan_info(25, 25, 10, 10)["distinct_products"]
+    return {"apertures": R.shape[0], "ms_per_launch": ms, "apertures_per_s": R.shape[0] / (ms * 1e-3),
+            "distinct_products_per_s": um / (ms * 1e-3), "fp32_fma_frac": 8.0 * um / (ms * 1e-3) / fp32_peak,
+            "r_bytes": R.numel() * 8, "graph_captured": True}
 
 
 def bench_adjoint(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:

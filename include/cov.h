@@ -268,6 +268,19 @@ typedef struct {
 
 typedef struct cov_batched_plan cov_batched_plan;
 
+/* Apertures of one image (the image-processing use of Section 2.3: one
+ * covariance matrix per overlapping aperture). Fills descs[k] (HOST, up to
+ * max_count entries) for the ap_n x ap_m apertures at rows a*step_r and
+ * columns b*step_c of the H x W image (device, leading dimension ld), in
+ * row-major order of (a, b): A points into the image in place (lda = ld; no
+ * copies), R = R + k * (PQ)^2 complex elements (device, caller-owned,
+ * count * (PQ)^2 elements). *count = the number of apertures; with
+ * descs == NULL only *count is set. Host only; pass the result to
+ * cov_batched_plan_create. */
+cov_status cov_aperture_descs(const void *image, cov_dtype dtype, int64_t H, int64_t W, int64_t ld,
+                              int ap_n, int ap_m, int step_r, int step_c, int P, int Q, void *R,
+                              cov_desc *descs, int max_count, int *count);
+
 /* Validates `count` descriptors (HOST array, copied) and builds the task
  * schedule. Only COV_C64 with COV_RECURRENCE (or COV_AUTO) is supported; every
  * member must satisfy the COV_RECURRENCE shape rule. On success *plan owns

@@ -78,6 +78,8 @@ SIGNATURES = [
     ("cov_batched_plan_create", _I, [ctypes.POINTER(CovDesc), _I, _I, _I, _I,
                                      ctypes.POINTER(_VP)]),
     ("cov_batched_workspace_size", _I, [_VP, ctypes.POINTER(_SZ)]),
+    ("cov_aperture_descs", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _I, _I, _I, _I, _VP,
+                                ctypes.POINTER(CovDesc), _I, ctypes.POINTER(ctypes.c_int)]),
     ("cov_batched_upload", _I, [_VP, _VP, _SZ, _VP]),
     ("cov_estimate_batched", _I, [_VP, _VP, _SZ, _VP]),
     ("cov_batched_plan_destroy", None, [_VP]),
@@ -269,14 +271,19 @@ class BatchedPlan:
     plan keeps the device pointers: the tensors must outlive it.
     """
 
-    def __init__(self, items, norm: str = "mean"):
+    def __init__(self, items, norm: str = "mean", descs=None):
         lib = load()
-        n = len(items)
-        arr = (CovDesc * n)()
-        for k, (A, R, P, Q) in enumerate(items):
-            if not (A.is_cuda and R.is_cuda) or A.stride(1) != 1 or not R.is_contiguous():
-                raise ValueError("A and R must be CUDA tensors (A unit column stride, R contiguous)")
-            arr[k] = CovDesc(A.data_ptr(), R.data_ptr(), A.stride(0), A.shape[0], A.shape[1], P, Q)
+        if descs is not None:  # prepared descriptors (e.g. aperture_batch)
+            arr, n = descs, len(descs)
+        else:
+            n = len(items)
+            arr = (CovDesc * n)()
+            for k, (A, R, P, Q) in enumerate(items):
+                if not (A.is_cuda and R.is_cuda) or A.stride(1) != 1 or not R.is_contiguous():
+                    raise ValueError("A and R must be CUDA tensors (A unit column stride, "
+                                     "R contiguous)")
+                arr[k] = CovDesc(A.data_ptr(), R.data_ptr(), A.stride(0), A.shape[0], A.shape[1],
+                                 P, Q)
         ptr = ctypes.c_void_p()
         _check(lib.cov_batched_plan_create(arr, n, DTYPES["c64"], ALGOS["auto"], NORMS[norm],
                                            ctypes.byref(ptr)), "cov_batched_plan_create")
@@ -298,6 +305,41 @@ class BatchedPlan:
         if getattr(self, "ptr", None) is not None and self.ptr.value:
             self._lib.cov_batched_plan_destroy(self.ptr)
             self.ptr = None
+
+
+def aperture_descs(image_ptr: int, dtype: str, H: int, W: int, ld: int, ap: tuple, step: tuple,
+                   P: int, Q: int, R_ptr: int):
+    """Descriptors of every ap[0] x ap[1] aperture at stride step of an image
+    (device pointers; host-side construction only)."""
+    lib = load()
+    n = ctypes.c_int(0)
+    _check(lib.cov_aperture_descs(None, DTYPES[dtype], H, W, ld, ap[0], ap[1], step[0], step[1],
+                                  P, Q, None, None, 0, ctypes.byref(n)), "cov_aperture_descs")
+    arr = (CovDesc * n.value)()
+    _check(lib.cov_aperture_descs(image_ptr, DTYPES[dtype], H, W, ld, ap[0], ap[1], step[0],
+                                  step[1], P, Q, R_ptr, arr, n.value, ctypes.byref(n)),
+           "cov_aperture_descs")
+    return arr
+
+
+def aperture_batch(image, ap: tuple, step: tuple, P: int, Q: int, norm: str = "mean"):
+    """One batched plan over every aperture of a complex64 CUDA image, read in
+    place: returns (plan, R) with R of shape (count, PQ, PQ); run the plan to
+    fill R (plan.upload once, then plan.run)."""
+    torch = _torch()
+    if not image.is_cuda or image.dtype != torch.complex64 or image.stride(1) != 1:
+        raise ValueError("image must be a complex64 CUDA tensor with unit column stride")
+    H, W = image.shape
+    n = ctypes.c_int(0)
+    _check(load().cov_aperture_descs(None, DTYPES["c64"], H, W, image.stride(0), ap[0], ap[1],
+                                     step[0], step[1], P, Q, None, None, 0, ctypes.byref(n)),
+           "cov_aperture_descs")
+    R = torch.empty((n.value, P * Q, P * Q), dtype=torch.complex64, device=image.device)
+    arr = aperture_descs(image.data_ptr(), "c64", H, W, image.stride(0), ap, step, P, Q,
+                         R.data_ptr())
+    plan = BatchedPlan(None, norm=norm, descs=arr)
+    plan._keep = (image, R)
+    return plan, R
 
 
 def set_stage_events(events) -> None:

@@ -359,6 +359,35 @@ cov_status cov_partition_matrices(const cov_desc *descs, int count, int n_ranks,
   return COV_OK;
 }
 
+cov_status cov_aperture_descs(const void *image, cov_dtype dtype, int64_t H, int64_t W, int64_t ld,
+                              int ap_n, int ap_m, int step_r, int step_c, int P, int Q, void *R,
+                              cov_desc *descs, int max_count, int *count) {
+  if (!count || H < 1 || W < 1 || ld < W || ap_n < 1 || ap_m < 1 || ap_n > H || ap_m > W ||
+      step_r < 1 || step_c < 1 || P < 1 || Q < 1 || P > ap_n || Q > ap_m || max_count < 0 ||
+      (dtype != COV_C64 && dtype != COV_C128))
+    return COV_EINVAL;
+  const long long nr = (H - ap_n) / step_r + 1, nc = (W - ap_m) / step_c + 1;
+  if (nr * nc > (1LL << 30)) return COV_EINVAL;
+  *count = (int)(nr * nc);
+  if (!descs) return COV_OK;  // size query
+  if (!image || !R || max_count < *count) return COV_EINVAL;
+  const size_t elem = dtype == COV_C128 ? 16 : 8;
+  const size_t rbytes = (size_t)P * Q * P * Q * elem;
+  for (long long a = 0; a < nr; ++a)
+    for (long long b = 0; b < nc; ++b) {
+      const long long k = a * nc + b;
+      cov_desc &d = descs[k];
+      d.A = (const char *)image + ((size_t)(a * step_r) * ld + (size_t)(b * step_c)) * elem;
+      d.R = (char *)R + (size_t)k * rbytes;
+      d.lda = ld;
+      d.N = ap_n;
+      d.M = ap_m;
+      d.P = P;
+      d.Q = Q;
+    }
+  return COV_OK;
+}
+
 cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype, cov_algo algo,
                                    cov_norm norm, cov_batched_plan **plan) {
   if (!descs || count < 1 || !plan || (norm != COV_MEAN && norm != COV_SUM)) return COV_EINVAL;

@@ -1,0 +1,50 @@
+"""Host-side construction of the aperture descriptors (every overlapping
+aperture of one image, read in place): counts, pointer offsets, strides and
+argument checks. No device memory is touched."""
+import ctypes
+
+import pytest
+
+import paper_1303_2285_gb300 as cov
+
+
+def test_count_and_offsets():
+    img, R = 0x10000000, 0x20000000
+    H, W, ld = 64, 80, 96
+    arr = cov.aperture_descs(img, "c64", H, W, ld, (25, 20), (10, 7), 5, 4, R)
+    nr, nc = (H - 25) // 10 + 1, (W - 20) // 7 + 1
+    assert len(arr) == nr * nc
+    for a in range(nr):
+        for b in range(nc):
+            d = arr[a * nc + b]
+            assert d.A == img + ((a * 10) * ld + b * 7) * 8
+            assert d.R == R + (a * nc + b) * (20 * 20) * 8
+            assert (d.lda, d.N, d.M, d.P, d.Q) == (ld, 25, 20, 5, 4)
+
+
+def test_c128_element_size():
+    arr = cov.aperture_descs(0x1000, "c128", 10, 10, 10, (5, 5), (5, 5), 2, 2, 0x9000)
+    assert len(arr) == 4
+    assert arr[3].A == 0x1000 + (5 * 10 + 5) * 16
+    assert arr[3].R == 0x9000 + 3 * 16 * 16
+
+
+@pytest.mark.parametrize("H,W,ld,an,am,sr,sc,P,Q", [
+    (5, 30, 30, 30, 10, 1, 1, 2, 2),     # aperture taller than the image
+    (30, 30, 29, 10, 10, 1, 1, 2, 2),    # ld < W
+    (30, 30, 30, 10, 10, 0, 1, 2, 2),    # zero step
+    (30, 30, 30, 10, 10, 1, 1, 11, 2),   # P > aperture rows
+])
+def test_argument_checks(H, W, ld, an, am, sr, sc, P, Q):
+    n = ctypes.c_int(0)
+    assert cov.load().cov_aperture_descs(None, 0, H, W, ld, an, am, sr, sc, P, Q, None, None, 0,
+                                         ctypes.byref(n)) == 1
+
+
+def test_too_small_output_array():
+    lib = cov.load()
+    n = ctypes.c_int(0)
+    arr = (cov.CovDesc * 2)()
+    assert lib.cov_aperture_descs(0x1000, 0, 30, 30, 30, 10, 10, 10, 10, 2, 2, 0x2000, arr, 2,
+                                  ctypes.byref(n)) == 1
+    assert n.value == 9
