@@ -44,6 +44,13 @@ cudaError_t launch_direct(const DirectParams &p, bool c128, cudaStream_t s);
 bool fused_supported(const RecParams &p, bool fp64);
 cudaError_t launch_fused(const RecParams &p, const CUtensorMap &tmap, int num_sms, cudaStream_t s);
 
+// 2-D tiled tensor map (FLOAT64 or FLOAT32 elements; out-of-bounds reads are
+// zero): dim0 innermost. False if the driver entry point is missing or the
+// encode fails (alignment, box limits).
+bool encode_tiled_2d(CUtensorMap &map, bool f64, const void *base, unsigned long long dim0,
+                     unsigned long long dim1, unsigned long long row_bytes, unsigned box0,
+                     unsigned box1);
+
 // Dense form on tcgen05 (gemm_tc.cu); complex64 input and output.
 bool gemm_shape_ok(long long N, long long M, int P, int Q);
 size_t gemm_workspace_size(long long N, long long M, int P, int Q);
