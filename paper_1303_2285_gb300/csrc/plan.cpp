@@ -113,7 +113,7 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.RB = 4;
   p.ngroups_f = n_groups(P, Q, p.GF);
   p.nrb = (P - 1 + p.RB - 1) / p.RB;
-  p.CWF = elem == 16 ? 8 : 16;
+  p.CWF = elem == 16 ? 8 : 32;
   p.FPB = elem == 16 ? 32 : 256;
   p.NCH = (int)((M - 2LL * Q + 2 + p.CWF - 1) / p.CWF);
   p.QMAXF = Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;

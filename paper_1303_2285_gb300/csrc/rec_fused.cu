@@ -73,7 +73,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
   const long long tb = NT * blockIdx.x / gridDim.x;
   const long long te = NT * (blockIdx.x + 1) / gridDim.x;
   bool ok = true;
-  if (p.n_inner > 0) ok = products_phase<float, G, 8, PITCH, NCW>(p, tmap, smem_f, tb, te);
+  if (p.n_inner > 0) ok = products_phase<float, G, 16, PITCH, NCW>(p, tmap, smem_f, tb, te);
   ok = __syncthreads_and(ok) != 0;
   if (threadIdx.x == 0 && p.n_inner > 0 && tb < te) {
     // the barriers' memory is reused below
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
 template <int G, int PITCH, int QMAX>
 static cudaError_t launch_fused_t(const RecParams &p, const CUtensorMap &tmap, int num_sms,
                                   cudaStream_t s) {
-  constexpr int NCW = G == 16 ? 12 : 16;  // as the stand-alone product kernel
+  constexpr int NCW = 12;  // as the stand-alone product kernel
   auto kern = k_fused<G, PITCH, NCW, QMAX>;
   size_t smem = 2 * tile_buf_bytes<float, PITCH>(p.STR) + 64;
   const size_t fs = (size_t)(2 * p.P - 2) * p.FPITCH * sizeof(float2);

@@ -26,10 +26,12 @@ constexpr int kConsumerWarps = 16;
 template <typename T, int G, int PITCH>
 static cudaError_t launch_products_p(const RecParams &p, const CUtensorMap &tmap, int num_sms,
                                      cudaStream_t s) {
-  // 16 lags keep two FP32 accumulator pairs each: 12 consumer warps leave
-  // them 150 registers a thread
-  constexpr int NCW = (sizeof(T) == 4 && G == 16) ? 12 : kConsumerWarps;
-  auto kern = k_products_inner<T, G, 8, PITCH, NCW>;
+  // FP32: 16 rows per register block (each shared-memory load then feeds
+  // more FMAs; the loads are within a factor two of the FMA time), 12
+  // consumer warps for the registers of two accumulator pairs per lag
+  constexpr bool f32 = sizeof(T) == 4;
+  constexpr int NCW = f32 ? 12 : kConsumerWarps;
+  auto kern = k_products_inner<T, G, f32 ? 16 : 8, PITCH, NCW>;
   const size_t smem = 2 * tile_buf_bytes<T, PITCH>(p.STR) + 64;
   cudaError_t e = ensure_smem_attr(kern, smem);
   if (e != cudaSuccess) return e;

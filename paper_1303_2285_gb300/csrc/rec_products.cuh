@@ -133,11 +133,18 @@ __device__ __forceinline__ void product_task(const RecParams &p, long long tile,
     unsigned long long accd[G], accx[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) accd[k] = accx[k] = 0ull;
+    // Full R-row chunks, then 8-row chunks: a chunk at row r0 reads b rows up
+    // to r0 + (chunk rows) + G - 2 past the task's first row, which stays in
+    // the tile (and its halo) only while r0 + chunk rows <= TRB; TRB is a
+    // multiple of 8, not necessarily of R.
+    static_assert(R % 8 == 0, "row blocks are multiples of 8");
     int r0 = 0;
     for (; r0 + R <= rows; r0 += R)
       product_chunk_f2<G, R, PITCH, false>(Sa + r0 * PITCH, Sb + r0 * PITCH, R, accd, accx);
+    for (; r0 + 8 <= rows; r0 += 8)
+      product_chunk_f2<G, 8, PITCH, false>(Sa + r0 * PITCH, Sb + r0 * PITCH, 8, accd, accx);
     if (r0 < rows)
-      product_chunk_f2<G, R, PITCH, true>(Sa + r0 * PITCH, Sb + r0 * PITCH, rows - r0, accd,
+      product_chunk_f2<G, 8, PITCH, true>(Sa + r0 * PITCH, Sb + r0 * PITCH, rows - r0, accd,
                                           accx);
 #pragma unroll
     for (int k = 0; k < G; ++k) {

@@ -118,8 +118,9 @@ __device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int
   }
 }
 
-// Rows of fringe rows per RV warp task (their loads are issued together).
-constexpr int kRowsPerTask = 4;
+// Fringe rows per RV warp task (their loads are issued together). One row
+// a task measured fastest: more warps in flight beat longer tasks.
+constexpr int kRowsPerTask = 1;
 
 // Warp task: the box-row sums RV[D][j][fr] of the fringe rows
 // fr0 .. fr0+kRowsPerTask-1 (those < NFR) for every column offset j: S_in
