@@ -37,16 +37,19 @@ FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
 FALLBACK_SM_MAX_MHZ = 2070.0
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic per launch of the product kernel from one ncu capture, keyed
-# by a hash of the kernel source at capture time (null when it has changed).
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# the production kernel from one ncu capture, keyed by (workload, kernel,
+# hash of the library sources at capture time): null once they have changed.
 NCU_TRAFFIC = {}
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("recurrence.cu", "cov_device.cuh", "cov_internal.h", "plan.cpp"):
-        with open(os.path.join(ROOT, "paper_1303_2285_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_1303_2285_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -270,7 +273,12 @@ def bench_ours(args, rank, world, local):
     info = cov.plan_info(w.N, w.M, w.P, w.Q)
     um = info["distinct_products"]
     tune_ms, source = None, "defaults"
-    if args.tuning_file and os.path.exists(args.tuning_file):
+    if args.knobs:
+        g_, trb_, l_, k_ = (int(x) for x in args.knobs.split(","))
+        cov.tuning_set(w.dtype, w.N, w.M, w.P, w.Q, {"lag_group": g_, "rows_per_task": trb_,
+                                                     "reseed_interval": l_, "kernels": k_})
+        source = "given"
+    elif args.tuning_file and os.path.exists(args.tuning_file):
         cov.tuning_load(args.tuning_file)
         source = "file"
     elif args.autotune:
@@ -718,6 +726,41 @@ def extras(args, cov, torch, np, wl, mk_events, stream) -> dict:
     return out
 
 
+def profile_case(case: str) -> int:
+    """Small cases of the secondary kernels for ncu captures: 600 uneven
+    matrices through the batched launch (seed 3), the dense TF32x3 form on the
+    bench workload, the adjoint of one 256 x 256 input with a 12 x 12 window."""
+    import torch
+
+    import cov_workloads as wl
+    import paper_1303_2285_gb300 as cov
+    if case == "batched":
+        items = []
+        for k, (N, M, P, Q) in enumerate(wl.batched_shapes(600, wl.BATCHED_SEED)):
+            A = torch.from_numpy(wl.complex_normal((N, M), wl.BATCHED_SEED * 100003 + k, "c64")).cuda()
+            items.append((A, torch.empty((P * Q, P * Q), dtype=torch.complex64, device="cuda"), P, Q))
+        plan = cov.BatchedPlan(items)
+        ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+        plan.upload(ws)
+        for _ in range(3):
+            plan.run(ws)
+    elif case == "gemm":
+        w = wl.WORKLOADS[DEFAULT_WORKLOAD]
+        A = torch.from_numpy(wl.workload_input(w)).cuda()
+        for _ in range(2):
+            cov.estimate(A, w.P, w.Q, algo="gemm_tf32x3")
+    else:
+        N = M = 256
+        P = Q = 12
+        A = torch.from_numpy(wl.complex_normal((N, M), 4, "c64")).cuda()
+        G = torch.from_numpy(wl.complex_normal((P * Q, P * Q), 5, "c64")).cuda()
+        for _ in range(3):
+            cov.estimate_backward(A, G, P, Q)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": case, "ok": True}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -732,9 +775,17 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false", default=True)
     ap.add_argument("--tuning-file", default=None,
                     help="load the knobs from this file if it exists, else autotune and save them")
+    ap.add_argument("--knobs", default=None,
+                    help="G,TRB,L,K: use these knobs (lag group, rows per task, re-seed interval, "
+                         "kernels 1|4) instead of autotuning")
+    ap.add_argument("--profile-case", choices=("batched", "gemm", "adjoint"), default=None,
+                    help="run a few launches of one secondary kernel on a small case (for ncu) "
+                         "and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_case:
+        return profile_case(args.profile_case)
     rank, world, local = dist_setup()
     if args.impl == "reference":
         return bench_reference(args, rank, world)
