@@ -41,12 +41,17 @@ namespace cov {
 
 constexpr int kBMaxPQ = 16;      // P, Q <= 16
 constexpr int kBMaxM = 512;      // M <= 512 (16 column blocks)
-constexpr int kBMaxD = 2 * kBMaxPQ - 1;   // combinations per dc
+constexpr int kBMaxD = 2 * kBMaxPQ - 1;   // combinations per column lag
 constexpr int kBMaxF = 2 * (kBMaxPQ - 1); // fringe rows / columns
 constexpr int kBMaxCB = kBMaxM / 32;
 constexpr int kBMaxRS = 4;       // row ranges of phase A
 constexpr int kBWarps = 16;
 constexpr int kBG = 8;           // lags per group
+// shared memory: the per-combination arrays of one pass, for the largest
+// member (P = Q = 16, M = 512: one column lag, 31 combinations)
+constexpr size_t kBSmemBytes =
+    (size_t)kBMaxD *
+    (kBMaxCB * kBMaxRS + kBMaxF * kBMaxRS + kBMaxF + kBMaxPQ + kBMaxPQ * kBMaxF) * sizeof(float2);
 
 struct BDesc {
   const float2 *A;
@@ -55,20 +60,40 @@ struct BDesc {
   int N, M, P, Q;
 };
 
-struct BSmem {
-  float2 core[kBMaxD][kBMaxCB][kBMaxRS];
-  float2 cs[kBMaxD][kBMaxF][kBMaxRS];
-  float2 sin[kBMaxD][kBMaxF];
-  float2 cv[kBMaxD][kBMaxPQ];
-  float2 rv[kBMaxD][kBMaxPQ][kBMaxF];
-};
-
 __device__ __forceinline__ float2 ld2(const float2 *p) { return __ldg(p); }
+
+// Combinations of a pass over the column lags [dc_a, dc_b): dc = 0 has P
+// (dr = 0..P-1), every other dc 2P-1 (dr = -(P-1)..P-1), in dc order.
+struct BPass {
+  int P, dc_a, dc_b, n0;  // n0: combinations of dc_a (P if dc_a == 0)
+  __device__ __forceinline__ int first(int dc) const {  // local index of (dr_lo(dc), dc)
+    return dc == dc_a ? 0 : n0 + (dc - dc_a - 1) * (2 * P - 1);
+  }
+  __device__ __forceinline__ void of(int dl, int &dr, int &dc) const {
+    if (dl < n0) {
+      dc = dc_a;
+    } else {
+      dc = dc_a + 1 + (dl - n0) / (2 * P - 1);
+    }
+    const int lo = dc ? -(P - 1) : 0;
+    dr = lo + dl - first(dc);
+  }
+  // group index over the pass (ng0 groups for dc_a, ng1 for each other dc)
+  __device__ __forceinline__ void group(int gi, int ng0, int ng1, int &dc, int &g) const {
+    if (gi < ng0) {
+      dc = dc_a;
+      g = gi;
+    } else {
+      dc = dc_a + 1 + (gi - ng0) / ng1;
+      g = (gi - ng0) % ng1;
+    }
+  }
+};
 
 __global__ void __launch_bounds__(kBWarps * 32, 1)
     k_batched(const BDesc *descs, const int *order, const int *cta_begin, int mean) {
   extern __shared__ __align__(16) unsigned char smem_b[];
-  BSmem &S = *(BSmem *)smem_b;
+  float2 *pool = (float2 *)smem_b;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int mi = cta_begin[blockIdx.x]; mi < cta_begin[blockIdx.x + 1]; ++mi) {
     const BDesc d = descs[order[mi]];
@@ -79,11 +104,25 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
     const int n_cb = (M + 31) / 32, NFR = 2 * (P - 1), NFC = 2 * (Q - 1), W = M - Q + 1;
     const long long K = (long long)(N - P + 1) * (M - Q + 1);
     const long long DD = (long long)P * Q;
-    for (int dc = 0; dc < Q; ++dc) {
-      const int dr_lo = dc ? -(P - 1) : 0;
-      const int nD = P - dr_lo, ng = (nD + kBG - 1) / kBG;
-      int RS = 1;
-      while (RS < kBMaxRS && ng * n_cb * RS < 2 * kBWarps && n_inner >= 16 * RS * 2) RS *= 2;
+    // row ranges of phase A: as many as keep 4 row chunks each (at most 4)
+    int RS = 1;
+    while (RS < kBMaxRS && n_inner >= 32 * RS * 2) RS *= 2;
+    // per-combination shared arrays (float2): core [n_cb][RS], cs [NFC][RS],
+    // sin [NFR], cv [Q], rv [Q][NFR]
+    const int per = n_cb * RS + NFC * RS + NFR + Q + Q * NFR;
+    const int cap = (int)(kBSmemBytes / sizeof(float2)) / per;  // combinations per pass
+    for (int dc_a = 0; dc_a < Q;) {
+      // as many whole column lags as fit
+      int dc_b = dc_a, nDp = 0;
+      while (dc_b < Q && nDp + (dc_b ? 2 * P - 1 : P) <= cap) nDp += dc_b++ ? 2 * P - 1 : P;
+      const BPass ps = {P, dc_a, dc_b, dc_a ? 2 * P - 1 : P};
+      float2 *core = pool;
+      float2 *cs = core + nDp * n_cb * RS;
+      float2 *sinp = cs + nDp * NFC * RS;
+      float2 *cv = sinp + nDp * NFR;
+      float2 *rv = cv + nDp * Q;
+      const int ng0 = (ps.n0 + kBG - 1) / kBG, ng1 = (2 * P - 1 + kBG - 1) / kBG;
+      const int ngp = ng0 + (dc_b - dc_a - 1) * ng1;  // groups of the pass
       // ---- A: products over inner rows -------------------------------------
       // Packed FP32x2 FMA with direct and cross accumulator pairs (as the
       // single-matrix product kernel). Loads use clamped addresses instead of
@@ -91,11 +130,15 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
       // are dropped; a lane whose partner column m+dc is past M zeroes its a
       // values (no valid product); partner rows past N-1 occur only for the
       // unused lag slots of the last group, whose sums are dropped.
-      const int nA = ng * n_cb * RS;
+      const int nA = ngp * n_cb * RS;
       for (int t = warp; t < nA; t += kBWarps) {
-        const int rs = t % RS, cb = (t / RS) % n_cb, g = t / (RS * n_cb);
+        const int rs = t % RS, cb = (t / RS) % n_cb, gi = t / (RS * n_cb);
+        int dc, g;
+        ps.group(gi, ng0, ng1, dc, g);
+        const int dr_lo = dc ? -(P - 1) : 0;
         const int d0 = dr_lo + g * kBG;
         const int cnt = min(kBG, P - d0);
+        const int dl0 = ps.first(dc) + g * kBG;
         const int r_beg = inner_lo + (int)((long long)n_inner * rs / RS);
         const int r_end = inner_lo + (int)((long long)n_inner * (rs + 1) / RS);
         const int m = cb * 32 + lane;
@@ -142,7 +185,7 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           const int fc = m < Q - 1 ? m : m - (M - 2 * Q + 2);
 #pragma unroll
           for (int k = 0; k < kBG; ++k)
-            if (k < cnt) S.cs[d0 + k - dr_lo][fc][rs] = acc[k];
+            if (k < cnt) cs[((dl0 + k) * NFC + fc) * RS + rs] = acc[k];
         }
         float v[2 * kBG];
 #pragma unroll
@@ -153,15 +196,19 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
         warp_transpose_reduce<2 * kBG>(v, lane);  // lane holds value index lane >> 1
         if ((lane & 1) == 0) {
           const int k = lane >> 2, comp = (lane >> 1) & 1;
-          if (k < cnt) ((float *)&S.core[d0 + k - dr_lo][cb][rs])[comp] = v[0];
+          if (k < cnt) ((float *)&core[((dl0 + k) * n_cb + cb) * RS + rs])[comp] = v[0];
         }
       }
       // ---- B: fringe rows x inner columns ---------------------------------
       const int nrb = (P - 1 + 3) / 4;
-      const int nB = 2 * nrb * ng;
+      const int nB = 2 * nrb * ngp;
       for (int t = warp; t < nB; t += kBWarps) {
-        const int g = t % ng, rb = (t / ng) % nrb, side = t / (ng * nrb);
+        const int gi = t % ngp, rb = (t / ngp) % nrb, side = t / (ngp * nrb);
+        int dc, g;
+        ps.group(gi, ng0, ng1, dc, g);
+        const int dr_lo = dc ? -(P - 1) : 0;
         const int d0 = dr_lo + g * kBG, cnt = min(kBG, P - d0);
+        const int dl0 = ps.first(dc) + g * kBG;
         const int fr0 = rb * 4, nrows = min(4, P - 1 - fr0);
         const int nbase = side == 0 ? fr0 : (N - P + 1) + fr0;
         float2 acc[4][kBG];
@@ -197,48 +244,52 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           }
         warp_transpose_reduce<2 * 4 * kBG>(v, lane);  // lane holds complex index lane
         const int r = lane / kBG, k = lane % kBG;
-        if (r < nrows && k < cnt) S.sin[d0 + k - dr_lo][side * (P - 1) + fr0 + r] = make_float2(v[0], v[1]);
+        if (r < nrows && k < cnt) sinp[(dl0 + k) * NFR + side * (P - 1) + fr0 + r] = make_float2(v[0], v[1]);
       }
       __syncthreads();
       // ---- C: CV per combination, RV per (combination, fringe row) ---------
       // one thread per value set: suffix sums over the left fringe columns,
       // prefix sums over the right ones, as running sums
-      const int nC = nD * (1 + NFR);
+      const int nC = nDp * (1 + NFR);
       for (int t = threadIdx.x; t < nC; t += blockDim.x) {
-        const int dl = t % nD, kind = t / nD;  // kind 0: CV, kind 1+fr: RV of fringe row fr
-        const int dr = dl + dr_lo, J = Q - dc;
+        const int dl = t % nDp, kind = t / nDp;  // kind 0: CV, kind 1+fr: RV of fringe row fr
+        int dr, dc;
+        ps.of(dl, dr, dc);
+        const int J = Q - dc;
+        float2 *cvd = cv + dl * Q;
         if (kind == 0) {
           Neu<float> cr, ci;
+          const float2 *cd = core + dl * n_cb * RS;
           for (int k = 0; k < n_cb * RS; ++k) {
-            const float2 x = S.core[dl][k / RS][k % RS];
-            cr.add(x.x);
-            ci.add(x.y);
+            cr.add(cd[k].x);
+            ci.add(cd[k].y);
           }
+          const float2 *csd = cs + dl * NFC * RS;
           // left fringe columns k = Q-2 .. j (suffix), then right ones k < j
           float2 suf = make_float2(0.f, 0.f);
           for (int k = Q - 2; k >= 0; --k) {
             float2 l = make_float2(0.f, 0.f);
             for (int rs = 0; rs < RS; ++rs) {
-              l.x += S.cs[dl][k][rs].x;
-              l.y += S.cs[dl][k][rs].y;
+              l.x += csd[k * RS + rs].x;
+              l.y += csd[k * RS + rs].y;
             }
             suf.x += l.x;
             suf.y += l.y;
-            if (k < J) S.cv[dl][k] = suf;
+            if (k < J) cvd[k] = suf;
           }
-          if (Q - 1 < J) S.cv[dl][Q - 1] = make_float2(0.f, 0.f);
+          if (Q - 1 < J) cvd[Q - 1] = make_float2(0.f, 0.f);
           float2 pre = make_float2(0.f, 0.f);
           for (int j = 0; j < J; ++j) {
             Neu<float> vr = cr, vi = ci;
-            vr.add(S.cv[dl][j].x);
-            vi.add(S.cv[dl][j].y);
+            vr.add(cvd[j].x);
+            vi.add(cvd[j].y);
             vr.add(pre.x);
             vi.add(pre.y);
-            S.cv[dl][j] = make_float2(vr.value(), vi.value());
+            cvd[j] = make_float2(vr.value(), vi.value());
             if (j < Q - 1) {
               for (int rs = 0; rs < RS; ++rs) {
-                pre.x += S.cs[dl][Q - 1 + j][rs].x;
-                pre.y += S.cs[dl][Q - 1 + j][rs].y;
+                pre.x += csd[(Q - 1 + j) * RS + rs].x;
+                pre.y += csd[(Q - 1 + j) * RS + rs].y;
               }
             }
           }
@@ -246,44 +297,47 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           const int fr = kind - 1;
           const int n = fr < P - 1 ? fr : (N - P + 1) + (fr - (P - 1));
           const bool rowok = n + dr >= 0 && n + dr < N;
-          const float2 si = rowok ? S.sin[dl][fr] : make_float2(0.f, 0.f);
+          const float2 si = rowok ? sinp[dl * NFR + fr] : make_float2(0.f, 0.f);
           const float2 *An = A + (long long)n * lda;
           const float2 *Ab = A + (long long)(rowok ? n + dr : 0) * lda + dc;
+          float2 *rvd = rv + dl * Q * NFR + fr;  // rv[dl][j][fr] at rvd[j * NFR]
           // own left fringe-column products, suffix sums
           float2 suf = make_float2(0.f, 0.f);
           for (int k = Q - 2; k >= 0; --k) {
             if (rowok) cmac_conj(suf, ld2(An + k), ld2(Ab + k));
-            if (k < J) S.rv[dl][k][fr] = make_float2(si.x + suf.x, si.y + suf.y);
+            if (k < J) rvd[k * NFR] = make_float2(si.x + suf.x, si.y + suf.y);
           }
-          if (Q - 1 < J) S.rv[dl][Q - 1][fr] = si;
+          if (Q - 1 < J) rvd[(Q - 1) * NFR] = si;
           // own right fringe-column products, prefix sums
           float2 pre = make_float2(0.f, 0.f);
           for (int j = 1; j < J; ++j) {
             const int k = j - 1;
             if (rowok && W + k + dc < M) cmac_conj(pre, ld2(An + W + k), ld2(Ab + W + k));
-            S.rv[dl][j][fr].x += pre.x;
-            S.rv[dl][j][fr].y += pre.y;
+            rvd[j * NFR].x += pre.x;
+            rvd[j * NFR].y += pre.y;
           }
         }
       }
       __syncthreads();
       // ---- D: seed, walk, write -------------------------------------------
-      const int J = Q - dc;
-      for (int t = threadIdx.x; t < nD * J; t += blockDim.x) {
-        const int dl = t % nD, j = t / nD;
-        const int dr = dl + dr_lo;
+      for (int t = threadIdx.x; t < nDp * Q; t += blockDim.x) {
+        const int dl = t % nDp, j = t / nDp;
+        int dr, dc;
+        ps.of(dl, dr, dc);
+        if (j >= Q - dc) continue;
         const int adr = dr < 0 ? -dr : dr;
         const int i0 = dr < 0 ? -dr : 0, I = P - adr;
+        const float2 *rvj = rv + (dl * Q + j) * NFR;
         Neu<float> orr, oii;
-        orr.add(S.cv[dl][j].x);
-        oii.add(S.cv[dl][j].y);
+        orr.add(cv[dl * Q + j].x);
+        oii.add(cv[dl * Q + j].y);
         for (int n = i0; n <= P - 2; ++n) {
-          orr.add(S.rv[dl][j][n].x);
-          oii.add(S.rv[dl][j][n].y);
+          orr.add(rvj[n].x);
+          oii.add(rvj[n].y);
         }
         for (int k = 0; k < i0; ++k) {
-          orr.add(S.rv[dl][j][P - 1 + k].x);
-          oii.add(S.rv[dl][j][P - 1 + k].y);
+          orr.add(rvj[P - 1 + k].x);
+          oii.add(rvj[P - 1 + k].y);
         }
         for (int i = i0; i < i0 + I; ++i) {
           float re = orr.value(), im = oii.value();
@@ -301,14 +355,15 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           d.R[a * DD + b] = make_float2(re, im);
           if (a != b) d.R[b * DD + a] = make_float2(re, -im);
           if (i + 1 < i0 + I) {  // walk: row i leaves the box, row i+N-P+1 enters
-            orr.add(-S.rv[dl][j][i].x);
-            oii.add(-S.rv[dl][j][i].y);
-            orr.add(S.rv[dl][j][P - 1 + i].x);
-            oii.add(S.rv[dl][j][P - 1 + i].y);
+            orr.add(-rvj[i].x);
+            oii.add(-rvj[i].y);
+            orr.add(rvj[P - 1 + i].x);
+            oii.add(rvj[P - 1 + i].y);
           }
         }
       }
       __syncthreads();
+      dc_a = dc_b;
     }
   }
 }
@@ -468,7 +523,7 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, s
   if (ws_bytes < plan->total || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   char *w = (char *)workspace;
-  const size_t smem = sizeof(cov::BSmem);
+  const size_t smem = cov::kBSmemBytes;
   static bool attr_done[64] = {false};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return COV_ECUDA;
