@@ -107,8 +107,9 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
     // row ranges of phase A: as many as keep 4 row chunks each (at most 4)
     int RS = 1;
     while (RS < kBMaxRS && n_inner >= 32 * RS * 2) RS *= 2;
-    // per-combination shared arrays (float2): core [n_cb][RS], cs [NFC][RS],
-    // sin [NFR], cv [Q], rv [Q][NFR]
+    // per-pass shared arrays (float2), the pass's combination index dl
+    // fastest (threads of phases C and D take consecutive dl): core
+    // [n_cb*RS][dl], cs [NFC*RS][dl], sin [NFR][dl], cv [Q][dl], rv [Q][NFR][dl]
     const int per = n_cb * RS + NFC * RS + NFR + Q + Q * NFR;
     const int cap = (int)(kBSmemBytes / sizeof(float2)) / per;  // combinations per pass
     for (int dc_a = 0; dc_a < Q;) {
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           const int fc = m < Q - 1 ? m : m - (M - 2 * Q + 2);
 #pragma unroll
           for (int k = 0; k < kBG; ++k)
-            if (k < cnt) cs[((dl0 + k) * NFC + fc) * RS + rs] = acc[k];
+            if (k < cnt) cs[(fc * RS + rs) * nDp + dl0 + k] = acc[k];
         }
         float v[2 * kBG];
 #pragma unroll
@@ -196,12 +197,37 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
         warp_transpose_reduce<2 * kBG>(v, lane);  // lane holds value index lane >> 1
         if ((lane & 1) == 0) {
           const int k = lane >> 2, comp = (lane >> 1) & 1;
-          if (k < cnt) ((float *)&core[((dl0 + k) * n_cb + cb) * RS + rs])[comp] = v[0];
+          if (k < cnt) ((float *)&core[(cb * RS + rs) * nDp + dl0 + k])[comp] = v[0];
         }
       }
       // ---- B: fringe rows x inner columns ---------------------------------
+      // narrow members (few inner columns): one thread per (combination,
+      // fringe row), serial over the inner columns with two accumulators;
+      // otherwise warp tasks (4 rows x 8 lags, lanes over the columns)
+      const int n_ic = M - 2 * Q + 2;
+      const bool narrow = n_ic <= 64;
+      if (narrow) {
+        for (int t = threadIdx.x; t < nDp * NFR; t += blockDim.x) {
+          const int dl = t % nDp, fr = t / nDp;
+          int dr, dc;
+          ps.of(dl, dr, dc);
+          const int n = fr < P - 1 ? fr : (N - P + 1) + (fr - (P - 1));
+          float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+          if (n + dr >= 0 && n + dr < N) {
+            const float2 *An = A + (long long)n * lda + (Q - 1);
+            const float2 *Ab = A + (long long)(n + dr) * lda + (Q - 1) + dc;
+            int m = 0;
+            for (; m + 1 < n_ic; m += 2) {
+              cmac_conj(s0, ld2(An + m), ld2(Ab + m));
+              cmac_conj(s1, ld2(An + m + 1), ld2(Ab + m + 1));
+            }
+            if (m < n_ic) cmac_conj(s0, ld2(An + m), ld2(Ab + m));
+          }
+          sinp[fr * nDp + dl] = make_float2(s0.x + s1.x, s0.y + s1.y);
+        }
+      }
       const int nrb = (P - 1 + 3) / 4;
-      const int nB = 2 * nrb * ngp;
+      const int nB = narrow ? 0 : 2 * nrb * ngp;
       for (int t = warp; t < nB; t += kBWarps) {
         const int gi = t % ngp, rb = (t / ngp) % nrb, side = t / (ngp * nrb);
         int dc, g;
@@ -244,7 +270,8 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           }
         warp_transpose_reduce<2 * 4 * kBG>(v, lane);  // lane holds complex index lane
         const int r = lane / kBG, k = lane % kBG;
-        if (r < nrows && k < cnt) sinp[(dl0 + k) * NFR + side * (P - 1) + fr0 + r] = make_float2(v[0], v[1]);
+        if (r < nrows && k < cnt)
+          sinp[(side * (P - 1) + fr0 + r) * nDp + dl0 + k] = make_float2(v[0], v[1]);
       }
       __syncthreads();
       // ---- C: CV per combination, RV per (combination, fringe row) ---------
@@ -256,40 +283,40 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
         int dr, dc;
         ps.of(dl, dr, dc);
         const int J = Q - dc;
-        float2 *cvd = cv + dl * Q;
+        float2 *cvd = cv + dl;  // cv[j][dl] at cvd[j * nDp]
         if (kind == 0) {
           Neu<float> cr, ci;
-          const float2 *cd = core + dl * n_cb * RS;
           for (int k = 0; k < n_cb * RS; ++k) {
-            cr.add(cd[k].x);
-            ci.add(cd[k].y);
+            const float2 x = core[k * nDp + dl];
+            cr.add(x.x);
+            ci.add(x.y);
           }
-          const float2 *csd = cs + dl * NFC * RS;
+          const float2 *csd = cs + dl;  // cs[fc*RS + rs][dl] at csd[(fc*RS + rs) * nDp]
           // left fringe columns k = Q-2 .. j (suffix), then right ones k < j
           float2 suf = make_float2(0.f, 0.f);
           for (int k = Q - 2; k >= 0; --k) {
             float2 l = make_float2(0.f, 0.f);
             for (int rs = 0; rs < RS; ++rs) {
-              l.x += csd[k * RS + rs].x;
-              l.y += csd[k * RS + rs].y;
+              l.x += csd[(k * RS + rs) * nDp].x;
+              l.y += csd[(k * RS + rs) * nDp].y;
             }
             suf.x += l.x;
             suf.y += l.y;
-            if (k < J) cvd[k] = suf;
+            if (k < J) cvd[k * nDp] = suf;
           }
-          if (Q - 1 < J) cvd[Q - 1] = make_float2(0.f, 0.f);
+          if (Q - 1 < J) cvd[(Q - 1) * nDp] = make_float2(0.f, 0.f);
           float2 pre = make_float2(0.f, 0.f);
           for (int j = 0; j < J; ++j) {
             Neu<float> vr = cr, vi = ci;
-            vr.add(cvd[j].x);
-            vi.add(cvd[j].y);
+            vr.add(cvd[j * nDp].x);
+            vi.add(cvd[j * nDp].y);
             vr.add(pre.x);
             vi.add(pre.y);
-            cvd[j] = make_float2(vr.value(), vi.value());
+            cvd[j * nDp] = make_float2(vr.value(), vi.value());
             if (j < Q - 1) {
               for (int rs = 0; rs < RS; ++rs) {
-                pre.x += csd[(Q - 1 + j) * RS + rs].x;
-                pre.y += csd[(Q - 1 + j) * RS + rs].y;
+                pre.x += csd[((Q - 1 + j) * RS + rs) * nDp].x;
+                pre.y += csd[((Q - 1 + j) * RS + rs) * nDp].y;
               }
             }
           }
@@ -297,24 +324,25 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           const int fr = kind - 1;
           const int n = fr < P - 1 ? fr : (N - P + 1) + (fr - (P - 1));
           const bool rowok = n + dr >= 0 && n + dr < N;
-          const float2 si = rowok ? sinp[dl * NFR + fr] : make_float2(0.f, 0.f);
+          const float2 si = rowok ? sinp[fr * nDp + dl] : make_float2(0.f, 0.f);
           const float2 *An = A + (long long)n * lda;
           const float2 *Ab = A + (long long)(rowok ? n + dr : 0) * lda + dc;
-          float2 *rvd = rv + dl * Q * NFR + fr;  // rv[dl][j][fr] at rvd[j * NFR]
+          float2 *rvd = rv + fr * nDp + dl;  // rv[j][fr][dl] at rvd[j * NFR * nDp]
+          const int RJ = NFR * nDp;
           // own left fringe-column products, suffix sums
           float2 suf = make_float2(0.f, 0.f);
           for (int k = Q - 2; k >= 0; --k) {
             if (rowok) cmac_conj(suf, ld2(An + k), ld2(Ab + k));
-            if (k < J) rvd[k * NFR] = make_float2(si.x + suf.x, si.y + suf.y);
+            if (k < J) rvd[k * RJ] = make_float2(si.x + suf.x, si.y + suf.y);
           }
-          if (Q - 1 < J) rvd[(Q - 1) * NFR] = si;
+          if (Q - 1 < J) rvd[(Q - 1) * RJ] = si;
           // own right fringe-column products, prefix sums
           float2 pre = make_float2(0.f, 0.f);
           for (int j = 1; j < J; ++j) {
             const int k = j - 1;
             if (rowok && W + k + dc < M) cmac_conj(pre, ld2(An + W + k), ld2(Ab + W + k));
-            rvd[j * NFR].x += pre.x;
-            rvd[j * NFR].y += pre.y;
+            rvd[j * RJ].x += pre.x;
+            rvd[j * RJ].y += pre.y;
           }
         }
       }
@@ -327,17 +355,17 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
         if (j >= Q - dc) continue;
         const int adr = dr < 0 ? -dr : dr;
         const int i0 = dr < 0 ? -dr : 0, I = P - adr;
-        const float2 *rvj = rv + (dl * Q + j) * NFR;
+        const float2 *rvj = rv + j * NFR * nDp + dl;  // rv[j][n][dl] at rvj[n * nDp]
         Neu<float> orr, oii;
-        orr.add(cv[dl * Q + j].x);
-        oii.add(cv[dl * Q + j].y);
+        orr.add(cv[j * nDp + dl].x);
+        oii.add(cv[j * nDp + dl].y);
         for (int n = i0; n <= P - 2; ++n) {
-          orr.add(rvj[n].x);
-          oii.add(rvj[n].y);
+          orr.add(rvj[n * nDp].x);
+          oii.add(rvj[n * nDp].y);
         }
         for (int k = 0; k < i0; ++k) {
-          orr.add(rvj[P - 1 + k].x);
-          oii.add(rvj[P - 1 + k].y);
+          orr.add(rvj[(P - 1 + k) * nDp].x);
+          oii.add(rvj[(P - 1 + k) * nDp].y);
         }
         for (int i = i0; i < i0 + I; ++i) {
           float re = orr.value(), im = oii.value();
@@ -355,10 +383,10 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           d.R[a * DD + b] = make_float2(re, im);
           if (a != b) d.R[b * DD + a] = make_float2(re, -im);
           if (i + 1 < i0 + I) {  // walk: row i leaves the box, row i+N-P+1 enters
-            orr.add(-rvj[i].x);
-            oii.add(-rvj[i].y);
-            orr.add(rvj[P - 1 + i].x);
-            oii.add(rvj[P - 1 + i].y);
+            orr.add(-rvj[i * nDp].x);
+            oii.add(-rvj[i * nDp].y);
+            orr.add(rvj[(P - 1 + i) * nDp].x);
+            oii.add(rvj[(P - 1 + i) * nDp].y);
           }
         }
       }
