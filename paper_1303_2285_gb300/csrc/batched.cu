@@ -131,9 +131,11 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
       // are dropped; a lane whose partner column m+dc is past M zeroes its a
       // values (no valid product); partner rows past N-1 occur only for the
       // unused lag slots of the last group, whose sums are dropped.
+      // consecutive warps take the lag groups of one (column block, row range),
+      // so the A block they share stays in L1
       const int nA = ngp * n_cb * RS;
       for (int t = warp; t < nA; t += kBWarps) {
-        const int rs = t % RS, cb = (t / RS) % n_cb, gi = t / (RS * n_cb);
+        const int gi = t % ngp, rs = (t / ngp) % RS, cb = t / (ngp * RS);
         int dc, g;
         ps.group(gi, ng0, ng1, dc, g);
         const int dr_lo = dc ? -(P - 1) : 0;
