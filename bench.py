@@ -597,35 +597,61 @@ def bench_adjoint(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
     plan.run(wsf)
     torch.cuda.synchronize()
     Gs = [(2.0 * (R - T)).contiguous() for R in Rs]
-    wsb = torch.empty(cov.backward_workspace_size(N, M, P, Q), dtype=torch.uint8, device="cuda")
+    wsb = torch.empty(max(cov.backward_workspace_size(N, M, P, Q, "dense"),
+                          cov.backward_workspace_size(N, M, P, Q, "stencil")),
+                      dtype=torch.uint8, device="cuda")
     dAs = [torch.empty_like(A) for A in As]
     lib = cov.load()
     sp = stream.cuda_stream
 
-    def backward_all():
+    form = {"stencil": 2, "dense": 1}
+
+    def backward_all(f="stencil"):
         for A, G, dA in zip(As, Gs, dAs):
-            lib.cov_estimate_backward(A.data_ptr(), G.data_ptr(), 0, N, M, P, Q, 0, dA.data_ptr(),
-                                      wsb.data_ptr(), wsb.numel(), sp)
+            lib.cov_estimate_backward_ex(A.data_ptr(), G.data_ptr(), 0, N, M, P, Q, 0, form[f],
+                                         dA.data_ptr(), wsb.data_ptr(), wsb.numel(), sp)
 
     backward_all()
+    backward_all("dense")
+    torch.cuda.synchronize()
+    # each form's 64 calls captured in one CUDA graph (device time, no host gaps)
+    side = torch.cuda.Stream()
+    graphs = {}
+    for f in ("stencil", "dense"):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            for A, G, dA in zip(As, Gs, dAs):
+                lib.cov_estimate_backward_ex(A.data_ptr(), G.data_ptr(), 0, N, M, P, Q, 0, form[f],
+                                             dA.data_ptr(), wsb.data_ptr(), wsb.numel(),
+                                             side.cuda_stream)
+        graphs[f] = g
+    for g in graphs.values():
+        g.replay()
     torch.cuda.synchronize()
     n = 3
-    ev = mk_events(3 * n)
+    ev = mk_events(4 * n)
     for k in range(n):
-        ev[3 * k].record(stream)
+        ev[4 * k].record(stream)
         plan.run(wsf)
-        ev[3 * k + 1].record(stream)
-        backward_all()
-        ev[3 * k + 2].record(stream)
+        ev[4 * k + 1].record(stream)
+        graphs["stencil"].replay()
+        ev[4 * k + 2].record(stream)
+        graphs["dense"].replay()
+        ev[4 * k + 3].record(stream)
     torch.cuda.synchronize()
-    fwd = sum(ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(n)) / n
-    bwd = sum(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(n)) / n
+    fwd = sum(ev[4 * k].elapsed_time(ev[4 * k + 1]) for k in range(n)) / n
+    bwd = sum(ev[4 * k + 1].elapsed_time(ev[4 * k + 2]) for k in range(n)) / n
+    bwd_dense = sum(ev[4 * k + 2].elapsed_time(ev[4 * k + 3]) for k in range(n)) / n
     D = P * Q
     KW = (N - P + 1) * (M - Q + 1)
-    hx_flops = 8.0 * D * D * KW * B  # complex MACs of Y = H X
-    return {"batch": B, "forward_ms": fwd, "backward_ms": bwd, "forward_plus_backward_ms": fwd + bwd,
-            "backward_hx_tflops": hx_flops / (bwd * 1e-3) / 1e12,
-            "backward_fp32_fma_frac": hx_flops / (bwd * 1e-3) / fp32_peak,
+    ND = (2 * P - 1) * (2 * Q - 1)
+    st_flops = 8.0 * ND * N * M * B     # complex MACs of the stencil (upper bound: full support)
+    hx_flops = 8.0 * D * D * KW * B     # complex MACs of Y = H X
+    return {"batch": B, "forward_ms": fwd, "backward_ms": bwd, "backward_form": "stencil",
+            "forward_plus_backward_ms": fwd + bwd,
+            "backward_fp32_fma_frac": st_flops / (bwd * 1e-3) / fp32_peak,
+            "backward_dense_ms": bwd_dense,
+            "backward_dense_fp32_fma_frac": hx_flops / (bwd_dense * 1e-3) / fp32_peak,
             "workspace_bytes_backward": wsb.numel()}
 
 

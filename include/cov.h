@@ -307,12 +307,33 @@ void cov_batched_plan_destroy(cov_batched_plan *plan);
  * with X recomputed from A (never stored) and a gather-form col2im (one
  * writer per element of dA, no atomics). COV_C64 only.
  * ------------------------------------------------------------------------- */
+/* Two forms of the same dA (equal up to rounding):
+ *   COV_BWD_DENSE    the formula above (H X, (PQ)^2 complex MACs per window);
+ *   COV_BWD_STENCIL  dA[n][m] = sum over combinations Delta = (dr, dc), both
+ *                    signs, of T_Delta * A[n+dr][m+dc], where T_Delta sums
+ *                    H[a][a+Delta] over the window offsets a that a valid
+ *                    window places on (n, m) (a rectangle, so T takes
+ *                    (2P-1)(2Q-1) values per Delta: the paper's combination
+ *                    structure, Sections 3.1-3.3, applied to the adjoint):
+ *                    (2P-1)(2Q-1) complex MACs per element of dA. Needs
+ *                    N >= 2P-1, M >= 2Q-1 and (2P-1)(2Q-1) <= 2048;
+ *   COV_BWD_AUTO     the stencil where it applies, else dense.
+ * The workspace depends on the form. */
+typedef enum { COV_BWD_AUTO = 0, COV_BWD_DENSE = 1, COV_BWD_STENCIL = 2 } cov_bwd_form;
+
 cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P,
                                        int Q, size_t *bytes);
+cov_status cov_backward_workspace_size_ex(cov_dtype dtype, int64_t N, int64_t M, int P,
+                                          int Q, cov_bwd_form form, size_t *bytes);
+/* COV_BWD_AUTO. */
 cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype,
                                  int64_t N, int64_t M, int P, int Q, cov_norm norm,
                                  void *dA, void *workspace, size_t ws_bytes,
                                  cov_stream_t stream);
+cov_status cov_estimate_backward_ex(const void *A, const void *G, cov_dtype dtype,
+                                    int64_t N, int64_t M, int P, int Q, cov_norm norm,
+                                    cov_bwd_form form, void *dA, void *workspace,
+                                    size_t ws_bytes, cov_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Sharding across GPUs (one process per GPU). Section 4.2 gives every

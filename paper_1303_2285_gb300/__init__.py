@@ -85,6 +85,9 @@ SIGNATURES = [
     ("cov_batched_plan_destroy", None, [_VP]),
     ("cov_backward_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
     ("cov_estimate_backward", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _VP, _VP, _SZ, _VP]),
+    ("cov_backward_workspace_size_ex", _I, [_I, _I64, _I64, _I, _I, _I, ctypes.POINTER(_SZ)]),
+    ("cov_estimate_backward_ex", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _I, _VP, _VP, _SZ,
+                                      _VP]),
     ("cov_selftest_timeout", _I, [_VP, _SZ, ctypes.c_uint32, _VP]),
     ("cov_partition_lags", _I, [_I64, _I64, _I, _I, _I, ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_int64)]),
@@ -202,15 +205,21 @@ def estimate(A, P: int, Q: int, algo: str = "auto", norm: str = "mean", workspac
     return estimate_into(A, R, P, Q, algo, norm, workspace, stream)
 
 
-def backward_workspace_size(N: int, M: int, P: int, Q: int) -> int:
+BWD_FORMS = {"auto": 0, "dense": 1, "stencil": 2}
+
+
+def backward_workspace_size(N: int, M: int, P: int, Q: int, form: str = "auto") -> int:
     out = ctypes.c_size_t(0)
-    _check(load().cov_backward_workspace_size(DTYPES["c64"], N, M, P, Q, ctypes.byref(out)),
+    _check(load().cov_backward_workspace_size_ex(DTYPES["c64"], N, M, P, Q, BWD_FORMS[form],
+                                                 ctypes.byref(out)),
            "cov_backward_workspace_size")
     return int(out.value)
 
 
-def estimate_backward(A, G, P: int, Q: int, norm: str = "mean", workspace=None, stream=None):
-    """dL/dA for G = dL/dR (complex64 CUDA tensors; dL/dRe + i dL/dIm convention)."""
+def estimate_backward(A, G, P: int, Q: int, norm: str = "mean", workspace=None, stream=None,
+                      form: str = "auto"):
+    """dL/dA for G = dL/dR (complex64 CUDA tensors; dL/dRe + i dL/dIm convention).
+    ``form``: "auto" (stencil where it applies), "stencil" or "dense"."""
     torch = _torch()
     if not (A.is_cuda and G.is_cuda) or A.dtype != torch.complex64 or G.dtype != torch.complex64:
         raise ValueError("A and G must be complex64 CUDA tensors")
@@ -219,13 +228,14 @@ def estimate_backward(A, G, P: int, Q: int, norm: str = "mean", workspace=None, 
     N, M = A.shape
     if tuple(G.shape) != (P * Q, P * Q):
         raise ValueError("G must be PQ x PQ")
-    need = backward_workspace_size(N, M, P, Q)
+    need = backward_workspace_size(N, M, P, Q, form)
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=A.device)
     dA = torch.empty_like(A)
-    _check(load().cov_estimate_backward(A.data_ptr(), G.data_ptr(), DTYPES["c64"], N, M, P, Q,
-                                        NORMS[norm], dA.data_ptr(), workspace.data_ptr(),
-                                        workspace.numel(), _stream_ptr(stream)),
+    _check(load().cov_estimate_backward_ex(A.data_ptr(), G.data_ptr(), DTYPES["c64"], N, M, P, Q,
+                                           NORMS[norm], BWD_FORMS[form], dA.data_ptr(),
+                                           workspace.data_ptr(), workspace.numel(),
+                                           _stream_ptr(stream)),
            "cov_estimate_backward")
     return dA
 

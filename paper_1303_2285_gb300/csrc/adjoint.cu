@@ -19,6 +19,12 @@
 
 namespace cov {
 
+// stencil form (adjoint_stencil.cu)
+bool stencil_adjoint_ok(long long N, long long M, int P, int Q);
+size_t stencil_adjoint_workspace(int P, int Q);
+cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, long long M, int P,
+                                   int Q, int mean, void *dA, void *workspace, cudaStream_t s);
+
 constexpr int kAdjTA = 48;   // rows a of Y per CTA
 constexpr int kAdjTW = 128;  // windows per CTA (one window row p, consecutive q)
 constexpr int kAdjPQMax = 1024;
@@ -141,27 +147,58 @@ cov_status cov_partition_rows(int64_t N, int P, int n_ranks, int64_t *row_begin,
   return COV_OK;
 }
 
-cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
-                                       size_t *bytes) {
-  if (!bytes || N < 1 || M < 1 || P < 1 || Q < 1 || P > N || Q > M) return COV_EINVAL;
-  if (dtype != COV_C64 || (long long)P * Q > cov::kAdjPQMax) return COV_EUNSUPPORTED;
+static bool bwd_args_ok(int64_t N, int64_t M, int P, int Q) {
+  return N >= 1 && M >= 1 && P >= 1 && Q >= 1 && P <= N && Q <= M && N < (1LL << 30) &&
+         M < (1LL << 30);
+}
+
+// the form AUTO resolves to: the stencil wherever it applies
+static cov_bwd_form resolve_bwd(cov_bwd_form f, int64_t N, int64_t M, int P, int Q) {
+  if (f != COV_BWD_AUTO) return f;
+  return cov::stencil_adjoint_ok(N, M, P, Q) ? COV_BWD_STENCIL : COV_BWD_DENSE;
+}
+
+cov_status cov_backward_workspace_size_ex(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                                          cov_bwd_form form, size_t *bytes) {
+  if (!bytes || !bwd_args_ok(N, M, P, Q)) return COV_EINVAL;
+  if (dtype != COV_C64) return COV_EUNSUPPORTED;
+  form = resolve_bwd(form, N, M, P, Q);
+  if (form == COV_BWD_STENCIL) {
+    if (!cov::stencil_adjoint_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+    *bytes = cov::stencil_adjoint_workspace(P, Q);
+    return COV_OK;
+  }
+  if (form != COV_BWD_DENSE) return COV_EINVAL;
+  if ((long long)P * Q > cov::kAdjPQMax) return COV_EUNSUPPORTED;
   const long long KW = (N - P + 1) * (M - Q + 1);
   *bytes = cov::kWsHeader + (((size_t)P * Q * KW * 8 + 255) & ~(size_t)255);
   return COV_OK;
 }
 
-cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype, int64_t N, int64_t M,
-                                 int P, int Q, cov_norm norm, void *dA, void *workspace,
-                                 size_t ws_bytes, cov_stream_t stream) {
-  if (!A || !G || !dA || N < 1 || M < 1 || P < 1 || Q < 1 || P > N || Q > M ||
-      (norm != COV_MEAN && norm != COV_SUM) || N >= (1LL << 30) || M >= (1LL << 30))
+cov_status cov_backward_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
+                                       size_t *bytes) {
+  return cov_backward_workspace_size_ex(dtype, N, M, P, Q, COV_BWD_AUTO, bytes);
+}
+
+cov_status cov_estimate_backward_ex(const void *A, const void *G, cov_dtype dtype, int64_t N,
+                                    int64_t M, int P, int Q, cov_norm norm, cov_bwd_form form,
+                                    void *dA, void *workspace, size_t ws_bytes, cov_stream_t stream) {
+  if (!A || !G || !dA || !bwd_args_ok(N, M, P, Q) || (norm != COV_MEAN && norm != COV_SUM))
     return COV_EINVAL;
-  if (dtype != COV_C64 || (long long)P * Q > cov::kAdjPQMax) return COV_EUNSUPPORTED;
+  if (dtype != COV_C64) return COV_EUNSUPPORTED;
   if ((((uintptr_t)A) & 7) || (((uintptr_t)G) & 7) || (((uintptr_t)dA) & 7)) return COV_EINVAL;
+  form = resolve_bwd(form, N, M, P, Q);
   size_t need = 0;
-  cov_backward_workspace_size(dtype, N, M, P, Q, &need);
+  const cov_status st = cov_backward_workspace_size_ex(dtype, N, M, P, Q, form, &need);
+  if (st != COV_OK) return st;
   if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(workspace, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  if (form == COV_BWD_STENCIL)
+    return cov::launch_stencil_adjoint(A, G, N, M, P, Q, norm == COV_MEAN ? 1 : 0, dA, workspace,
+                                       s) == cudaSuccess
+               ? COV_OK
+               : COV_ECUDA;
   cov::AdjParams p;
   p.A = (const float2 *)A;
   p.G = (const float2 *)G;
@@ -186,7 +223,6 @@ cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype, 
       return COV_ECUDA;
     attr_done = smem;
   }
-  if (cudaMemsetAsync(workspace, 0, 4, s) != cudaSuccess) return COV_ECUDA;
   const long long nqc = (p.W + cov::kAdjTW - 1) / cov::kAdjTW;
   const long long grid1 = nqc * p.Hn * ((D + cov::kAdjTA - 1) / cov::kAdjTA);
   cov::k_adj_hx<<<(unsigned)grid1, 256, smem, s>>>(p);
@@ -194,6 +230,13 @@ cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype, 
   const long long grid2 = (N * M + 255) / 256;
   cov::k_adj_col2im<<<(unsigned)grid2, 256, 0, s>>>(p);
   return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
+}
+
+cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype, int64_t N, int64_t M,
+                                 int P, int Q, cov_norm norm, void *dA, void *workspace,
+                                 size_t ws_bytes, cov_stream_t stream) {
+  return cov_estimate_backward_ex(A, G, dtype, N, M, P, Q, norm, COV_BWD_AUTO, dA, workspace,
+                                  ws_bytes, stream);
 }
 
 }  // extern "C"

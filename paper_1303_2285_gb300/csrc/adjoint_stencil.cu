@@ -1,0 +1,260 @@
+// Stencil form of the adjoint (not in the paper; it reuses the paper's
+// combination structure, Sections 3.1-3.3, for the derivative of Eq. 2.2).
+//
+// With H = (G + G^H)/K (G + G^H for the plain sum) the dense adjoint is
+//   dA[n][m] = sum over windows w = (p, q) holding (n, m) of (H x_w)[a],
+//   a = (n - p) + P (m - q).
+// Writing b = a + Delta, Delta = (dr, dc) a combination (both signs), gives
+// x_w[b] = A[n + dr][m + dc] for every such window, so
+//   dA[n][m] = sum over Delta of T_Delta(n, m) * A[n + dr][m + dc],
+//   T_Delta(n, m) = sum of H[a][a + Delta] over the a that some valid window
+//                   places on (n, m) and with a + Delta inside the window.
+// The admissible a form the rectangle i_a in I(n), j_a in J(m) with
+// I(n) = [max(0, n - (N-P)), min(P-1, n)], so T depends on (n, m) only through
+// a row class (2P-1 of them: the P-1 top fringe rows, the inner rows, the P-1
+// bottom fringe rows) and a column class (2Q-1). Kernel 1 tabulates
+// T[class][Delta] from FP64 prefix sums of H along each Delta; kernel 2
+// applies the inner-class stencil (a 2-D correlation with (2P-1)(2Q-1)
+// weights) to the inner rows and columns from a staged tile of A; kernel 3
+// takes the fringe elements one by one. Every element of dA has one writer;
+// no atomics. Work: (2P-1)(2Q-1) complex MACs per element instead of (PQ)^2
+// per window.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cov.h"
+#include "cov_device.cuh"
+#include "cov_internal.h"
+
+namespace cov {
+
+constexpr int kStTR = 16;  // output tile of the inner stencil: 16 rows x 32 columns,
+constexpr int kStTC = 32;  // two rows a thread
+
+struct StParams {
+  const float2 *A;
+  const float2 *G;
+  float2 *T;   // [NRC * NCC][ND]
+  float2 *dA;  // N x M, leading dimension M
+  long long lda;
+  int N, M, P, Q, Hn, W;
+  long long K;
+  int mean, NRC, NCC, ND;
+};
+
+// class -> admissible range of the window offset (rows; columns alike)
+__device__ __forceinline__ void class_range(int c, int P, int &lo, int &hi) {
+  if (c < P - 1) {
+    lo = 0;
+    hi = c;
+  } else if (c == P - 1) {
+    lo = 0;
+    hi = P - 1;
+  } else {
+    lo = c - P + 1;
+    hi = P - 1;
+  }
+}
+__device__ __forceinline__ int row_class(int n, int P, int Hn) {
+  return n < P - 1 ? n : (n < Hn ? P - 1 : P + (n - Hn));
+}
+
+// T[(rc * NCC + cc) * ND + Delta], Delta = (dr + P - 1) + (2P - 1)(dc + Q - 1).
+// One CTA per Delta: the P x Q grid h[i][j] = H[(i,j)][(i+dr, j+dc)] (zero
+// where (i+dr, j+dc) leaves the window) is turned into FP64 2-D prefix sums
+// in shared memory; each (row class, column class) entry is then one
+// rectangle sum (four lookups).
+__global__ void __launch_bounds__(256) k_adjs_weights(const StParams p) {
+  extern __shared__ __align__(16) unsigned char smem_w[];
+  const int P = p.P, Q = p.Q, D = P * Q;
+  double2 *S = (double2 *)smem_w;  // [(P+1) x (Q+1)], S[i][j] = sum over i' < i, j' < j
+  const int di = blockIdx.x;
+  const int dr = di % (2 * P - 1) - (P - 1), dc = di / (2 * P - 1) - (Q - 1);
+  for (int e = threadIdx.x; e < (P + 1) * (Q + 1); e += blockDim.x) {
+    const int i = e % (P + 1), j = e / (P + 1);
+    double2 h = make_double2(0.0, 0.0);
+    if (i > 0 && j > 0) {
+      const int ii = i - 1, jj = j - 1;
+      if (ii + dr >= 0 && ii + dr < P && jj + dc >= 0 && jj + dc < Q) {
+        const int a = ii + P * jj, b = (ii + dr) + P * (jj + dc);
+        const float2 g1 = __ldg(p.G + (long long)a * D + b), g2 = __ldg(p.G + (long long)b * D + a);
+        h.x = (double)g1.x + (double)g2.x;  // H[a][b] = G[a][b] + conj(G[b][a])
+        h.y = (double)g1.y - (double)g2.y;
+      }
+    }
+    S[i + (P + 1) * j] = h;
+  }
+  __syncthreads();
+  // prefix sums along i (one thread per column j), then along j (per row i)
+  for (int j = threadIdx.x; j <= Q; j += blockDim.x)
+    for (int i = 1; i <= P; ++i) {
+      S[i + (P + 1) * j].x += S[i - 1 + (P + 1) * j].x;
+      S[i + (P + 1) * j].y += S[i - 1 + (P + 1) * j].y;
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= P; i += blockDim.x)
+    for (int j = 1; j <= Q; ++j) {
+      S[i + (P + 1) * j].x += S[i + (P + 1) * (j - 1)].x;
+      S[i + (P + 1) * j].y += S[i + (P + 1) * (j - 1)].y;
+    }
+  __syncthreads();
+  const double inv = p.mean ? 1.0 / (double)p.K : 1.0;
+  for (int cls = threadIdx.x; cls < p.NRC * p.NCC; cls += blockDim.x) {
+    const int rc = cls / p.NCC, cc = cls - rc * p.NCC;
+    int ilo, ihi, jlo, jhi;
+    class_range(rc, P, ilo, ihi);
+    class_range(cc, Q, jlo, jhi);
+    // rectangle [ilo, ihi] x [jlo, jhi] (invalid cells are zero in h)
+    const double2 s11 = S[(ihi + 1) + (P + 1) * (jhi + 1)], s01 = S[ilo + (P + 1) * (jhi + 1)];
+    const double2 s10 = S[(ihi + 1) + (P + 1) * jlo], s00 = S[ilo + (P + 1) * jlo];
+    const double re = (s11.x - s01.x - s10.x + s00.x) * inv;
+    const double im = (s11.y - s01.y - s10.y + s00.y) * inv;
+    p.T[(long long)cls * p.ND + di] = make_float2((float)re, (float)im);
+  }
+}
+
+// Inner rows [P-1, Hn-1] x inner columns [Q-1, W-1]: one 16 x 32 tile per
+// CTA, the tile of A with its (P-1, Q-1) halo and the inner-class weights in
+// shared memory; thread (ty, tx) computes rows ty and ty+8 of column tx.
+__global__ void __launch_bounds__(256) k_adjs_inner(const StParams p) {
+  extern __shared__ __align__(16) unsigned char smem_st[];
+  const int P = p.P, Q = p.Q;
+  const int SW = kStTC + 2 * Q - 2, SH = kStTR + 2 * P - 2;
+  float2 *As = (float2 *)smem_st;  // [SH][SW]
+  float2 *Ws = As + SH * SW;       // [ND]
+  const int n_in = p.Hn - (P - 1), m_in = p.W - (Q - 1);
+  const int tiles_x = (m_in + kStTC - 1) / kStTC;
+  const int n0 = (P - 1) + (blockIdx.x / tiles_x) * kStTR;
+  const int m0 = (Q - 1) + (blockIdx.x % tiles_x) * kStTC;
+  const float2 *Tin = p.T + (long long)((P - 1) * p.NCC + (Q - 1)) * p.ND;
+  for (int e = threadIdx.x; e < p.ND; e += blockDim.x) Ws[e] = __ldg(Tin + e);
+  for (int e = threadIdx.x; e < SH * SW; e += blockDim.x) {
+    const int r = e / SW, c = e - r * SW;
+    const int gr = n0 - (P - 1) + r, gc = m0 - (Q - 1) + c;
+    As[e] = (gr < p.N && gc < p.M) ? __ldg(p.A + (long long)gr * p.lda + gc) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float2 acc[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int dc = 0; dc < 2 * Q - 1; ++dc) {
+    const float2 *wrow = Ws + dc * (2 * P - 1);
+    const float2 *arow = As + ty * SW + tx + dc;
+    for (int dr = 0; dr < 2 * P - 1; ++dr) {
+      const float2 w = wrow[dr];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {  // acc += w * A[n + dr][m + dc]
+        const float2 a = arow[(dr + 8 * k) * SW];
+        acc[k].x = fma_rn(w.x, a.x, acc[k].x);
+        acc[k].x = fma_rn(-w.y, a.y, acc[k].x);
+        acc[k].y = fma_rn(w.x, a.y, acc[k].y);
+        acc[k].y = fma_rn(w.y, a.x, acc[k].y);
+      }
+    }
+  }
+  const int m = m0 + tx;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int n = n0 + ty + 8 * k;
+    if (n - (P - 1) < n_in && m - (Q - 1) < m_in) p.dA[(long long)n * p.M + m] = acc[k];
+  }
+}
+
+// Fringe elements (outside the inner box), one warp each: lanes take the
+// combinations Delta in turn (coalesced weights of the element's row and
+// column class from the table), then a warp sum.
+__global__ void __launch_bounds__(256) k_adjs_fringe(const StParams p, long long n_fringe) {
+  const long long idx = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (idx >= n_fringe) return;
+  const int P = p.P, Q = p.Q, N = p.N, M = p.M;
+  // enumerate: the P-1 top rows and P-1 bottom rows (all columns), then the
+  // inner rows' Q-1 left and Q-1 right columns
+  const long long top = (long long)(P - 1) * M;
+  int n, m;
+  if (idx < 2 * top) {
+    const long long r = idx / M;
+    m = (int)(idx - r * M);
+    n = r < P - 1 ? (int)r : (int)(p.Hn + (r - (P - 1)));
+  } else {
+    const long long k = idx - 2 * top;
+    const int nf = 2 * (Q - 1);
+    n = (P - 1) + (int)(k / nf);
+    const int c = (int)(k % nf);
+    m = c < Q - 1 ? c : p.W + (c - (Q - 1));
+  }
+  const int rc = row_class(n, P, p.Hn), cc = row_class(m, Q, p.W);
+  const float2 *Tc = p.T + (long long)(rc * p.NCC + cc) * p.ND;
+  float sr = 0.f, si = 0.f;
+  for (int di = lane; di < p.ND; di += 32) {
+    const int dr = di % (2 * P - 1) - (P - 1), dc = di / (2 * P - 1) - (Q - 1);
+    const int nn = n + dr, mm = m + dc;
+    if (nn < 0 || nn >= N || mm < 0 || mm >= M) continue;
+    const float2 w = __ldg(Tc + di);
+    const float2 a = __ldg(p.A + (long long)nn * p.lda + mm);
+    sr = fma_rn(w.x, a.x, sr);
+    sr = fma_rn(-w.y, a.y, sr);
+    si = fma_rn(w.x, a.y, si);
+    si = fma_rn(w.y, a.x, si);
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) p.dA[(long long)n * p.M + m] = make_float2(sr, si);
+}
+
+bool stencil_adjoint_ok(long long N, long long M, int P, int Q) {
+  const long long ND = (2LL * P - 1) * (2LL * Q - 1);
+  return N >= 2LL * P - 1 && M >= 2LL * Q - 1 && ND <= 2048;
+}
+
+size_t stencil_adjoint_workspace(int P, int Q) {
+  const size_t ND = (size_t)(2 * P - 1) * (2 * Q - 1);
+  return kWsHeader + ((ND * ND * sizeof(float2) + 255) & ~(size_t)255);
+}
+
+cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, long long M, int P,
+                                   int Q, int mean, void *dA, void *workspace, cudaStream_t s) {
+  StParams p;
+  p.A = (const float2 *)A;
+  p.G = (const float2 *)G;
+  p.T = (float2 *)((char *)workspace + kWsHeader);
+  p.dA = (float2 *)dA;
+  p.lda = M;
+  p.N = (int)N;
+  p.M = (int)M;
+  p.P = P;
+  p.Q = Q;
+  p.Hn = (int)(N - P + 1);
+  p.W = (int)(M - Q + 1);
+  p.K = (long long)p.Hn * p.W;
+  p.mean = mean;
+  p.NRC = 2 * P - 1;
+  p.NCC = 2 * Q - 1;
+  p.ND = p.NRC * p.NCC;
+  const size_t wsm = (size_t)(P + 1) * (Q + 1) * sizeof(double2);
+  k_adjs_weights<<<(unsigned)p.ND, 256, wsm, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n_in = p.Hn - (P - 1), m_in = p.W - (Q - 1);
+  const long long tiles =
+      (long long)((n_in + kStTR - 1) / kStTR) * ((m_in + kStTC - 1) / kStTC);
+  const size_t smem =
+      ((size_t)(kStTR + 2 * P - 2) * (kStTC + 2 * Q - 2) + (size_t)p.ND) * sizeof(float2);
+  static size_t attr_done = 0;
+  if (smem > 48 * 1024 && smem > attr_done) {
+    e = cudaFuncSetAttribute(k_adjs_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = smem;
+  }
+  k_adjs_inner<<<(unsigned)tiles, 256, smem, s>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const long long n_fringe = 2LL * (P - 1) * M + (long long)n_in * 2 * (Q - 1);
+  if (n_fringe > 0) k_adjs_fringe<<<(unsigned)((n_fringe + 7) / 8), 256, 0, s>>>(p, n_fringe);
+  return cudaGetLastError();
+}
+
+}  // namespace cov

@@ -119,3 +119,15 @@ def test_batched_plan_validation_host_only():
     ptr = ctypes.c_void_p()
     assert lib.cov_batched_plan_create(arr, 1, 1, 0, 0, ctypes.byref(ptr)) == 5  # c128
     assert lib.cov_batched_plan_create(arr, 1, 0, 2, 0, ctypes.byref(ptr)) == 5  # gemm algo
+
+
+def test_backward_workspace_by_form():
+    # the stencil form tabulates (2P-1)(2Q-1) weights per class pair; the
+    # dense form keeps Y = H X (PQ x windows)
+    st = cov.backward_workspace_size(256, 256, 12, 12, "stencil")
+    de = cov.backward_workspace_size(256, 256, 12, 12, "dense")
+    assert st >= 23 ** 4 * 8 and de >= 144 * 245 * 245 * 8
+    assert cov.backward_workspace_size(256, 256, 12, 12) == st  # auto picks the stencil
+    assert cov.backward_workspace_size(9, 9, 9, 9) == cov.backward_workspace_size(9, 9, 9, 9, "dense")
+    with pytest.raises(cov.CovError):
+        cov.backward_workspace_size(9, 9, 9, 9, "stencil")

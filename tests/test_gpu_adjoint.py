@@ -15,16 +15,35 @@ from gpu_util import rel_fro  # noqa: E402
 F32_TOL = 1e-5
 
 
-@pytest.mark.parametrize("N,M,P,Q", [(20, 17, 4, 3), (16, 16, 4, 4), (37, 50, 7, 5),
-                                     (9, 9, 9, 9), (30, 12, 1, 1), (64, 70, 12, 12)])
+SHAPES = [(20, 17, 4, 3), (16, 16, 4, 4), (37, 50, 7, 5), (9, 9, 9, 9), (30, 12, 1, 1),
+          (64, 70, 12, 12), (47, 33, 24, 2), (100, 37, 3, 19), (11, 13, 6, 7)]
+
+
+def _stencil_ok(N, M, P, Q):
+    return N >= 2 * P - 1 and M >= 2 * Q - 1 and (2 * P - 1) * (2 * Q - 1) <= 2048
+
+
+@pytest.mark.parametrize("N,M,P,Q", SHAPES)
 @pytest.mark.parametrize("norm", ["mean", "sum"])
-def test_backward_matches_oracle(oracle_mod, N, M, P, Q, norm):
+@pytest.mark.parametrize("form", ["dense", "stencil", "auto"])
+def test_backward_matches_oracle(oracle_mod, N, M, P, Q, norm, form):
+    if form == "stencil" and not _stencil_ok(N, M, P, Q):
+        pytest.skip("the stencil form needs N >= 2P-1, M >= 2Q-1")
     A = wl.complex_normal((N, M), 11 + N, dtype="c64")
     G = wl.complex_normal((P * Q, P * Q), 12 + M, dtype="c64")
-    dA = cov.estimate_backward(torch.from_numpy(A).cuda(), torch.from_numpy(G).cuda(), P, Q, norm=norm)
+    dA = cov.estimate_backward(torch.from_numpy(A).cuda(), torch.from_numpy(G).cuda(), P, Q, norm=norm,
+                               form=form)
     want = oracle_mod.cov_backward(A.astype(np.complex128), G.astype(np.complex128), P, Q,
                                    mean=(norm == "mean"))
     assert rel_fro(dA.cpu().numpy(), want) < F32_TOL
+
+
+def test_stencil_form_refuses_small_shapes():
+    with pytest.raises(cov.CovError) as e:
+        cov.estimate_backward(torch.zeros((9, 9), dtype=torch.complex64, device="cuda"),
+                              torch.zeros((81, 81), dtype=torch.complex64, device="cuda"), 9, 9,
+                              form="stencil")
+    assert e.value.code == 5
 
 
 def test_autograd_against_fd_fp64(oracle_mod):
