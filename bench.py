@@ -17,6 +17,7 @@ data-path collective): weak scaling, value = all ranks' products / max time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -584,49 +585,45 @@ def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
 
 def bench_adjoint(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
     """Differentiation workload: batch of 64 A (256 x 256, window 12 x 12);
-    forward through the batched launch, adjoint dL/dA per member for
-    L = ||R - R_target||_F^2 (G = 2 (R - R_target) formed once, untimed)."""
+    forward through the batched launch, adjoint dL/dA of every member for
+    L = ||R - R_target||_F^2 (G = 2 (R - R_target) formed once, untimed):
+    the stencil form over the whole batch in one launch sequence, and the
+    dense form member by member (64 calls in one CUDA graph) for comparison."""
     w = wl.WORKLOADS["diff_b64_256x256_w12_f32"]
     P, Q, N, M, B = w.P, w.Q, w.N, w.M, w.batch
-    As = [torch.from_numpy(wl.complex_normal((N, M), w.seed + k, "c64")).cuda() for k in range(B)]
-    Rs = [torch.empty((P * Q, P * Q), dtype=torch.complex64, device="cuda") for _ in range(B)]
+    A_all = torch.stack([torch.from_numpy(wl.complex_normal((N, M), w.seed + k, "c64"))
+                         for k in range(B)]).cuda()
+    R_all = torch.empty((B, P * Q, P * Q), dtype=torch.complex64, device="cuda")
     T = cov.estimate(torch.from_numpy(wl.complex_normal((N, M), 5000, "c64")).cuda(), P, Q)
-    plan = cov.BatchedPlan([(A, R, P, Q) for A, R in zip(As, Rs)])
+    plan = cov.BatchedPlan([(A_all[k], R_all[k], P, Q) for k in range(B)])
     wsf = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
     plan.upload(wsf)
     plan.run(wsf)
     torch.cuda.synchronize()
-    Gs = [(2.0 * (R - T)).contiguous() for R in Rs]
-    wsb = torch.empty(max(cov.backward_workspace_size(N, M, P, Q, "dense"),
-                          cov.backward_workspace_size(N, M, P, Q, "stencil")),
-                      dtype=torch.uint8, device="cuda")
-    dAs = [torch.empty_like(A) for A in As]
+    G_all = (2.0 * (R_all - T)).contiguous()
+    dA_all = torch.empty_like(A_all)
     lib = cov.load()
-    sp = stream.cuda_stream
-
-    form = {"stencil": 2, "dense": 1}
-
-    def backward_all(f="stencil"):
-        for A, G, dA in zip(As, Gs, dAs):
-            lib.cov_estimate_backward_ex(A.data_ptr(), G.data_ptr(), 0, N, M, P, Q, 0, form[f],
-                                         dA.data_ptr(), wsb.data_ptr(), wsb.numel(), sp)
-
-    backward_all()
-    backward_all("dense")
-    torch.cuda.synchronize()
-    # each form's 64 calls captured in one CUDA graph (device time, no host gaps)
+    need = ctypes.c_size_t(0)
+    lib.cov_backward_strided_workspace_size(B, N, M, P, Q, ctypes.byref(need))
+    wss = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    wsd = torch.empty(cov.backward_workspace_size(N, M, P, Q, "dense"), dtype=torch.uint8,
+                      device="cuda")
+    D = P * Q
+    sargs = (A_all.data_ptr(), N * M, G_all.data_ptr(), D * D, dA_all.data_ptr(), N * M, B, N, M,
+             P, Q, 0, wss.data_ptr(), wss.numel(), stream.cuda_stream)
+    if lib.cov_estimate_backward_strided(*sargs) != 0:
+        raise RuntimeError("strided adjoint failed")
     side = torch.cuda.Stream()
-    graphs = {}
-    for f in ("stencil", "dense"):
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=side):
-            for A, G, dA in zip(As, Gs, dAs):
-                lib.cov_estimate_backward_ex(A.data_ptr(), G.data_ptr(), 0, N, M, P, Q, 0, form[f],
-                                             dA.data_ptr(), wsb.data_ptr(), wsb.numel(),
-                                             side.cuda_stream)
-        graphs[f] = g
-    for g in graphs.values():
-        g.replay()
+    g = torch.cuda.CUDAGraph()
+    codes = 0
+    with torch.cuda.graph(g, stream=side):
+        for k in range(B):
+            codes |= lib.cov_estimate_backward_ex(
+                A_all[k].data_ptr(), G_all[k].data_ptr(), 0, N, M, P, Q, 0, 1, dA_all[k].data_ptr(),
+                wsd.data_ptr(), wsd.numel(), side.cuda_stream)
+    if codes != 0:
+        raise RuntimeError("dense adjoint failed under capture")
+    g.replay()
     torch.cuda.synchronize()
     n = 3
     ev = mk_events(4 * n)
@@ -634,25 +631,26 @@ def bench_adjoint(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
         ev[4 * k].record(stream)
         plan.run(wsf)
         ev[4 * k + 1].record(stream)
-        graphs["stencil"].replay()
+        lib.cov_estimate_backward_strided(*sargs)
         ev[4 * k + 2].record(stream)
-        graphs["dense"].replay()
+        g.replay()
         ev[4 * k + 3].record(stream)
     torch.cuda.synchronize()
+    cov.check_device_status(wss)
     fwd = sum(ev[4 * k].elapsed_time(ev[4 * k + 1]) for k in range(n)) / n
     bwd = sum(ev[4 * k + 1].elapsed_time(ev[4 * k + 2]) for k in range(n)) / n
     bwd_dense = sum(ev[4 * k + 2].elapsed_time(ev[4 * k + 3]) for k in range(n)) / n
-    D = P * Q
     KW = (N - P + 1) * (M - Q + 1)
     ND = (2 * P - 1) * (2 * Q - 1)
     st_flops = 8.0 * ND * N * M * B     # complex MACs of the stencil (upper bound: full support)
     hx_flops = 8.0 * D * D * KW * B     # complex MACs of Y = H X
-    return {"batch": B, "forward_ms": fwd, "backward_ms": bwd, "backward_form": "stencil",
+    return {"batch": B, "forward_ms": fwd, "backward_ms": bwd,
+            "backward_form": "stencil, one strided-batch launch sequence",
             "forward_plus_backward_ms": fwd + bwd,
             "backward_fp32_fma_frac": st_flops / (bwd * 1e-3) / fp32_peak,
             "backward_dense_ms": bwd_dense,
             "backward_dense_fp32_fma_frac": hx_flops / (bwd_dense * 1e-3) / fp32_peak,
-            "workspace_bytes_backward": wsb.numel()}
+            "workspace_bytes_backward": wss.numel()}
 
 
 TF32_OVER_BF16_NOMINAL = 1.1 / 2.25  # dense tensor rates per GPU (recipe's nominal table)

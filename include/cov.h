@@ -334,6 +334,20 @@ cov_status cov_estimate_backward_ex(const void *A, const void *G, cov_dtype dtyp
                                     int64_t N, int64_t M, int P, int Q, cov_norm norm,
                                     cov_bwd_form form, void *dA, void *workspace,
                                     size_t ws_bytes, cov_stream_t stream);
+/* A batch of `batch` (1..65535) equal-shape COV_C64 members in one launch
+ * sequence, stencil form only: member k reads A + k*stride_A (N x M,
+ * leading dimension M), G + k*stride_G (PQ x PQ) and writes
+ * dA + k*stride_dA (strides in complex elements, at least one member's
+ * size). The workspace holds every member's weight table
+ * (cov_backward_strided_workspace_size). COV_EUNSUPPORTED where the stencil
+ * form does not apply. */
+cov_status cov_backward_strided_workspace_size(int batch, int64_t N, int64_t M, int P, int Q,
+                                               size_t *bytes);
+cov_status cov_estimate_backward_strided(const void *A, int64_t stride_A, const void *G,
+                                         int64_t stride_G, void *dA, int64_t stride_dA,
+                                         int batch, int64_t N, int64_t M, int P, int Q,
+                                         cov_norm norm, void *workspace, size_t ws_bytes,
+                                         cov_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Sharding across GPUs (one process per GPU). Section 4.2 gives every

@@ -85,6 +85,9 @@ SIGNATURES = [
     ("cov_batched_plan_destroy", None, [_VP]),
     ("cov_backward_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
     ("cov_estimate_backward", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _VP, _VP, _SZ, _VP]),
+    ("cov_backward_strided_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
+    ("cov_estimate_backward_strided", _I, [_VP, _I64, _VP, _I64, _VP, _I64, _I, _I64, _I64, _I,
+                                           _I, _I, _VP, _SZ, _VP]),
     ("cov_backward_workspace_size_ex", _I, [_I, _I64, _I64, _I, _I, _I, ctypes.POINTER(_SZ)]),
     ("cov_estimate_backward_ex", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _I, _VP, _VP, _SZ,
                                       _VP]),
@@ -237,6 +240,32 @@ def estimate_backward(A, G, P: int, Q: int, norm: str = "mean", workspace=None, 
                                            workspace.data_ptr(), workspace.numel(),
                                            _stream_ptr(stream)),
            "cov_estimate_backward")
+    return dA
+
+
+def estimate_backward_batch(A, G, P: int, Q: int, norm: str = "mean", workspace=None,
+                            stream=None):
+    """dL/dA for a batch: A (B, N, M) and G (B, PQ, PQ) contiguous complex64
+    CUDA tensors; one launch sequence of the stencil form."""
+    torch = _torch()
+    if not (A.is_cuda and G.is_cuda) or A.dtype != torch.complex64 or G.dtype != torch.complex64:
+        raise ValueError("A and G must be complex64 CUDA tensors")
+    if A.dim() != 3 or G.dim() != 3 or A.shape[0] != G.shape[0]:
+        raise ValueError("A must be (B, N, M) and G (B, PQ, PQ)")
+    A = A.contiguous()
+    G = G.contiguous()
+    B, N, M = A.shape
+    need = ctypes.c_size_t(0)
+    _check(load().cov_backward_strided_workspace_size(B, N, M, P, Q, ctypes.byref(need)),
+           "cov_backward_strided_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(int(need.value), dtype=torch.uint8, device=A.device)
+    dA = torch.empty_like(A)
+    _check(load().cov_estimate_backward_strided(A.data_ptr(), N * M, G.data_ptr(), P * Q * P * Q,
+                                                dA.data_ptr(), N * M, B, N, M, P, Q, NORMS[norm],
+                                                workspace.data_ptr(), workspace.numel(),
+                                                _stream_ptr(stream)),
+           "cov_estimate_backward_strided")
     return dA
 
 

@@ -21,9 +21,10 @@ namespace cov {
 
 // stencil form (adjoint_stencil.cu)
 bool stencil_adjoint_ok(long long N, long long M, int P, int Q);
-size_t stencil_adjoint_workspace(int P, int Q);
+size_t stencil_adjoint_workspace(int P, int Q, int batch);
 cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, long long M, int P,
-                                   int Q, int mean, void *dA, void *workspace, cudaStream_t s);
+                                   int Q, int mean, void *dA, void *workspace, cudaStream_t s,
+                                   int batch, long long sA, long long sG, long long sdA);
 
 constexpr int kAdjTA = 48;   // rows a of Y per CTA
 constexpr int kAdjTW = 128;  // windows per CTA (one window row p, consecutive q)
@@ -165,7 +166,7 @@ cov_status cov_backward_workspace_size_ex(cov_dtype dtype, int64_t N, int64_t M,
   form = resolve_bwd(form, N, M, P, Q);
   if (form == COV_BWD_STENCIL) {
     if (!cov::stencil_adjoint_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
-    *bytes = cov::stencil_adjoint_workspace(P, Q);
+    *bytes = cov::stencil_adjoint_workspace(P, Q, 1);
     return COV_OK;
   }
   if (form != COV_BWD_DENSE) return COV_EINVAL;
@@ -196,7 +197,7 @@ cov_status cov_estimate_backward_ex(const void *A, const void *G, cov_dtype dtyp
   if (cudaMemsetAsync(workspace, 0, 4, s) != cudaSuccess) return COV_ECUDA;
   if (form == COV_BWD_STENCIL)
     return cov::launch_stencil_adjoint(A, G, N, M, P, Q, norm == COV_MEAN ? 1 : 0, dA, workspace,
-                                       s) == cudaSuccess
+                                       s, 1, 0, 0, 0) == cudaSuccess
                ? COV_OK
                : COV_ECUDA;
   cov::AdjParams p;
@@ -230,6 +231,35 @@ cov_status cov_estimate_backward_ex(const void *A, const void *G, cov_dtype dtyp
   const long long grid2 = (N * M + 255) / 256;
   cov::k_adj_col2im<<<(unsigned)grid2, 256, 0, s>>>(p);
   return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
+}
+
+cov_status cov_backward_strided_workspace_size(int batch, int64_t N, int64_t M, int P, int Q,
+                                               size_t *bytes) {
+  if (!bytes || batch < 1 || batch > 65535 || !bwd_args_ok(N, M, P, Q)) return COV_EINVAL;
+  if (!cov::stencil_adjoint_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+  *bytes = cov::stencil_adjoint_workspace(P, Q, batch);
+  return COV_OK;
+}
+
+cov_status cov_estimate_backward_strided(const void *A, int64_t stride_A, const void *G,
+                                         int64_t stride_G, void *dA, int64_t stride_dA, int batch,
+                                         int64_t N, int64_t M, int P, int Q, cov_norm norm,
+                                         void *workspace, size_t ws_bytes, cov_stream_t stream) {
+  if (!A || !G || !dA || batch < 1 || batch > 65535 || !bwd_args_ok(N, M, P, Q) ||
+      (norm != COV_MEAN && norm != COV_SUM))
+    return COV_EINVAL;
+  const long long D = (long long)P * Q;
+  if (stride_A < N * M || stride_dA < N * M || stride_G < D * D) return COV_EINVAL;
+  if ((((uintptr_t)A) & 7) || (((uintptr_t)G) & 7) || (((uintptr_t)dA) & 7)) return COV_EINVAL;
+  if (!cov::stencil_adjoint_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
+  const size_t need = cov::stencil_adjoint_workspace(P, Q, batch);
+  if (!workspace || ws_bytes < need || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(workspace, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  return cov::launch_stencil_adjoint(A, G, N, M, P, Q, norm == COV_MEAN ? 1 : 0, dA, workspace, s,
+                                     batch, stride_A, stride_G, stride_dA) == cudaSuccess
+             ? COV_OK
+             : COV_ECUDA;
 }
 
 cov_status cov_estimate_backward(const void *A, const void *G, cov_dtype dtype, int64_t N, int64_t M,

@@ -16,7 +16,8 @@
 // T[class][Delta] from FP64 prefix sums of H along each Delta; kernel 2
 // applies the inner-class stencil (a 2-D correlation with (2P-1)(2Q-1)
 // weights) to the inner rows and columns from a staged tile of A; kernel 3
-// takes the fringe elements one by one. Every element of dA has one writer;
+// takes the fringe elements one by one; blockIdx.y indexes a batch of
+// equal-shape members with fixed strides. Every element of dA has one writer;
 // no atomics. Work: (2P-1)(2Q-1) complex MACs per element instead of (PQ)^2
 // per window.
 #include <cuda_runtime.h>
@@ -40,7 +41,20 @@ struct StParams {
   int N, M, P, Q, Hn, W;
   long long K;
   int mean, NRC, NCC, ND;
+  // batch member blockIdx.y: element strides between members
+  long long sA, sG, sdA, sT;
 };
+
+// The parameters of batch member blockIdx.y.
+__device__ __forceinline__ StParams member(const StParams &p0) {
+  StParams p = p0;
+  const long long b = blockIdx.y;
+  p.A += b * p.sA;
+  p.G += b * p.sG;
+  p.dA += b * p.sdA;
+  p.T += b * p.sT;
+  return p;
+}
 
 // class -> admissible range of the window offset (rows; columns alike)
 __device__ __forceinline__ void class_range(int c, int P, int &lo, int &hi) {
@@ -64,7 +78,8 @@ __device__ __forceinline__ int row_class(int n, int P, int Hn) {
 // where (i+dr, j+dc) leaves the window) is turned into FP64 2-D prefix sums
 // in shared memory; each (row class, column class) entry is then one
 // rectangle sum (four lookups).
-__global__ void __launch_bounds__(256) k_adjs_weights(const StParams p) {
+__global__ void __launch_bounds__(256) k_adjs_weights(const StParams p0) {
+  const StParams p = member(p0);
   extern __shared__ __align__(16) unsigned char smem_w[];
   const int P = p.P, Q = p.Q, D = P * Q;
   double2 *S = (double2 *)smem_w;  // [(P+1) x (Q+1)], S[i][j] = sum over i' < i, j' < j
@@ -116,7 +131,8 @@ __global__ void __launch_bounds__(256) k_adjs_weights(const StParams p) {
 // Inner rows [P-1, Hn-1] x inner columns [Q-1, W-1]: one 16 x 32 tile per
 // CTA, the tile of A with its (P-1, Q-1) halo and the inner-class weights in
 // shared memory; thread (ty, tx) computes rows ty and ty+8 of column tx.
-__global__ void __launch_bounds__(256) k_adjs_inner(const StParams p) {
+__global__ void __launch_bounds__(256) k_adjs_inner(const StParams p0) {
+  const StParams p = member(p0);
   extern __shared__ __align__(16) unsigned char smem_st[];
   const int P = p.P, Q = p.Q;
   const int SW = kStTC + 2 * Q - 2, SH = kStTR + 2 * P - 2;
@@ -164,7 +180,8 @@ __global__ void __launch_bounds__(256) k_adjs_inner(const StParams p) {
 // Fringe elements (outside the inner box), one warp each: lanes take the
 // combinations Delta in turn (coalesced weights of the element's row and
 // column class from the table), then a warp sum.
-__global__ void __launch_bounds__(256) k_adjs_fringe(const StParams p, long long n_fringe) {
+__global__ void __launch_bounds__(256) k_adjs_fringe(const StParams p0, long long n_fringe) {
+  const StParams p = member(p0);
   const long long idx = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (idx >= n_fringe) return;
@@ -211,13 +228,14 @@ bool stencil_adjoint_ok(long long N, long long M, int P, int Q) {
   return N >= 2LL * P - 1 && M >= 2LL * Q - 1 && ND <= 2048;
 }
 
-size_t stencil_adjoint_workspace(int P, int Q) {
+size_t stencil_adjoint_workspace(int P, int Q, int batch) {
   const size_t ND = (size_t)(2 * P - 1) * (2 * Q - 1);
-  return kWsHeader + ((ND * ND * sizeof(float2) + 255) & ~(size_t)255);
+  return kWsHeader + (((size_t)batch * ND * ND * sizeof(float2) + 255) & ~(size_t)255);
 }
 
 cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, long long M, int P,
-                                   int Q, int mean, void *dA, void *workspace, cudaStream_t s) {
+                                   int Q, int mean, void *dA, void *workspace, cudaStream_t s,
+                                   int batch, long long sA, long long sG, long long sdA) {
   StParams p;
   p.A = (const float2 *)A;
   p.G = (const float2 *)G;
@@ -235,8 +253,12 @@ cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, lo
   p.NRC = 2 * P - 1;
   p.NCC = 2 * Q - 1;
   p.ND = p.NRC * p.NCC;
+  p.sA = sA;
+  p.sG = sG;
+  p.sdA = sdA;
+  p.sT = (long long)p.ND * p.NRC * p.NCC;
   const size_t wsm = (size_t)(P + 1) * (Q + 1) * sizeof(double2);
-  k_adjs_weights<<<(unsigned)p.ND, 256, wsm, s>>>(p);
+  k_adjs_weights<<<dim3((unsigned)p.ND, (unsigned)batch), 256, wsm, s>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n_in = p.Hn - (P - 1), m_in = p.W - (Q - 1);
@@ -250,10 +272,11 @@ cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, lo
     if (e != cudaSuccess) return e;
     attr_done = smem;
   }
-  k_adjs_inner<<<(unsigned)tiles, 256, smem, s>>>(p);
+  k_adjs_inner<<<dim3((unsigned)tiles, (unsigned)batch), 256, smem, s>>>(p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const long long n_fringe = 2LL * (P - 1) * M + (long long)n_in * 2 * (Q - 1);
-  if (n_fringe > 0) k_adjs_fringe<<<(unsigned)((n_fringe + 7) / 8), 256, 0, s>>>(p, n_fringe);
+  if (n_fringe > 0)
+    k_adjs_fringe<<<dim3((unsigned)((n_fringe + 7) / 8), (unsigned)batch), 256, 0, s>>>(p, n_fringe);
   return cudaGetLastError();
 }
 

@@ -89,3 +89,16 @@ def test_autograd_matches_oracle_gradient_workload_shape(oracle_mod):
     G = 2.0 * (R.detach() - Tt).cpu().numpy().astype(np.complex128)
     want = oracle_mod.cov_backward(A.astype(np.complex128), G, P, Q)
     assert rel_fro(At.grad.cpu().numpy(), want) < F32_TOL
+
+
+@pytest.mark.parametrize("B,N,M,P,Q", [(5, 40, 33, 5, 4), (3, 64, 70, 12, 12), (4, 11, 13, 6, 7)])
+@pytest.mark.parametrize("norm", ["mean", "sum"])
+def test_strided_batch_matches_oracle(oracle_mod, B, N, M, P, Q, norm):
+    A = np.stack([wl.complex_normal((N, M), 50 + k, dtype="c64") for k in range(B)])
+    G = np.stack([wl.complex_normal((P * Q, P * Q), 90 + k, dtype="c64") for k in range(B)])
+    dA = cov.estimate_backward_batch(torch.from_numpy(A).cuda(), torch.from_numpy(G).cuda(), P, Q,
+                                     norm=norm).cpu().numpy()
+    for k in range(B):
+        want = oracle_mod.cov_backward(A[k].astype(np.complex128), G[k].astype(np.complex128), P, Q,
+                                       mean=(norm == "mean"))
+        assert rel_fro(dA[k], want) < F32_TOL
