@@ -39,18 +39,24 @@ FALLBACK_SM_MAX_MHZ = 2070.0
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# the production kernel from one ncu capture, keyed by (workload, kernel,
-# hash of the library sources at capture time): null once they have changed.
-NCU_TRAFFIC = {}
+# the production kernel from one ncu capture (profiles/), keyed by (workload,
+# kernel, hash of the combination path's kernel sources at capture time):
+# null once those sources have changed.
+NCU_TRAFFIC = {  # bytes per launch; profiles/k_fused_*.md, profiles/k_products_inner_*.md
+    ("cn_1024x1024_w16_f32", "k_fused", "461dd7e0470cf668"): 8574720,
+    ("cn_1024x1024_w16_f32", "k_products_inner", "461dd7e0470cf668"): 8438272,
+}
+KERNEL_SOURCES = ("cov_device.cuh", "cov_internal.h", "rec_common.cuh", "rec_products.cuh",
+                  "rec_products.cu", "rec_fringe.cuh", "rec_fringe.cu", "rec_reduce.cuh",
+                  "rec_reduce.cu", "rec_fused.cu", "recurrence.cu", "plan.cpp", "plan.h")
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1303_2285_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
