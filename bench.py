@@ -759,7 +759,8 @@ def extras(args, cov, torch, np, wl, mk_events, stream) -> dict:
 def profile_case(case: str) -> int:
     """Small cases of the secondary kernels for ncu captures: 600 uneven
     matrices through the batched launch (seed 3), the dense TF32x3 form on the
-    bench workload, the adjoint of one 256 x 256 input with a 12 x 12 window."""
+    bench workload, the stencil adjoint of a batch of eight 256 x 256 inputs
+    with a 12 x 12 window."""
     import torch
 
     import cov_workloads as wl
@@ -782,10 +783,12 @@ def profile_case(case: str) -> int:
     else:
         N = M = 256
         P = Q = 12
-        A = torch.from_numpy(wl.complex_normal((N, M), 4, "c64")).cuda()
-        G = torch.from_numpy(wl.complex_normal((P * Q, P * Q), 5, "c64")).cuda()
+        A = torch.stack([torch.from_numpy(wl.complex_normal((N, M), 4 + k, "c64"))
+                         for k in range(8)]).cuda()
+        G = torch.stack([torch.from_numpy(wl.complex_normal((P * Q, P * Q), 5 + k, "c64"))
+                         for k in range(8)]).cuda()
         for _ in range(3):
-            cov.estimate_backward(A, G, P, Q)
+            cov.estimate_backward_batch(A, G, P, Q)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": case, "ok": True}))
     return 0

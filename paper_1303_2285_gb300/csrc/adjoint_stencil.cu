@@ -13,7 +13,7 @@
 // I(n) = [max(0, n - (N-P)), min(P-1, n)], so T depends on (n, m) only through
 // a row class (2P-1 of them: the P-1 top fringe rows, the inner rows, the P-1
 // bottom fringe rows) and a column class (2Q-1). Kernel 1 tabulates
-// T[class][Delta] from FP64 prefix sums of H along each Delta; kernel 2
+// T[class][Delta] from prefix and suffix sums of H along each Delta; kernel 2
 // applies the inner-class stencil (a 2-D correlation with (2P-1)(2Q-1)
 // weights) to the inner rows and columns from a staged tile of A; kernel 3
 // takes the fringe elements one by one; blockIdx.y indexes a batch of
@@ -29,8 +29,8 @@
 
 namespace cov {
 
-constexpr int kStTR = 16;  // output tile of the inner stencil: 16 rows x 32 columns,
-constexpr int kStTC = 32;  // two rows a thread
+constexpr int kStTR = 32;  // output tile of the inner stencil: 32 rows x 32 columns,
+constexpr int kStTC = 32;  // four consecutive rows a thread
 
 struct StParams {
   const float2 *A;
@@ -74,67 +74,97 @@ __device__ __forceinline__ int row_class(int n, int P, int Hn) {
 }
 
 // T[(rc * NCC + cc) * ND + Delta], Delta = (dr + P - 1) + (2P - 1)(dc + Q - 1).
-// One CTA per Delta: the P x Q grid h[i][j] = H[(i,j)][(i+dr, j+dc)] (zero
-// where (i+dr, j+dc) leaves the window) is turned into FP64 2-D prefix sums
-// in shared memory; each (row class, column class) entry is then one
-// rectangle sum (four lookups).
+// One CTA per Delta. The admissible offsets of a class are a prefix (top
+// classes), the full range (inner class) or a suffix (bottom classes) of
+// [0, P-1] (columns alike), so every entry is a sum of column prefix or
+// suffix sums over a prefix or suffix of the columns: no differences, no
+// cancellation. h[i][j] = H[(i,j)][(i+dr, j+dc)], zero where (i+dr, j+dc)
+// leaves the window.
 __global__ void __launch_bounds__(256) k_adjs_weights(const StParams p0) {
   const StParams p = member(p0);
   extern __shared__ __align__(16) unsigned char smem_w[];
   const int P = p.P, Q = p.Q, D = P * Q;
-  double2 *S = (double2 *)smem_w;  // [(P+1) x (Q+1)], S[i][j] = sum over i' < i, j' < j
+  float2 *pre = (float2 *)smem_w;  // [Q][P]: pre[j][r] = sum_{i <= r} h[i][j]
+  float2 *suf = pre + P * Q;       // [Q][P]: suf[j][r] = sum_{i >= r} h[i][j]
   const int di = blockIdx.x;
   const int dr = di % (2 * P - 1) - (P - 1), dc = di / (2 * P - 1) - (Q - 1);
-  for (int e = threadIdx.x; e < (P + 1) * (Q + 1); e += blockDim.x) {
-    const int i = e % (P + 1), j = e / (P + 1);
-    double2 h = make_double2(0.0, 0.0);
-    if (i > 0 && j > 0) {
-      const int ii = i - 1, jj = j - 1;
-      if (ii + dr >= 0 && ii + dr < P && jj + dc >= 0 && jj + dc < Q) {
-        const int a = ii + P * jj, b = (ii + dr) + P * (jj + dc);
-        const float2 g1 = __ldg(p.G + (long long)a * D + b), g2 = __ldg(p.G + (long long)b * D + a);
-        h.x = (double)g1.x + (double)g2.x;  // H[a][b] = G[a][b] + conj(G[b][a])
-        h.y = (double)g1.y - (double)g2.y;
-      }
+  for (int e = threadIdx.x; e < P * Q; e += blockDim.x) {
+    const int i = e % P, j = e / P;
+    float2 h = make_float2(0.f, 0.f);
+    if (i + dr >= 0 && i + dr < P && j + dc >= 0 && j + dc < Q) {
+      const int a = i + P * j, b = (i + dr) + P * (j + dc);
+      const float2 g1 = __ldg(p.G + (long long)a * D + b), g2 = __ldg(p.G + (long long)b * D + a);
+      h = make_float2(g1.x + g2.x, g1.y - g2.y);  // H[a][b] = G[a][b] + conj(G[b][a])
     }
-    S[i + (P + 1) * j] = h;
+    pre[e] = h;
+    suf[e] = h;
   }
   __syncthreads();
-  // prefix sums along i (one thread per column j), then along j (per row i)
-  for (int j = threadIdx.x; j <= Q; j += blockDim.x)
-    for (int i = 1; i <= P; ++i) {
-      S[i + (P + 1) * j].x += S[i - 1 + (P + 1) * j].x;
-      S[i + (P + 1) * j].y += S[i - 1 + (P + 1) * j].y;
+  for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+    for (int i = 1; i < P; ++i) {
+      pre[j * P + i].x += pre[j * P + i - 1].x;
+      pre[j * P + i].y += pre[j * P + i - 1].y;
     }
-  __syncthreads();
-  for (int i = threadIdx.x; i <= P; i += blockDim.x)
-    for (int j = 1; j <= Q; ++j) {
-      S[i + (P + 1) * j].x += S[i + (P + 1) * (j - 1)].x;
-      S[i + (P + 1) * j].y += S[i + (P + 1) * (j - 1)].y;
+    for (int i = P - 2; i >= 0; --i) {
+      suf[j * P + i].x += suf[j * P + i + 1].x;
+      suf[j * P + i].y += suf[j * P + i + 1].y;
     }
+  }
   __syncthreads();
-  const double inv = p.mean ? 1.0 / (double)p.K : 1.0;
-  for (int cls = threadIdx.x; cls < p.NRC * p.NCC; cls += blockDim.x) {
-    const int rc = cls / p.NCC, cc = cls - rc * p.NCC;
-    int ilo, ihi, jlo, jhi;
-    class_range(rc, P, ilo, ihi);
-    class_range(cc, Q, jlo, jhi);
-    // rectangle [ilo, ihi] x [jlo, jhi] (invalid cells are zero in h)
-    const double2 s11 = S[(ihi + 1) + (P + 1) * (jhi + 1)], s01 = S[ilo + (P + 1) * (jhi + 1)];
-    const double2 s10 = S[(ihi + 1) + (P + 1) * jlo], s00 = S[ilo + (P + 1) * jlo];
-    const double re = (s11.x - s01.x - s10.x + s00.x) * inv;
-    const double im = (s11.y - s01.y - s10.y + s00.y) * inv;
-    p.T[(long long)cls * p.ND + di] = make_float2((float)re, (float)im);
+  const float inv = p.mean ? 1.0f / (float)p.K : 1.0f;
+  const bool exact = !p.mean || p.K <= (1LL << 24);
+  for (int rc = threadIdx.x; rc < p.NRC; rc += blockDim.x) {
+    // v[j]: the row class's range summed in column j
+    const float2 *src = rc <= P - 1 ? pre + rc : suf + (rc - P + 1);
+    float2 *out = p.T + (long long)rc * p.NCC * p.ND + di;
+    auto put = [&](int cc, float2 v) {
+      if (p.mean) {
+        if (exact) {
+          v.x = v.x / (float)p.K;
+          v.y = v.y / (float)p.K;
+        } else {
+          v.x *= inv;
+          v.y *= inv;
+        }
+      }
+      out[(long long)cc * p.ND] = v;
+    };
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = 0; j < Q; ++j) {  // column classes 0..Q-1: prefixes j' <= cc
+      acc.x += src[j * P].x;
+      acc.y += src[j * P].y;
+      put(j, acc);
+    }
+    acc = make_float2(0.f, 0.f);
+    for (int j = Q - 1; j >= 1; --j) {  // classes Q..2Q-2: suffixes j' >= cc - Q + 1
+      acc.x += src[j * P].x;
+      acc.y += src[j * P].y;
+      put(Q - 1 + j, acc);
+    }
   }
 }
 
-// Inner rows [P-1, Hn-1] x inner columns [Q-1, W-1]: one 16 x 32 tile per
+// Inner rows [P-1, Hn-1] x inner columns [Q-1, W-1]: one 32 x 32 tile per
 // CTA, the tile of A with its (P-1, Q-1) halo and the inner-class weights in
-// shared memory; thread (ty, tx) computes rows ty and ty+8 of column tx.
+// shared memory. Thread (ty, tx) computes rows 4ty .. 4ty+3 of column tx:
+// for each dc it slides a window of four A values down the column, so each
+// shared-memory load of A feeds four complex MACs (one per row).
+__device__ __forceinline__ void cmac4(float2 (&acc)[4], float2 w, float2 x0, float2 x1, float2 x2,
+                                      float2 x3) {
+  const float2 x[4] = {x0, x1, x2, x3};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {  // acc += w * x
+    acc[k].x = fma_rn(w.x, x[k].x, acc[k].x);
+    acc[k].x = fma_rn(-w.y, x[k].y, acc[k].x);
+    acc[k].y = fma_rn(w.x, x[k].y, acc[k].y);
+    acc[k].y = fma_rn(w.y, x[k].x, acc[k].y);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_adjs_inner(const StParams p0) {
   const StParams p = member(p0);
   extern __shared__ __align__(16) unsigned char smem_st[];
-  const int P = p.P, Q = p.Q;
+  const int P = p.P, Q = p.Q, DR = 2 * P - 1;
   const int SW = kStTC + 2 * Q - 2, SH = kStTR + 2 * P - 2;
   float2 *As = (float2 *)smem_st;  // [SH][SW]
   float2 *Ws = As + SH * SW;       // [ND]
@@ -151,35 +181,47 @@ __global__ void __launch_bounds__(256) k_adjs_inner(const StParams p0) {
   }
   __syncthreads();
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float2 acc[2];
+  float2 acc[4];
 #pragma unroll
-  for (int k = 0; k < 2; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int k = 0; k < 4; ++k) acc[k] = make_float2(0.f, 0.f);
   for (int dc = 0; dc < 2 * Q - 1; ++dc) {
-    const float2 *wrow = Ws + dc * (2 * P - 1);
-    const float2 *arow = As + ty * SW + tx + dc;
-    for (int dr = 0; dr < 2 * P - 1; ++dr) {
-      const float2 w = wrow[dr];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {  // acc += w * A[n + dr][m + dc]
-        const float2 a = arow[(dr + 8 * k) * SW];
-        acc[k].x = fma_rn(w.x, a.x, acc[k].x);
-        acc[k].x = fma_rn(-w.y, a.y, acc[k].x);
-        acc[k].y = fma_rn(w.x, a.y, acc[k].y);
-        acc[k].y = fma_rn(w.y, a.x, acc[k].y);
-      }
+    const float2 *wv = Ws + dc * DR;
+    const float2 *col = As + (4 * ty) * SW + tx + dc;  // row 4ty of the window at dr = 0
+    float2 a0 = col[0], a1 = col[SW], a2 = col[2 * SW];
+    int dr = 0;
+    // rows used at lag dr: 4ty+dr .. 4ty+dr+3 (at most 4ty+2P+1 < SH)
+    for (; dr + 4 <= DR; dr += 4) {
+      const float2 a3 = col[(dr + 3) * SW];
+      cmac4(acc, wv[dr], a0, a1, a2, a3);
+      const float2 a4 = col[(dr + 4) * SW];
+      cmac4(acc, wv[dr + 1], a1, a2, a3, a4);
+      const float2 a5 = col[(dr + 5) * SW];
+      cmac4(acc, wv[dr + 2], a2, a3, a4, a5);
+      const float2 a6 = col[(dr + 6) * SW];
+      cmac4(acc, wv[dr + 3], a3, a4, a5, a6);
+      a0 = a4;
+      a1 = a5;
+      a2 = a6;
+    }
+    for (; dr < DR; ++dr) {
+      const float2 a3 = col[(dr + 3) * SW];
+      cmac4(acc, wv[dr], a0, a1, a2, a3);
+      a0 = a1;
+      a1 = a2;
+      a2 = a3;
     }
   }
   const int m = m0 + tx;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int n = n0 + ty + 8 * k;
+  for (int k = 0; k < 4; ++k) {
+    const int n = n0 + 4 * ty + k;
     if (n - (P - 1) < n_in && m - (Q - 1) < m_in) p.dA[(long long)n * p.M + m] = acc[k];
   }
 }
 
 // Fringe elements (outside the inner box), one warp each: lanes take the
-// combinations Delta in turn (coalesced weights of the element's row and
-// column class from the table), then a warp sum.
+// column lags (coalesced loads of A), a loop takes the row lags, weights of
+// the element's row and column class from the table, then a warp sum.
 __global__ void __launch_bounds__(256) k_adjs_fringe(const StParams p0, long long n_fringe) {
   const StParams p = member(p0);
   const long long idx = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -204,16 +246,21 @@ __global__ void __launch_bounds__(256) k_adjs_fringe(const StParams p0, long lon
   const int rc = row_class(n, P, p.Hn), cc = row_class(m, Q, p.W);
   const float2 *Tc = p.T + (long long)(rc * p.NCC + cc) * p.ND;
   float sr = 0.f, si = 0.f;
-  for (int di = lane; di < p.ND; di += 32) {
-    const int dr = di % (2 * P - 1) - (P - 1), dc = di / (2 * P - 1) - (Q - 1);
-    const int nn = n + dr, mm = m + dc;
-    if (nn < 0 || nn >= N || mm < 0 || mm >= M) continue;
-    const float2 w = __ldg(Tc + di);
-    const float2 a = __ldg(p.A + (long long)nn * p.lda + mm);
-    sr = fma_rn(w.x, a.x, sr);
-    sr = fma_rn(-w.y, a.y, sr);
-    si = fma_rn(w.x, a.y, si);
-    si = fma_rn(w.y, a.x, si);
+  // lanes over the column lags (coalesced A rows), a loop over the row lags
+  for (int c0 = 0; c0 < 2 * Q - 1; c0 += 32) {
+    const int dci = c0 + lane, mm = m + dci - (Q - 1);
+    const bool cok = dci < 2 * Q - 1 && mm >= 0 && mm < M;
+    for (int dri = 0; dri < 2 * P - 1; ++dri) {
+      const int nn = n + dri - (P - 1);
+      if (nn < 0 || nn >= N) continue;  // uniform over the warp
+      if (!cok) continue;
+      const float2 w = __ldg(Tc + dri + (2 * P - 1) * dci);
+      const float2 a = __ldg(p.A + (long long)nn * p.lda + mm);
+      sr = fma_rn(w.x, a.x, sr);
+      sr = fma_rn(-w.y, a.y, sr);
+      si = fma_rn(w.x, a.y, si);
+      si = fma_rn(w.y, a.x, si);
+    }
   }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
@@ -257,7 +304,7 @@ cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, lo
   p.sG = sG;
   p.sdA = sdA;
   p.sT = (long long)p.ND * p.NRC * p.NCC;
-  const size_t wsm = (size_t)(P + 1) * (Q + 1) * sizeof(double2);
+  const size_t wsm = (size_t)2 * P * Q * sizeof(float2);
   k_adjs_weights<<<dim3((unsigned)p.ND, (unsigned)batch), 256, wsm, s>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
