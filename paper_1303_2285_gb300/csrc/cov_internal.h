@@ -145,7 +145,7 @@ struct RecParams {
   // workspace
   unsigned *status;
   void *core_part;      // [n_uc][n_rb][n_cb]
-  void *colsum_part;    // [n_uc][NFC][n_rb]
+  void *colsum_part;    // [n_uc][n_rb][NFC]
   void *sin_part;       // [n_uc][NFR][NCH]
   void *rowval;         // [n_uc][Q][NFR]
   void *colval;         // [n_uc][Q]

@@ -170,7 +170,7 @@ __device__ __forceinline__ void product_task(const RecParams &p, long long tile,
     for (int k = 0; k < G; ++k)
       if (k < cnt) {
         const int D = combo_index(p.P, d0 + k, dc);
-        cs[((long long)D * p.NFC + fc) * p.n_rb + rb] = acc[k];
+        cs[((long long)D * p.n_rb + rb) * p.NFC + fc] = acc[k];  // lanes: consecutive fc
       }
   }
   T v[2 * G];

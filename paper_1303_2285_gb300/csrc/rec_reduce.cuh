@@ -76,15 +76,16 @@ __device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int
   // summed over the row blocks
   T lr = 0, li = 0, rr = 0, ri = 0;
   if (lane < Q - 1) {
-    const C2 *csl = (const C2 *)p.colsum_part + ((long long)D * p.NFC + lane) * p.n_rb;
-    const C2 *csr = csl + (long long)(Q - 1) * p.n_rb;
+    // partials [D][rb][fc]: lane's left column fc = lane, right fc = Q-1+lane
+    const C2 *csl = (const C2 *)p.colsum_part + (long long)D * p.n_rb * p.NFC + lane;
+    const C2 *csr = csl + (Q - 1);
     Neu<T> a, b, c, d;
     for (int rb0 = 0; rb0 < p.n_rb; rb0 += 4) {
       C2 x[4], y[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        x[u] = rb0 + u < p.n_rb ? csl[rb0 + u] : czero<C2>();
-        y[u] = rb0 + u < p.n_rb ? csr[rb0 + u] : czero<C2>();
+        x[u] = rb0 + u < p.n_rb ? csl[(long long)(rb0 + u) * p.NFC] : czero<C2>();
+        y[u] = rb0 + u < p.n_rb ? csr[(long long)(rb0 + u) * p.NFC] : czero<C2>();
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
