@@ -51,13 +51,18 @@ __device__ __forceinline__ unsigned long long swap2(unsigned long long a) {
   return pk2(v.y, v.x);
 }
 
+// |x| in x's own precision (an FP32 compare must not round-trip via FP64,
+// whose pipe is narrow).
+__device__ __forceinline__ float abs_of(float x) { return fabsf(x); }
+__device__ __forceinline__ double abs_of(double x) { return fabs(x); }
+
 // Compensated (Neumaier) running sum: the error of each addition is kept in c.
 template <typename T> struct Neu {
   T s, c;
   __device__ __forceinline__ Neu() : s(0), c(0) {}
   __device__ __forceinline__ void add(T x) {
     const T t = s + x;
-    c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+    c += (abs_of(s) >= abs_of(x)) ? ((s - t) + x) : ((x - t) + s);
     s = t;
   }
   __device__ __forceinline__ void merge(T s2, T c2) {

@@ -146,7 +146,7 @@ struct RecParams {
   unsigned *status;
   void *core_part;      // [n_uc][n_rb][n_cb]
   void *colsum_part;    // [n_uc][n_rb][NFC]
-  void *sin_part;       // [n_uc][NFR][NCH]
+  void *sin_part;       // [n_uc][NCH][NFR]
   void *rowval;         // [n_uc][Q][NFR]
   void *colval;         // [n_uc][Q]
 };

@@ -91,7 +91,7 @@ __device__ __forceinline__ void fringe_pair(const RecParams &p, const typename C
   for (int dc = 0; dc < QMAX; ++dc) {
     if (dc < p.dc_lo || dc >= p.dc_hi || (dc == 0 && dr < 0)) continue;
     const int D = combo_index(P, dr, dc);
-    out[((long long)D * p.NFR + fr) * p.NCH + cc] = acc[dc];
+    out[((long long)D * p.NCH + cc) * p.NFR + fr] = acc[dc];
   }
 }
 

@@ -17,9 +17,9 @@
 // skips the remaining work; no wait is unbounded.
 //
 // Memory visibility: data produced by other CTAs (partials, RV, CV) is read
-// only after a grid barrier (release by __threadfence before the arrival,
-// acquire load of the counter), and no CTA reads those addresses earlier in
-// the launch, so no stale copy can sit in its L1.
+// only after a grid barrier (release fence before the arrival, acquire load
+// of the counter), and no CTA reads those addresses earlier in the launch, so
+// no stale copy can sit in its L1.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -36,13 +36,16 @@ constexpr int kCtlFringe = 2;   // next fringe-row task
 
 // Grid-wide barrier: arrival `target / gridDim.x` of every CTA. Returns false
 // (and records COV_ETIMEOUT) if the other CTAs do not arrive within the limit.
+// Release/acquire only: the CTA barrier orders the CTA's writes before thread
+// 0's release pattern (fence.acq_rel + the arrival), whose acquire load of the
+// counter is ordered before the CTA's later reads by the closing CTA barrier.
 __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
                                              unsigned *status) {
   __syncthreads();
   int failed = 0;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(counter, 1u);
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0;; ++it) {
       unsigned v;
@@ -55,7 +58,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned *counter, unsigned target,
       }
       __nanosleep(32);
     }
-    __threadfence();
   }
   return __syncthreads_or(failed) == 0;
 }
@@ -86,7 +88,8 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
 
   // ---- 2. fringe rows x inner columns, tasks (side, chunk, pair block) ---
   // a task's (fringe row, row lag) pairs: at most one per thread, blocks of
-  // equal size
+  // equal size (finer tasks, four threads a pair, measured slower: their
+  // extra shuffles and claims cost more than the shorter tail saves)
   const int npairs = (p.P - 1) * (2 * p.P - 1);
   const int npb = (npairs + (int)blockDim.x - 1) / (int)blockDim.x;
   const int n_ftasks = p.NFR > 0 ? 2 * p.NCH * npb : 0;
@@ -109,10 +112,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
   // ---- 3. reductions (warp tasks) ------------------------------------------
   ok = grid_barrier(&ctl[kCtlBarrier], gridDim.x, p.status) && ok;
   if (ok) {
-    const int nw = blockDim.x >> 5;
-    const long long total = reduce_tasks(p);
-    for (long long w = (long long)blockIdx.x * nw + warp; w < total; w += (long long)gridDim.x * nw)
-      reduce_task<float>(p, w, lane);
+    // task w on warp w / gridDim.x of CTA w % gridDim.x: spread over all SMs
+    const int total = reduce_tasks(p), nw = blockDim.x >> 5;
+    for (int w = warp * (int)gridDim.x + (int)blockIdx.x; w < total; w += (int)gridDim.x * nw)
+      reduce_task<float, QMAX>(p, w, lane);
   }
 
   // ---- 4. seed, walk and write the blocks of R -----------------------------

@@ -8,12 +8,12 @@
 namespace cov {
 
 // Kernel 3: one warp per reduction task (reduce_task).
-template <typename T>
+template <typename T, int QMAX>
 __global__ void __launch_bounds__(128) k_reduce(const RecParams p) {
   pdl_launch_dependents();
   pdl_wait();  // the product and fringe-row kernels' partials
-  const long long w = (long long)blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (w < reduce_tasks(p)) reduce_task<T>(p, w, threadIdx.x & 31);
+  const int w = (int)blockIdx.x * 4 + (int)(threadIdx.x >> 5);
+  if (w < reduce_tasks(p)) reduce_task<T, QMAX>(p, w, threadIdx.x & 31);
 }
 
 // Kernel 4: one CTA per block (bj, bj + dc) of R.
@@ -26,12 +26,20 @@ __global__ void __launch_bounds__(256) k_walk_write(const RecParams p) {
   walk_block<T>(p, dc, bj, smem_k4);
 }
 
+template <typename T, int QMAX>
+static cudaError_t launch_reduce_q(const RecParams &p, cudaStream_t s, bool pdl) {
+  const int blocks = (reduce_tasks(p) + 3) / 4;  // 4 warps a block
+  const cudaError_t e = ensure_smem_attr(k_reduce<T, QMAX>, 0);
+  if (e != cudaSuccess) return e;
+  return launch_k(k_reduce<T, QMAX>, dim3((unsigned)blocks), dim3(128), 0, s, pdl, p);
+}
+
+// QMAX >= Q: the register count of the box-row task's running sums
 template <typename T>
 static cudaError_t launch_reduce_t(const RecParams &p, cudaStream_t s, bool pdl) {
-  const long long blocks = (reduce_tasks(p) + 3) / 4;  // 4 warps a block
-  const cudaError_t e = ensure_smem_attr(k_reduce<T>, 0);
-  if (e != cudaSuccess) return e;
-  return launch_k(k_reduce<T>, dim3((unsigned)blocks), dim3(128), 0, s, pdl, p);
+  if (p.Q <= 8) return launch_reduce_q<T, 8>(p, s, pdl);
+  if (p.Q <= 16) return launch_reduce_q<T, 16>(p, s, pdl);
+  return launch_reduce_q<T, 32>(p, s, pdl);
 }
 
 template <typename T>

@@ -14,8 +14,8 @@ namespace cov {
 //    sums CS over inner rows, and CV[D][j] = core + the fringe-column sums
 //    inside the box of column offset j (suffix scan over the left fringe
 //    columns, prefix scan over the right ones);
-//  - per (D, fringe row fr): S_in = sum of the row's partials, the row's own
-//    fringe-column products (one per lane, each formed once) and the box-row
+//  - per D, one lane per fringe row fr: S_in = sum of the row's partials,
+//    the row's own fringe-column products (each formed once) and the box-row
 //    sums RV[D][j][fr] = S_in + the fringe-column products inside the box.
 // ---------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ T warp_sum(T x) {
@@ -119,91 +119,87 @@ __device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int
   }
 }
 
-// Fringe rows per RV warp task (their loads are issued together). One row
-// a task measured fastest: more warps in flight beat longer tasks.
-constexpr int kRowsPerTask = 1;
-
-// Warp task: the box-row sums RV[D][j][fr] of the fringe rows
-// fr0 .. fr0+kRowsPerTask-1 (those < NFR) for every column offset j: S_in
-// from the chunk partials plus each row's own fringe-column products (each
-// formed once), with prefix and suffix scans over the fringe columns.
-template <typename T>
-__device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int fr0, int lane) {
+// Warp task: the box-row sums RV[D][j][fr] of every fringe row fr of
+// combination D, one lane per fringe row (no cross-lane traffic): S_in = the
+// sum of the row's chunk partials (sin_part is [D][chunk][fr], so the lanes'
+// loads are contiguous), plus the row's own fringe-column products (each
+// formed once) inside the box of column offset j: a suffix over the left
+// fringe columns k >= j and a prefix over the right ones k < j, both running
+// sums in registers. The lane's J = Q - dc outputs are stored per j, lanes
+// again contiguous.
+template <typename T, int QMAX>
+__device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int lane) {
   using C2 = typename C2t<T>::type;
-  constexpr int RF = kRowsPerTask;
-  const int P = p.P, Q = p.Q, W = p.M - p.Q + 1, NFR = p.NFR;
+  const int P = p.P, Q = p.Q, W = p.M - p.Q + 1, NFR = p.NFR, NCH = p.NCH;
   int dr, dc;
   combo_of(P, D, dr, dc);
+  const int J = Q - dc;
   const C2 *A = (const C2 *)p.A;
-  C2 a0[RF], b0[RF], a1[RF], b1[RF];
-  bool has_r[RF];
-  T sr[RF], si[RF];
-  // all loads of the RF rows first
-#pragma unroll
-  for (int f = 0; f < RF; ++f) {
-    const int fr = fr0 + f;
+  const C2 *sin_d = (const C2 *)p.sin_part + (long long)D * NCH * NFR;
+  C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR;
+  for (int fr = lane; fr < NFR; fr += 32) {
     const int n = fr < P - 1 ? fr : (p.N - P + 1) + (fr - (P - 1));
-    const bool rowok = fr < NFR && n + dr >= 0 && n + dr < p.N;
-    a0[f] = b0[f] = a1[f] = b1[f] = czero<C2>();
-    has_r[f] = rowok && lane < Q - 1 && W + lane + dc < p.M;
-    if (rowok && lane < Q - 1) {
+    const bool rowok = n + dr >= 0 && n + dr < p.N;
+    // S_in: four interleaved partial sums over the chunks, 16 loads in
+    // flight per round
+    T sr[4] = {T(0), T(0), T(0), T(0)}, si[4] = {T(0), T(0), T(0), T(0)};
+    const C2 *sp = sin_d + fr;
+    for (int cc = 0; cc < NCH; cc += 16) {
+      C2 x[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) x[u] = cc + u < NCH ? sp[(long long)(cc + u) * NFR] : czero<C2>();
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        sr[u & 3] += x[u].x;
+        si[u & 3] += x[u].y;
+      }
+    }
+    const T s_r = (sr[0] + sr[1]) + (sr[2] + sr[3]);
+    const T s_i = (si[0] + si[1]) + (si[2] + si[3]);
+    // out[j] = suffix of the left fringe-column products (k >= j)
+    T outr[QMAX], outi[QMAX];
+    {
       const C2 *An = A + (long long)n * p.lda;
       const C2 *Ab = A + (long long)(n + dr) * p.lda + dc;
-      a0[f] = __ldg(An + lane);
-      b0[f] = __ldg(Ab + lane);
-      if (has_r[f]) {
-        a1[f] = __ldg(An + W + lane);
-        b1[f] = __ldg(Ab + W + lane);
-      }
-    }
-    sr[f] = si[f] = T(0);
-    if (fr < NFR) {
-      const C2 *sp = (const C2 *)p.sin_part + ((long long)D * NFR + fr) * p.NCH;
-      for (int cc = lane; cc < p.NCH; cc += 32) {
-        const C2 x = sp[cc];
-        sr[f] += x.x;
-        si[f] += x.y;
-      }
-    }
-  }
-  const int J = Q - dc;
+      C2 acc = czero<C2>();
 #pragma unroll
-  for (int f = 0; f < RF; ++f) {
-    const int fr = fr0 + f;
-    C2 lft = czero<C2>(), rgt = czero<C2>();
-    cmac_conj(lft, a0[f], b0[f]);
-    if (has_r[f]) cmac_conj(rgt, a1[f], b1[f]);
-    const T s_r = warp_sum(sr[f]), s_i = warp_sum(si[f]);
-    const T lsr = scan_suffix(lft.x, lane), lsi = scan_suffix(lft.y, lane);
-    T rpr = scan_incl(rgt.x, lane), rpi = scan_incl(rgt.y, lane);
-    rpr = __shfl_up_sync(0xffffffffu, rpr, 1);
-    rpi = __shfl_up_sync(0xffffffffu, rpi, 1);
-    if (lane == 0) rpr = rpi = T(0);
-    if (fr < NFR && lane < J) {
-      C2 o;
-      o.x = s_r + (lane < Q - 1 ? lsr : T(0)) + rpr;
-      o.y = s_i + (lane < Q - 1 ? lsi : T(0)) + rpi;
-      ((C2 *)p.rowval)[((long long)D * Q + lane) * NFR + fr] = o;
+      for (int k = QMAX - 1; k >= 0; --k) {
+        if (rowok && k < Q - 1) cmac_conj(acc, __ldg(An + k), __ldg(Ab + k));
+        outr[k] = acc.x;
+        outi[k] = acc.y;
+      }
+    }
+    // + prefix of the right fringe-column products (k < j), then store
+    {
+      const C2 *An = A + (long long)n * p.lda + W;
+      const C2 *Ab = A + (long long)(n + dr) * p.lda + W + dc;
+      C2 acc = czero<C2>();
+#pragma unroll
+      for (int j = 0; j < QMAX; ++j) {
+        if (j < J) {
+          C2 o;
+          o.x = s_r + outr[j] + acc.x;
+          o.y = s_i + outi[j] + acc.y;
+          rv[(long long)j * NFR + fr] = o;
+        }
+        if (rowok && j < Q - 1 && W + j + dc < p.M) cmac_conj(acc, __ldg(An + j), __ldg(Ab + j));
+      }
     }
   }
 }
 
-// Reduction warp task w of the shard: [0, n_own) the combinations (CV), then
-// (combination, block of kRowsPerTask fringe rows) pairs (RV).
-__host__ __device__ __forceinline__ long long reduce_tasks(const RecParams &p) {
-  const long long n_own = p.u_hi - p.u_lo;
-  return n_own * (1 + (p.NFR + kRowsPerTask - 1) / kRowsPerTask);
+// Reduction warp task w of the shard: [0, n_own) the combinations' CV, then
+// [n_own, 2 n_own) their RV.
+__host__ __device__ __forceinline__ int reduce_tasks(const RecParams &p) {
+  return 2 * (p.u_hi - p.u_lo);
 }
-template <typename T>
-__device__ __forceinline__ void reduce_task(const RecParams &p, long long w, int lane) {
-  const long long n_own = p.u_hi - p.u_lo;
-  if (w < n_own) {
-    reduce_combo_warp<T>(p, p.u_lo + (int)w, lane);
-  } else {
-    const int nb = (p.NFR + kRowsPerTask - 1) / kRowsPerTask;
-    const long long w2 = w - n_own;
-    reduce_rows_warp<T>(p, p.u_lo + (int)(w2 / nb), (int)(w2 % nb) * kRowsPerTask, lane);
-  }
+template <typename T, int QMAX>
+__device__ __forceinline__ void reduce_task(const RecParams &p, int w, int lane) {
+  const int n_own = p.u_hi - p.u_lo;
+  if (w < n_own)
+    reduce_combo_warp<T>(p, p.u_lo + w, lane);
+  else
+    reduce_rows_warp<T, QMAX>(p, p.u_lo + (w - n_own), lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -265,22 +261,29 @@ __device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, u
     const C2 *RV = RVs + (dr + P - 1) * NFR;
     const C2 cv = CVs[dr + P - 1];
     // seed: the direct sum over the box of output (is, bj): the top fringe
-    // rows n in [is, P-2] and the bottom fringe rows N-P+1+k, k < is
-    Neu<T> orr, oii;
+    // rows n in [is, P-2] and the bottom fringe rows N-P+1+k, k < is, i.e.
+    // the staged entries RV[is .. is+P-2], one contiguous range; two
+    // interleaved compensated sums (independent chains), merged
+    Neu<T> orr, oii, o2r, o2i;
     orr.add(cv.x);
     oii.add(cv.y);
-#pragma unroll
-    for (int n = 0; n < kMaxPQ - 1; ++n)
-      if (n >= is && n <= P - 2) {
-        orr.add(RV[n].x);
-        oii.add(RV[n].y);
+    {
+      const int ue = is + P - 1;
+      int u = is;
+      for (; u + 2 <= ue; u += 2) {
+        const C2 a = RV[u], b = RV[u + 1];
+        orr.add(a.x);
+        oii.add(a.y);
+        o2r.add(b.x);
+        o2i.add(b.y);
       }
-#pragma unroll
-    for (int k = 0; k < kMaxPQ - 1; ++k)
-      if (k < is) {
-        orr.add(RV[P - 1 + k].x);
-        oii.add(RV[P - 1 + k].y);
+      if (u < ue) {
+        orr.add(RV[u].x);
+        oii.add(RV[u].y);
       }
+      orr.merge(o2r.s, o2r.c);
+      oii.merge(o2i.s, o2i.c);
+    }
     for (int i = is; i < ie; ++i) {
       T re = orr.value(), im = oii.value();
       if (p.mean) {
