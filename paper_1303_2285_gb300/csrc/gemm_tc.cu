@@ -4,19 +4,23 @@
 // Real form: Y = [Re X; Im X] (2PQ x K) and B = Y Y^T, so that
 //   Re R[a][b] = B[a][b] + B[D+a][D+b],  Im R[a][b] = B[D+a][b] - B[a][D+b].
 // B is symmetric; only its upper 128 x 128 tiles are formed. A CTA owns one
-// tile and one range of the windows (split-K). Per K-step of 32 windows (one
-// window row p, 32 consecutive q) the A region those windows read (P rows x
-// 32+Q-1 columns) is staged by one TMA load into a 3-deep ring, two steps
-// ahead; all threads then build the operand tiles in shared memory from it
-// (K-major core-matrix layout, no swizzle) with each value split into TF32
-// hi + lo; one thread issues the three products hi*hi + hi*lo + lo*hi as
-// tcgen05.mma kind::tf32 (M = N = 128, K = 8) and commits them to an
-// mbarrier, while the other threads build the next stage. Accumulation runs
-// in TMEM: chunk accumulators of 4 K-steps alternate between two 128-column
-// regions and are added (FP32, round to nearest, tcgen05.ld / st) into a
-// third region, the running sum. A second kernel sums the K-split partials
-// in a fixed order (FP64) and assembles R. Shapes whose region does not fit
-// the ring build the operands from A in global memory instead.
+// tile and one range of the windows (split-K), and is warp-specialised:
+//  - eight filler warps build the operand tiles of each K-step (16 windows:
+//    one window row p, 16 consecutive q) in shared memory (K-major
+//    core-matrix layout, no swizzle), each value split into TF32 hi + lo,
+//    from the A region those windows read (P rows x 16+Q-1 columns), which a
+//    TMA load stages into a ring of up to 12 slots, as many steps ahead; a
+//    stage is handed over by one mbarrier arrival per warp;
+//  - one thread of the ninth warp issues the three products hi*hi + hi*lo +
+//    lo*hi as tcgen05.mma kind::tf32 (M = N = 128, K = 8) and commits each
+//    stage back to its fillers, four stages deep.
+// Accumulation runs in TMEM: chunk accumulators of 8 K-steps alternate
+// between two 128-column regions; the filler warps add each finished chunk
+// (FP32, round to nearest, tcgen05.ld / st) into a third region, the running
+// sum, half a chunk later, before the accumulator is reused. A second kernel
+// sums the K-split partials in a fixed order (FP64) and assembles R. Shapes
+// whose region does not fit the ring build the operands from A in global
+// memory instead.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,13 +35,20 @@
 namespace cov {
 
 constexpr int kGT = 128;         // tile rows / columns of B
-constexpr int kGKW = 32;         // windows per K-step (TF32: 128-byte rows)
-constexpr int kGThreads = 256;
-constexpr int kGTileBytes = kGT * kGKW * 4;  // 16 KB per operand tile
+constexpr int kGKW = 16;         // windows per K-step (TF32: 64-byte rows)
+constexpr int kGStages = 4;      // operand stages in flight
+constexpr int kGFillWarps = 8;   // operand builders; one more warp issues the MMAs
+constexpr int kGFillThreads = kGFillWarps * 32;
+constexpr int kGThreads = kGFillThreads + 32;
+constexpr int kGTileBytes = kGT * kGKW * 4;  // 8 KB per operand tile
+constexpr int kGStageBytes = 4 * kGTileBytes;  // A_hi, A_lo, B_hi, B_lo
 constexpr unsigned long long kGWaitNs = 2000000000ull;
-constexpr int kGRegStages = 3;             // A regions in flight
+constexpr int kGRegMaxStages = 12;         // A regions in flight (at most)
+constexpr int kGRegRingBytes = 49152;      // the region ring
 constexpr int kGRegMaxBytes = 16384;       // one region: P rows x RWf floats
 constexpr unsigned kGRunCol = 256;         // TMEM columns of the running sum
+constexpr int kGBars = 2 * kGStages + 2 + 2 * kGRegMaxStages + 1;
+constexpr size_t kGSmemBytes = (size_t)kGStages * kGStageBytes + (size_t)kGRegRingBytes + 512;
 
 struct GemmParams {
   const float2 *A;
@@ -51,14 +62,16 @@ struct GemmParams {
   long long K;
   int mean;
   int use_tma, RWf;  // A region per K-step: P rows x RWf floats, staged by TMA
+  int RS, RSLOT;     // region slots in the ring (RS steps of prefetch) and slot bytes
 };
 
 __device__ __forceinline__ uint64_t smem_desc(unsigned addr) {
   // K-major, no swizzle: core matrices of 8 rows x 16 bytes; 128 B between
-  // core matrices along K (leading), 1024 B along M/N (stride); version 1.
+  // core matrices along K (leading), 512 B along M/N (stride: the 4 core
+  // matrices of a 16-window row group); version 1.
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
   d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((1024u >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
@@ -80,20 +93,23 @@ __device__ __forceinline__ void tile_of(int t, int nt, int &ti, int &tj) {
   tj = i + rem;
 }
 
-// One thread's four (row, 4-window chunk) items of an operand tile: rows are
-// fixed for the whole kernel, so their (component, i, j) are decoded once.
+// One filler thread's two (row, 4-window chunk) items of an operand tile:
+// rows are fixed for the whole kernel, so their (component, i, j) are decoded
+// once.
 struct GItem {
   int ok, comp, i, col, qoff, soff;  // col: A column of the chunk's first window; soff: tile offset
 };
 
-__device__ __forceinline__ void build_items(const GemmParams &p, int tile_row0, GItem (&it)[4]) {
+__device__ __forceinline__ void build_items(const GemmParams &p, int tile_row0, GItem (&it)[2]) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int item = threadIdx.x + u * kGThreads;  // 1024 items: 128 rows x 8 chunks
-    const int r8 = item & 7, chunk = (item >> 3) & 7, rg = item >> 6;
+  for (int u = 0; u < 2; ++u) {
+    // 512 items: 128 rows x 4 chunks; a warp's lanes take 32 consecutive rows
+    // of one chunk (their region reads then meet at most two to a bank)
+    const int item = threadIdx.x + u * kGFillThreads;
+    const int r8 = item & 7, chunk = (item >> 5) & 3, rg = ((item >> 7) << 2) | ((item >> 3) & 3);
     const int row = rg * 8 + r8;
     const int r = tile_row0 + row;
-    it[u].soff = rg * 256 + chunk * 32 + r8 * 4;  // (rg*1024 + chunk*128 + r8*16) bytes / 4
+    it[u].soff = rg * 128 + chunk * 32 + r8 * 4;  // (rg*512 + chunk*128 + r8*16) bytes / 4
     it[u].ok = r < 2 * p.D;
     const int a = r % p.D;
     it[u].comp = r >= p.D ? 1 : 0;
@@ -103,10 +119,10 @@ __device__ __forceinline__ void build_items(const GemmParams &p, int tile_row0, 
   }
 }
 
-__device__ __forceinline__ void fill_tile(const GemmParams &p, const GItem (&it)[4], int pw, int q0,
+__device__ __forceinline__ void fill_tile(const GemmParams &p, const GItem (&it)[2], int pw, int q0,
                                           float *hi, float *lo) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 2; ++u) {
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (it[u].ok) {
       const float2 *src = p.A + (long long)(pw + it[u].i) * p.lda + q0 + it[u].col;
@@ -134,10 +150,10 @@ __device__ __forceinline__ void fill_tile(const GemmParams &p, const GItem (&it)
 
 // The same operand tile from the staged A region: reg[r * RWf + 2c + comp]
 // holds component comp of A[pw + r][q0 + c].
-__device__ __forceinline__ void fill_tile_smem(const GemmParams &p, const GItem (&it)[4], int q0,
+__device__ __forceinline__ void fill_tile_smem(const GemmParams &p, const GItem (&it)[2], int q0,
                                                const float *reg, float *hi, float *lo) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 2; ++u) {
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (it[u].ok) {
       const float *src = reg + it[u].i * p.RWf + 2 * it[u].col + it[u].comp;
@@ -168,12 +184,12 @@ __device__ __forceinline__ void mma_tf32(unsigned tmem, uint64_t ad, uint64_t bd
       : "memory");
 }
 
-// TMEM accumulators hold at most kGChunk K-steps: the tensor core's FP32
-// accumulation is not round-to-nearest, so long chains drift. Chunks
-// alternate between two accumulators; each finished chunk is added (FP32,
-// round to nearest) into the running sum one chunk later, while the tensor
-// core works on the other accumulator.
-constexpr int kGChunk = 4;
+// TMEM accumulators hold at most kGChunk K-steps (128 windows): the tensor
+// core's FP32 accumulation is not round-to-nearest, so long chains drift.
+// Chunks alternate between two accumulators; each finished chunk is added
+// (FP32, round to nearest) into the running sum while the tensor core works
+// on the other accumulator.
+constexpr int kGChunk = 8;
 
 #define COV_R32(r)                                                                              \
   "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),          \
@@ -204,7 +220,8 @@ __device__ __forceinline__ void tmem_st32(unsigned taddr, const unsigned (&r)[32
 }
 
 // Adds TMEM accumulator `acc_col` (128 x 128 FP32) into the running sum
-// (`first`: copies it): warp w takes lane quadrant w % 4 and column half w / 4.
+// (`first`: copies it): filler warp w takes lane quadrant w % 4 and column
+// half w / 4.
 __device__ __forceinline__ void flush_acc(unsigned tmem, unsigned acc_col, bool first) {
   const int warp = threadIdx.x >> 5;
   const int quad = warp & 3, half = warp >> 2;
@@ -227,15 +244,18 @@ __device__ __forceinline__ void flush_acc(unsigned tmem, unsigned acc_col, bool 
 __global__ void __launch_bounds__(kGThreads, 1)
     k_gemm_tf32x3(const GemmParams p, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) unsigned char smem_g[];
-  // two stages x [A_hi, A_lo, B_hi, B_lo], the A-region ring, then the
+  // operand stages x [A_hi, A_lo, B_hi, B_lo], the A-region ring, then the
   // barriers and the TMEM address
   float *stage_base = (float *)smem_g;
-  float *reg_base = (float *)(smem_g + 2 * 4 * kGTileBytes);
-  uint64_t *bars = (uint64_t *)((unsigned char *)reg_base + kGRegStages * kGRegMaxBytes);
-  uint64_t *mma_done = bars;        // [2] per smem stage
-  uint64_t *chunk_done = bars + 2;  // [2] per TMEM accumulator
-  uint64_t *reg_full = bars + 4;    // [3] per region stage
-  unsigned *tmem_slot = (unsigned *)(bars + 4 + kGRegStages);
+  unsigned char *reg_base = smem_g + kGStages * kGStageBytes;
+  uint64_t *bars = (uint64_t *)(reg_base + kGRegRingBytes);
+  uint64_t *full = bars;                          // [stages] built: one arrival per filler warp
+  uint64_t *empty = full + kGStages;              // [stages] read by the tensor core (commit)
+  uint64_t *chunk_done = empty + kGStages;        // [2] a chunk accumulator is complete (commit)
+  uint64_t *reg_full = chunk_done + 2;              // [RS] A region landed (TMA)
+  uint64_t *reg_empty = reg_full + kGRegMaxStages;  // [RS] A region read by every filler warp
+  uint64_t *mma_fin = reg_empty + kGRegMaxStages;   // every issued MMA has completed
+  unsigned *tmem_slot = (unsigned *)(bars + kGBars);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tile = blockIdx.x % p.ntiles, split = blockIdx.x / p.ntiles;
   int ti, tj;
@@ -253,78 +273,147 @@ __global__ void __launch_bounds__(kGThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int b = 0; b < 4 + kGRegStages; ++b) mbar_init(&bars[b], 1);
+    for (int b = 0; b < kGStages; ++b) {
+      mbar_init(&full[b], kGFillWarps);
+      mbar_init(&empty[b], 1);
+    }
+    mbar_init(&chunk_done[0], 1);
+    mbar_init(&chunk_done[1], 1);
+    for (int b = 0; b < kGRegMaxStages; ++b) {
+      mbar_init(&reg_full[b], 1);
+      mbar_init(&reg_empty[b], kGFillWarps);
+    }
+    mbar_init(mma_fin, 1);
     fence_mbar_init();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = *tmem_slot;
-
-  // the A region of K-step k (TMA, complete_tx on reg_full[k % 3])
-  auto issue_region = [&](long long k) {
-    const long long step = s0 + k;
-    const int pw = (int)(step / p.qsteps), q0 = (int)(step % p.qsteps) * kGKW;
-    const int b = (int)(k % kGRegStages);
-    mbar_arrive_expect_tx(&reg_full[b], reg_bytes);
-    tma_load_2d((unsigned char *)reg_base + b * kGRegMaxBytes, &tmap, 2 * q0, pw, &reg_full[b]);
-  };
-  long long issued = 0;
-  if (p.use_tma && tid == 0)
-    for (; issued < 2 && issued < nk; ++issued) issue_region(issued);
-
-  GItem ia[4], ib[4];
-  build_items(p, ti * kGT, ia);
-  build_items(p, tj * kGT, ib);
-  // D = f32 (bit 4), A = B = tf32 (2), both K-major, N = 128, M = 128
-  const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
   bool ok = true;
-  long long k = 0;
-  for (; k < nk; ++k) {
-    const long long step = s0 + k;
-    const int st = (int)(k & 1);
-    const long long chunk = k / kGChunk;
-    const bool chunk_start = (k % kGChunk) == 0;
-    bool w = true;
-    if (k >= 2) w = mbar_wait(&mma_done[st], (unsigned)(((k >> 1) - 1) & 1), kGWaitNs);
-    if (chunk_start && chunk >= 2) {
-      // chunk - 2 used the accumulator this chunk is about to reuse: add it in
-      const long long c = chunk - 2;
-      w = w && mbar_wait(&chunk_done[c & 1], (unsigned)((c >> 1) & 1), kGWaitNs);
+
+  if (warp < kGFillWarps) {
+    // ---- filler warps ------------------------------------------------------
+    // the A region of K-step k into ring slot b (TMA, complete_tx on reg_full)
+    auto issue_region = [&](long long k, int b) {
+      const long long step = s0 + k;
+      const int rpw = (int)(step / p.qsteps), q0 = (int)(step % p.qsteps) * kGKW;
+      mbar_arrive_expect_tx(&reg_full[b], reg_bytes);
+      tma_load_2d(reg_base + b * p.RSLOT, &tmap, 2 * q0, rpw, &reg_full[b]);
+    };
+    long long issued = 0;  // thread 0 only
+    if (p.use_tma && tid == 0)
+      for (; issued < p.RS && issued < nk; ++issued) issue_region(issued, (int)issued);
+    GItem ia[2], ib[2];
+    build_items(p, ti * kGT, ia);
+    build_items(p, tj * kGT, ib);
+    long long flushed = 0;  // chunks added into the running sum
+    // step k's ring slot and its phase parity, and its window row / column
+    // step, kept incrementally (no divisions in the loop)
+    int rslot = 0;
+    unsigned rpar = 0;
+    int pw = (int)(s0 / p.qsteps), qs = (int)(s0 % p.qsteps);
+    long long k = 0;
+    for (; k < nk; ++k) {
+      const int st = (int)(k % kGStages);
+      bool w = ok;
+      // the tensor core has read this stage's previous operands
+      if (w && k >= kGStages) w = mbar_wait(&empty[st], (unsigned)(((k / kGStages) - 1) & 1), kGWaitNs);
+      if (w && p.use_tma) w = mbar_wait(&reg_full[rslot], rpar, kGWaitNs);
+      // half a chunk into chunk c + 1, add chunk c into the running sum: its
+      // accumulator is reused by chunk c + 2, whose first MMA waits for this
+      // warp's arrival on the stage of step 8 (c + 2), issued after this
+      if (w && (k % kGChunk) == kGChunk / 2 && k >= kGChunk + kGChunk / 2) {
+        const long long c = flushed;  // == k / kGChunk - 1
+        w = mbar_wait(&chunk_done[c & 1], (unsigned)((c >> 1) & 1), kGWaitNs);
+        if (w) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          flush_acc(tmem, (unsigned)(c & 1) * 128, c == 0);
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          ++flushed;
+        }
+      }
+      if (!__all_sync(0xffffffffu, w)) {
+        ok = false;
+        break;
+      }
+      float *ahi = stage_base + st * (kGStageBytes / 4);
+      float *alo = ahi + kGTileBytes / 4;
+      float *bhi = alo + kGTileBytes / 4;
+      float *blo = bhi + kGTileBytes / 4;
+      const int q0 = qs * kGKW;
+      if (p.use_tma) {
+        const float *reg = (const float *)(reg_base + rslot * p.RSLOT);
+        fill_tile_smem(p, ia, q0, reg, ahi, alo);
+        if (!diag) fill_tile_smem(p, ib, q0, reg, bhi, blo);
+      } else {
+        fill_tile(p, ia, pw, q0, ahi, alo);
+        if (!diag) fill_tile(p, ib, pw, q0, bhi, blo);
+      }
+      // generic-proxy writes visible to the tensor core, then hand over
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&full[st]);
+        if (p.use_tma) mbar_arrive(&reg_empty[rslot]);
+      }
+      // refill region k's slot with region k + RS once every filler warp has
+      // read region k
+      if (p.use_tma && tid == 0 && issued < nk) {
+        if (mbar_wait(&reg_empty[rslot], rpar, kGWaitNs))
+          issue_region(issued++, rslot);
+        else
+          ok = false;  // this warp leaves the loop at the next step
+      }
+      if (++rslot == p.RS) {
+        rslot = 0;
+        rpar ^= 1u;
+      }
+      if (++qs == p.qsteps) {
+        qs = 0;
+        ++pw;
+      }
     }
-    if (p.use_tma)
-      w = w && mbar_wait(&reg_full[k % kGRegStages], (unsigned)((k / kGRegStages) & 1), kGWaitNs);
-    // the CTA agrees on the outcome, so that a timeout leaves the loop in all
-    // threads together
-    if (__syncthreads_or(!w)) {
-      ok = false;
-      break;
+    // add in the chunks not yet added
+    if (ok && nk > 0) {
+      const long long last = (nk - 1) / kGChunk;
+      for (long long c = flushed; c <= last; ++c) {
+        const bool w = mbar_wait(&chunk_done[c & 1], (unsigned)((c >> 1) & 1), kGWaitNs);
+        if (!__all_sync(0xffffffffu, w)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        flush_acc(tmem, (unsigned)(c & 1) * 128, c == 0);
+      }
     }
-    if (chunk_start && chunk >= 2) {
+    if (p.use_tma && tid == 0) {
+      // regions issued but not consumed (only after a timeout): let them land
+      // before the CTA exits
+      for (long long r = k; r < issued; ++r) {
+        mbar_wait(&reg_full[rslot], rpar, kGWaitNs);
+        if (++rslot == p.RS) {
+          rslot = 0;
+          rpar ^= 1u;
+        }
+      }
+    }
+  } else if (lane == 0) {
+    // ---- MMA issuer -----------------------------------------------------------
+    // D = f32 (bit 4), A = B = tf32 (2), both K-major, N = 128, M = 128
+    const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    for (long long k = 0; k < nk; ++k) {
+      const int st = (int)(k % kGStages);
+      if (!mbar_wait(&full[st], (unsigned)((k / kGStages) & 1), kGWaitNs)) {
+        ok = false;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      flush_acc(tmem, (unsigned)((chunk - 2) & 1) * 128, chunk == 2);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    }
-    float *ahi = stage_base + st * 4 * (kGTileBytes / 4);
-    float *alo = ahi + kGTileBytes / 4;
-    float *bhi = alo + kGTileBytes / 4;
-    float *blo = bhi + kGTileBytes / 4;
-    const int pw = (int)(step / p.qsteps), q0 = (int)(step % p.qsteps) * kGKW;
-    if (p.use_tma) {
-      const float *reg = (const float *)((const unsigned char *)reg_base +
-                                         (k % kGRegStages) * kGRegMaxBytes);
-      fill_tile_smem(p, ia, q0, reg, ahi, alo);
-      if (!diag) fill_tile_smem(p, ib, q0, reg, bhi, blo);
-    } else {
-      fill_tile(p, ia, pw, q0, ahi, alo);
-      if (!diag) fill_tile(p, ib, pw, q0, bhi, blo);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned uah = smem_u32(ahi), ual = smem_u32(alo);
-      const unsigned ubh = diag ? uah : smem_u32(bhi), ubl = diag ? ual : smem_u32(blo);
+      const long long chunk = k / kGChunk;
+      const bool chunk_start = (k % kGChunk) == 0;
+      const float *ahi = stage_base + st * (kGStageBytes / 4);
+      const unsigned uah = smem_u32(ahi), ual = uah + kGTileBytes;
+      const unsigned ubh = diag ? uah : uah + 2 * kGTileBytes, ubl = diag ? ual : uah + 3 * kGTileBytes;
       const unsigned dacc = tmem + (unsigned)(chunk & 1) * 128;
 #pragma unroll
       for (int s = 0; s < kGKW / 8; ++s) {
@@ -336,51 +425,37 @@ __global__ void __launch_bounds__(kGThreads, 1)
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&mma_done[st]))
+              smem_u32(&empty[st]))
           : "memory");
       if ((k % kGChunk) == kGChunk - 1 || k == nk - 1)
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&chunk_done[chunk & 1]))
             : "memory");
-      // the region two steps ahead reuses the buffer step k - 1 read, which
-      // every thread finished before the barrier above
-      if (p.use_tma && issued < nk && issued == k + 2) issue_region(issued++);
     }
+    // every MMA issued (also after a timeout) completes before TMEM is read
+    // back and freed
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(mma_fin))
+        : "memory");
+    if (!mbar_wait(mma_fin, 0u, kGWaitNs)) ok = false;
   }
-  // add in the last one or two chunks
-  if (ok && nk > 0) {
-    const long long last = (nk - 1) / kGChunk;
-    for (long long c = (last >= 1 ? last - 1 : 0); c <= last; ++c) {
-      const bool w = mbar_wait(&chunk_done[c & 1], (unsigned)((c >> 1) & 1), kGWaitNs);
-      if (__syncthreads_or(!w)) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      flush_acc(tmem, (unsigned)(c & 1) * 128, c == 0);
-    }
-  }
-  if (p.use_tma) {
-    // regions issued but not consumed (only after a timeout): let them land
-    // before the CTA exits
-    const long long n_issued = __shfl_sync(0xffffffffu, issued, 0);
-    for (long long r = k; r < n_issued && warp == 0; ++r)
-      mbar_wait(&reg_full[r % kGRegStages], (unsigned)((r / kGRegStages) & 1), kGWaitNs);
-  }
-  if (!ok && tid == 0) *p.status = kDevTimeout;
+  __syncwarp();  // each warp converged again before the CTA barriers below
+  if (!ok) *p.status = kDevTimeout;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // partial tile (row-major 128 x 128 floats) from the running sum
-  float *out = p.part + ((long long)split * p.ntiles + tile) * (kGT * kGT);
-  {
+  if (warp < kGFillWarps) {
+    float *out = p.part + ((long long)split * p.ntiles + tile) * (kGT * kGT);
     const int quad = warp & 3, half = warp >> 2;
     const int row = quad * 32 + lane;
+    const bool have = __all_sync(0xffffffffu, ok) && nk > 0;
 #pragma unroll 1
     for (int c0 = half * 64; c0 < half * 64 + 64; c0 += 32) {
       unsigned r[32];
-      if (nk > 0 && ok) {
+      if (have) {
         tmem_ld32(tmem + ((unsigned)(quad * 32) << 16) + kGRunCol + (unsigned)c0, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       } else {
@@ -486,10 +561,10 @@ cudaError_t launch_gemm_tf32x3(const void *A, long long N, long long M, long lon
   g.status = (unsigned *)workspace;
   g.R = (float2 *)R;
   g.mean = mean;
-  // the A region of a K-step (P rows, 32 + Q - 1 complex columns) by TMA when
+  // the A region of a K-step (P rows, 16 + Q - 1 complex columns) by TMA when
   // it fits the ring and A meets TMA's alignment; else operands from global
   g.RWf = ((2 * (kGKW + Q - 1)) + 3) / 4 * 4;
-  if (g.RWf % 32 == 0) g.RWf += 4;  // region rows of one warp's reads in different banks
+  if (g.RWf % 8 == 0) g.RWf += 4;  // = 4 mod 8: a warp's region reads two to a bank at most
   CUtensorMap tmap;
   memset(&tmap, 0, sizeof(tmap));
   g.use_tma = (size_t)P * g.RWf * 4 <= (size_t)kGRegMaxBytes && g.RWf <= 256 && P <= 256 &&
@@ -497,7 +572,12 @@ cudaError_t launch_gemm_tf32x3(const void *A, long long N, long long M, long lon
               encode_tiled_2d(tmap, false, A, (unsigned long long)(2 * M), (unsigned long long)N,
                               (unsigned long long)(lda * 8), (unsigned)g.RWf, (unsigned)P)
                   ? 1 : 0;
-  const size_t smem = 2 * 4 * kGTileBytes + (size_t)kGRegStages * kGRegMaxBytes + 128;
+  // ring slots: 128-byte aligned, as many as the ring holds (at most 12)
+  g.RSLOT = (int)(((size_t)P * g.RWf * 4 + 127) & ~(size_t)127);
+  g.RS = g.RSLOT > 0 ? kGRegRingBytes / g.RSLOT : 0;
+  if (g.RS > kGRegMaxStages) g.RS = kGRegMaxStages;
+  if (g.RS < 3) g.use_tma = 0;
+  const size_t smem = kGSmemBytes;
   static bool attr_done[64] = {false};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
