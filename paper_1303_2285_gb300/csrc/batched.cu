@@ -152,16 +152,39 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
         unsigned long long accd[kBG], accx[kBG];
 #pragma unroll
         for (int k = 0; k < kBG; ++k) accd[k] = accx[k] = 0ull;
+        const int ld = (int)lda;  // N * lda < 2^31 (checked when the plan is made)
         for (int n = r_beg; n < r_end; n += 8) {
           const int nv = r_end - n;  // valid a rows of this chunk (>= 8 except the last)
+          const int b0 = n + d0;     // >= 0: n >= P - 1 and d0 >= -(P - 1)
           unsigned long long a[8], as[8];
+          if (nv >= 8 && b0 + 8 + kBG - 1 <= N) {
+            // whole chunk, every partner row inside A: plain 32-bit offsets
+            const unsigned long long *pa = ua + (n * ld + ma), *pb = ua + (b0 * ld + mb);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              a[r] = __ldg(pa + r * ld) & amask;
+              as[r] = swap2(a[r]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8 + kBG - 1; ++k) {
+              const unsigned long long b = __ldg(pb + k * ld);
+#pragma unroll
+              for (int r = 0; r < 8; ++r) {
+                const int gg = k - r;
+                if (gg >= 0 && gg < kBG) {
+                  ffma2(accd[gg], a[r], b);
+                  ffma2(accx[gg], as[r], b);
+                }
+              }
+            }
+            continue;
+          }
 #pragma unroll
           for (int r = 0; r < 8; ++r) {
             const int row = n + r < r_end ? n + r : r_end - 1;
             a[r] = (r < nv ? __ldg(ua + (long long)row * lda + ma) : 0ull) & amask;
             as[r] = swap2(a[r]);
           }
-          const int b0 = n + d0;
           const bool clamp = b0 + 8 + kBG - 1 > N;
 #pragma unroll
           for (int k = 0; k < 8 + kBG - 1; ++k) {
@@ -239,36 +262,47 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
         const int dl0 = ps.first(dc) + g * kBG;
         const int fr0 = rb * 4, nrows = min(4, P - 1 - fr0);
         const int nbase = side == 0 ? fr0 : (N - P + 1) + fr0;
-        float2 acc[4][kBG];
+        // acc += a * conj(b) as packed (re, im) pairs: (ar, ai) * (br, br) then
+        // (ai, -ar) * (bi, bi), the roundings and order of cmac_conj;
+        // 32-bit row offsets (N * lda < 2^31)
+        unsigned long long acc[4][kBG];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int k = 0; k < kBG; ++k) acc[r][k] = make_float2(0.f, 0.f);
+          for (int k = 0; k < kBG; ++k) acc[r][k] = 0ull;
+        const int ld = (int)lda;
+        const int rb0 = nbase + d0;
         for (int m = Q - 1 + lane; m <= M - Q; m += 32) {
-          float2 a[4], bv[4 + kBG - 1];
+          unsigned long long a1[4], a2[4];
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
-            a[r] = r < nrows ? ld2(A + (long long)(nbase + r) * lda + m) : make_float2(0.f, 0.f);
-#pragma unroll
-          for (int k = 0; k < 4 + kBG - 1; ++k) {
-            const int row = nbase + d0 + k;
-            bv[k] = (row >= 0 && row < N) ? ld2(A + (long long)row * lda + m + dc) : make_float2(0.f, 0.f);
+          for (int r = 0; r < 4; ++r) {
+            const float2 x = r < nrows ? ld2(A + ((nbase + r) * ld + m)) : make_float2(0.f, 0.f);
+            a1[r] = pk2(x.x, x.y);
+            a2[r] = pk2(x.y, -x.x);
           }
 #pragma unroll
-          for (int k = 0; k < 4 + kBG - 1; ++k)
+          for (int k = 0; k < 4 + kBG - 1; ++k) {
+            const int row = rb0 + k;
+            const float2 b = (row >= 0 && row < N) ? ld2(A + (row * ld + m + dc)) : make_float2(0.f, 0.f);
+            const unsigned long long bx = pk2(b.x, b.x), by = pk2(b.y, b.y);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               const int gg = k - r;
-              if (gg >= 0 && gg < kBG) cmac_conj(acc[r][gg], a[r], bv[k]);
+              if (gg >= 0 && gg < kBG) {
+                ffma2(acc[r][gg], a1[r], bx);
+                ffma2(acc[r][gg], a2[r], by);
+              }
             }
+          }
         }
         float v[2 * 4 * kBG];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
           for (int k = 0; k < kBG; ++k) {
-            v[2 * (r * kBG + k)] = acc[r][k].x;
-            v[2 * (r * kBG + k) + 1] = acc[r][k].y;
+            const float2 x = upk2(acc[r][k]);
+            v[2 * (r * kBG + k)] = x.x;
+            v[2 * (r * kBG + k) + 1] = x.y;
           }
         warp_transpose_reduce<2 * 4 * kBG>(v, lane);  // lane holds complex index lane
         const int r = lane / kBG, k = lane % kBG;
@@ -333,6 +367,7 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           const int RJ = NFR * nDp;
           // own left fringe-column products, suffix sums
           float2 suf = make_float2(0.f, 0.f);
+#pragma unroll 4
           for (int k = Q - 2; k >= 0; --k) {
             if (rowok) cmac_conj(suf, ld2(An + k), ld2(Ab + k));
             if (k < J) rvd[k * RJ] = make_float2(si.x + suf.x, si.y + suf.y);
@@ -340,6 +375,7 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           if (Q - 1 < J) rvd[(Q - 1) * RJ] = si;
           // own right fringe-column products, prefix sums
           float2 pre = make_float2(0.f, 0.f);
+#pragma unroll 4
           for (int j = 1; j < J; ++j) {
             const int k = j - 1;
             if (rowok && W + k + dc < M) cmac_conj(pre, ld2(An + W + k), ld2(Ab + W + k));
@@ -417,7 +453,8 @@ namespace {
 bool batched_shape_ok(const cov_desc &d) {
   return d.A && d.R && d.N >= 1 && d.M >= 1 && d.P >= 1 && d.Q >= 1 && d.P <= cov::kBMaxPQ &&
          d.Q <= cov::kBMaxPQ && d.N >= 2 * d.P - 1 && d.M >= 2 * d.Q - 1 && d.M <= cov::kBMaxM &&
-         d.lda >= d.M && (((uintptr_t)d.A) & 7) == 0 && (((uintptr_t)d.R) & 7) == 0;
+         d.lda >= d.M && (long long)d.N * d.lda < (1LL << 31) && (((uintptr_t)d.A) & 7) == 0 &&
+         (((uintptr_t)d.R) & 7) == 0;
 }
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
