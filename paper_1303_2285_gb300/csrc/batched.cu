@@ -104,6 +104,9 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
     const int n_cb = (M + 31) / 32, NFR = 2 * (P - 1), NFC = 2 * (Q - 1), W = M - Q + 1;
     const long long K = (long long)(N - P + 1) * (M - Q + 1);
     const long long DD = (long long)P * Q;
+    // K exact in FP32 up to 2^24: the mean multiplies by its reciprocal
+    const bool smallK = K <= (1LL << 24);
+    const float rK = smallK ? 1.0f / (float)K : 1.0f;
     // row ranges of phase A: as many as keep 4 row chunks each (at most 4)
     int RS = 1;
     while (RS < kBMaxRS && n_inner >= 32 * RS * 2) RS *= 2;
@@ -386,6 +389,12 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
       }
       __syncthreads();
       // ---- D: seed, walk, write -------------------------------------------
+      // one thread per (combination, column offset j): the diagonal of block
+      // (j, j + dc). Its seed terms, the top fringe rows still in the box and
+      // the bottom ones already in, are the contiguous range rv[i0 .. i0+P-2]
+      // of the staged row sums, summed as two interleaved compensated chains.
+      // The mean's 1/K is a multiplication by the reciprocal (within 1.5 ulp
+      // of the quotient; R has (PQ)^2 elements, so this is per-element work).
       for (int t = threadIdx.x; t < nDp * Q; t += blockDim.x) {
         const int dl = t % nDp, j = t / nDp;
         int dr, dc;
@@ -394,32 +403,45 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
         const int adr = dr < 0 ? -dr : dr;
         const int i0 = dr < 0 ? -dr : 0, I = P - adr;
         const float2 *rvj = rv + j * NFR * nDp + dl;  // rv[j][n][dl] at rvj[n * nDp]
-        Neu<float> orr, oii;
+        Neu<float> orr, oii, o2r, o2i;
         orr.add(cv[j * nDp + dl].x);
         oii.add(cv[j * nDp + dl].y);
-        for (int n = i0; n <= P - 2; ++n) {
-          orr.add(rvj[n * nDp].x);
-          oii.add(rvj[n * nDp].y);
+        {
+          const int ue = i0 + P - 1;
+          int u = i0;
+          for (; u + 2 <= ue; u += 2) {
+            const float2 x = rvj[u * nDp], y = rvj[(u + 1) * nDp];
+            orr.add(x.x);
+            oii.add(x.y);
+            o2r.add(y.x);
+            o2i.add(y.y);
+          }
+          if (u < ue) {
+            orr.add(rvj[u * nDp].x);
+            oii.add(rvj[u * nDp].y);
+          }
+          orr.merge(o2r.s, o2r.c);
+          oii.merge(o2i.s, o2i.c);
         }
-        for (int k = 0; k < i0; ++k) {
-          orr.add(rvj[(P - 1 + k) * nDp].x);
-          oii.add(rvj[(P - 1 + k) * nDp].y);
-        }
+        // element (i, i + dr) of the block and its mirror; R has < 2^31 elements
+        int e1 = (i0 + P * j) * (int)DD + (i0 + dr) + P * (j + dc);
+        int e2 = ((i0 + dr) + P * (j + dc)) * (int)DD + i0 + P * j;
         for (int i = i0; i < i0 + I; ++i) {
           float re = orr.value(), im = oii.value();
           if (mean) {
-            if (K <= (1LL << 24)) {  // K exact in FP32: one IEEE division
-              re = re / (float)K;
-              im = im / (float)K;
+            if (smallK) {
+              re *= rK;
+              im *= rK;
             } else {
               re = (float)((double)re / (double)K);
               im = (float)((double)im / (double)K);
             }
           }
           if (dr == 0 && dc == 0) im = 0.f;
-          const long long a = i + (long long)P * j, b = (i + dr) + (long long)P * (j + dc);
-          d.R[a * DD + b] = make_float2(re, im);
-          if (a != b) d.R[b * DD + a] = make_float2(re, -im);
+          d.R[e1] = make_float2(re, im);
+          if (e1 != e2) d.R[e2] = make_float2(re, -im);
+          e1 += (int)DD + 1;
+          e2 += (int)DD + 1;
           if (i + 1 < i0 + I) {  // walk: row i leaves the box, row i+N-P+1 enters
             orr.add(-rvj[i * nDp].x);
             oii.add(-rvj[i * nDp].y);
