@@ -3,9 +3,10 @@
 // core busy where one matrix has too few combinations).
 //
 // Each CTA owns whole matrices, taken from a schedule the host builds once by
-// longest-processing-time-first assignment (cost = distinct products, Eq. 3.6,
-// plus a per-combination overhead). A CTA never waits on another CTA, so the
-// launch is one kernel and can be captured in a CUDA graph.
+// longest-processing-time-first assignment (cost = a model of the kernel's
+// cycles per member over its work counts: products with their padding,
+// passes, R elements; see batched_member_cost). A CTA never waits on another
+// CTA, so the launch is one kernel and can be captured in a CUDA graph.
 //
 // Per matrix, the CTA goes through the column lags dc = 0..Q-1; for one dc it
 // handles the combinations (dr, dc) of Eq. 3.3 together:
@@ -481,6 +482,52 @@ bool batched_shape_ok(const cov_desc &d) {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Cost of one member in k_batched, in SM cycles: a linear model over the
+// kernel's own work counts (padded inner-row products of phase A, its warp
+// tasks, the fringe-row tasks, passes over the column lags, R elements, ...),
+// with non-negative weights fitted to per-member cycle counts measured on
+// GB300 for the 4096-member uneven workload (median error 2 %). It replaces
+// the distinct-product count in the LPT schedule, whose error on small and
+// narrow members (padding, per-pass and per-element work) left the slowest
+// CTA 12 % above the mean.
+double batched_member_cost(long long N, long long M, int P, int Q) {
+  const long long n_inner = N - 2LL * P + 2;
+  int RS = 1;
+  while (RS < cov::kBMaxRS && n_inner >= 32LL * RS * 2) RS *= 2;
+  const long long n_cb = (M + 31) / 32;
+  const int NFR = 2 * (P - 1), NFC = 2 * (Q - 1);
+  const long long n_ic = M - 2LL * Q + 2;
+  const long long uc = (long long)P * Q + (long long)(P - 1) * (Q - 1);
+  double issuedA = 0;  // phase A: lag slots x column lanes x chunk rows
+  long long ngt = 0;   // lag groups over all column lags
+  for (int dc = 0; dc < Q; ++dc) {
+    const long long ng = ((dc ? 2 * P - 1 : P) + cov::kBG - 1) / cov::kBG;
+    ngt += ng;
+    for (int rs = 0; rs < RS; ++rs) {
+      const long long nr = n_inner * (rs + 1) / RS - n_inner * rs / RS;
+      issuedA += (double)(ng * cov::kBG) * (n_cb * 32) * (((nr + 7) / 8) * 8);
+    }
+  }
+  // passes over the column lags, as the kernel forms them
+  const long long per = n_cb * RS + (long long)NFC * RS + NFR + Q + (long long)Q * NFR;
+  const long long cap = (long long)(cov::kBSmemBytes / sizeof(float2)) / per;
+  long long passes = 0;
+  for (int dc_a = 0; dc_a < Q;) {
+    long long n = 0;
+    int dc_b = dc_a;
+    while (dc_b < Q && n + (dc_b ? 2 * P - 1 : P) <= cap) n += dc_b++ ? 2 * P - 1 : P;
+    if (dc_b == dc_a) dc_b = dc_a + 1;  // (cannot happen for accepted shapes)
+    ++passes;
+    dc_a = dc_b;
+  }
+  const double tasksA = (double)ngt * n_cb * RS;
+  const double tasksB = n_ic > 64 ? 2.0 * ((P - 1 + 3) / 4) * ngt * ((n_ic + 31) / 32) : 0.0;
+  const double narrowB = n_ic <= 64 ? (double)uc * NFR * (n_ic > 0 ? n_ic : 0) : 0.0;
+  const double DD = (double)P * Q;
+  return 0.05762 * issuedA + 2.111 * DD * DD + 11380.0 * passes + 120.1 + 136.0 * tasksA +
+         99.76 * tasksB + 0.2717 * narrowB + 9.607 * (double)uc * Q + 0.2529 * (double)N * M;
+}
+
 }  // namespace
 
 extern "C" {
@@ -551,7 +598,7 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   for (int i = 0; i < count; ++i) {
     const cov_desc &d = descs[i];
     pl->descs[i] = {(const float2 *)d.A, (float2 *)d.R, d.lda, d.N, d.M, d.P, d.Q};
-    cost[i] = cov::matrix_cost(d.N, d.M, d.P, d.Q);
+    cost[i] = (long long)batched_member_cost(d.N, d.M, d.P, d.Q);
   }
   const int grid = std::min(sms, count);
   std::vector<int> bin(count);
