@@ -457,6 +457,129 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batches whose members are all small (M <= 32, N M <= 1024): one warp per
+// member, whose A it stages in shared memory, 16 members in flight per SM,
+// no CTA barriers. Lanes own columns m. Per
+// combination (dr, dc) of Eq. 3.3, in the notation of Section 4.2:
+//  - the column sums C(i, m) of the products over the box rows n = i ..
+//    i+H-1 of the first output i (H = N-P+1) seed the walk; the products
+//    of the first I-1 box rows are kept (per lane, in shared memory);
+//  - the walk down the diagonal adds the entering row's products and
+//    subtracts the kept products of the leaving row (compensated), so each
+//    distinct product (Eq. 3.5) is formed once;
+//  - for every output i, the box sums over the columns j .. j+Wd-1
+//    (Wd = M-Q+1) of all column offsets j come from one warp scan of C:
+//    S(i, j) = pre(j+Wd-1) - pre(j-1), the column walk in closed form;
+//    lane j writes element (i + P j, i + dr + P (j + dc)) of R and its
+//    conjugate mirror.
+// ---------------------------------------------------------------------------
+constexpr int kWWarps = 8;    // members in flight per CTA (two CTAs an SM)
+constexpr int kWMaxM = 32;    // one column per lane
+constexpr int kWMaxPQ = 16;
+constexpr int kWMaxElems = 1024;  // N * M: the member's A is staged whole
+constexpr size_t kWWarpBytes = ((size_t)(kWMaxPQ - 1) * 32 + kWMaxElems) * sizeof(float2);
+
+__device__ __forceinline__ float warp_scan_incl(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+__global__ void __launch_bounds__(kWWarps * 32, 2)
+    k_batched_warp(const BDesc *descs, const int *order, const int *slot_begin, int mean) {
+  // per warp: the kept products of the leaving rows [P-1][32], then the
+  // member's A (row pitch M)
+  extern __shared__ __align__(16) unsigned char smem_w[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = blockIdx.x * kWWarps + warp;
+  float2(*keep)[32] = (float2(*)[32])(smem_w + (size_t)warp * kWWarpBytes);
+  float2 *As = (float2 *)(smem_w + (size_t)warp * kWWarpBytes) + (kWMaxPQ - 1) * 32;
+  for (int mi = slot_begin[slot]; mi < slot_begin[slot + 1]; ++mi) {
+    const BDesc d = descs[order[mi]];
+    const int N = d.N, M = d.M, P = d.P, Q = d.Q;
+    const int H = N - P + 1, Wd = M - Q + 1, DD = P * Q;
+    const long long K = (long long)H * Wd;
+    const bool smallK = K <= (1LL << 24);
+    const float rK = smallK ? 1.0f / (float)K : 1.0f;
+    // stage A (row pitch M) into the warp's buffer
+    __syncwarp();  // the previous member's reads of As are done
+#pragma unroll 4
+    for (int r = 0; r < N; ++r)
+      if (lane < M) As[r * M + lane] = __ldg(d.A + (long long)r * d.lda + lane);
+    __syncwarp();
+    const int ld = M;
+    const float2 *A = As;
+    const bool mok = lane < M;
+    for (int dc = 0; dc < Q; ++dc) {
+      const bool bok = mok && lane + dc < M;  // a product exists in this column
+      for (int dr = dc == 0 ? 0 : -(P - 1); dr < P; ++dr) {
+        const int i_lo = dr < 0 ? -dr : 0, I = P - (dr < 0 ? -dr : dr);
+        // seed: rows i_lo .. i_lo+H-1 (two plain accumulators), keeping the
+        // first I-1 rows' products
+        float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+        if (bok) {
+          const float2 *pa = A + (i_lo * ld + lane), *pb = A + ((i_lo + dr) * ld + lane + dc);
+          int r = 0;
+#pragma unroll 4
+          for (; r < I - 1; ++r) {
+            float2 v = make_float2(0.f, 0.f);
+            cmac_conj(v, pa[r * ld], pb[r * ld]);
+            keep[r][lane] = v;
+            s0.x += v.x;
+            s0.y += v.y;
+          }
+#pragma unroll 4
+          for (; r + 1 < H; r += 2) {
+            cmac_conj(s0, pa[r * ld], pb[r * ld]);
+            cmac_conj(s1, pa[(r + 1) * ld], pb[(r + 1) * ld]);
+          }
+          if (r < H) cmac_conj(s0, pa[r * ld], pb[r * ld]);
+        }
+        Neu<float> cr, ci;
+        cr.add(s0.x + s1.x);
+        ci.add(s0.y + s1.y);
+        const int J = Q - dc;
+        for (int i = i_lo; i < i_lo + I; ++i) {
+          const float pr = warp_scan_incl(cr.value(), lane), pi = warp_scan_incl(ci.value(), lane);
+          const int hi = lane + Wd - 1 < 31 ? lane + Wd - 1 : 31;
+          const float hr = __shfl_sync(0xffffffffu, pr, hi), hm = __shfl_sync(0xffffffffu, pi, hi);
+          const float lr = __shfl_sync(0xffffffffu, pr, lane > 0 ? lane - 1 : 0);
+          const float lm = __shfl_sync(0xffffffffu, pi, lane > 0 ? lane - 1 : 0);
+          if (lane < J) {
+            float re = lane > 0 ? hr - lr : hr, im = lane > 0 ? hm - lm : hm;
+            if (mean) {
+              if (smallK) {
+                re *= rK;
+                im *= rK;
+              } else {
+                re = (float)((double)re / (double)K);
+                im = (float)((double)im / (double)K);
+              }
+            }
+            if (dr == 0 && dc == 0) im = 0.f;
+            const int a = i + P * lane, b = i + dr + P * (lane + dc);
+            d.R[a * DD + b] = make_float2(re, im);
+            if (a != b) d.R[b * DD + a] = make_float2(re, -im);
+          }
+          if (i + 1 < i_lo + I && bok) {  // walk: row i leaves the box, row i+H enters
+            float2 vin = make_float2(0.f, 0.f);
+            cmac_conj(vin, A[(i + H) * ld + lane], A[(i + H + dr) * ld + lane + dc]);
+            const float2 vout = keep[i - i_lo][lane];
+            cr.add(-vout.x);
+            ci.add(-vout.y);
+            cr.add(vin.x);
+            ci.add(vin.y);
+          }
+        }
+      }
+    }
+  }
+}
+
 }  // namespace cov
 
 // ---------------------------------------------------------------------------
@@ -464,9 +587,10 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
 // ---------------------------------------------------------------------------
 struct cov_batched_plan {
   std::vector<cov::BDesc> descs;
-  std::vector<int> order;      // matrix indices, CTA by CTA
-  std::vector<int> cta_begin;  // grid + 1 offsets into order
+  std::vector<int> order;      // matrix indices, slot by slot
+  std::vector<int> cta_begin;  // slots + 1 offsets into order
   int grid;
+  int warp_kernel;             // 1: one warp per member (all members narrow)
   int mean;
   size_t off_desc, off_order, off_begin, total;
 };
@@ -600,20 +724,39 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
     pl->descs[i] = {(const float2 *)d.A, (float2 *)d.R, d.lda, d.N, d.M, d.P, d.Q};
     cost[i] = (long long)batched_member_cost(d.N, d.M, d.P, d.Q);
   }
-  const int grid = std::min(sms, count);
+  // narrow members only: one warp per member (k_batched_warp), schedule over
+  // the warps; its cost per member is the distinct products plus the
+  // per-output scan and write steps
+  bool narrow = true;
+  for (int i = 0; i < count; ++i)
+    narrow = narrow && descs[i].M <= cov::kWMaxM && descs[i].P <= cov::kWMaxPQ &&
+             descs[i].Q <= cov::kWMaxPQ && descs[i].N * descs[i].M <= cov::kWMaxElems;
+  pl->warp_kernel = narrow ? 1 : 0;
+  if (narrow)
+    for (int i = 0; i < count; ++i) {
+      const cov_desc &d = descs[i];
+      long long steps = 0;  // outputs i of every combination
+      for (int dc = 0; dc < d.Q; ++dc)
+        for (int dr = dc ? -(d.P - 1) : 0; dr < d.P; ++dr) steps += d.P - (dr < 0 ? -dr : dr);
+      cost[i] = cov::distinct_products(d.N, d.M, d.P, d.Q) / 8 + 40 * steps + 200;
+    }
+  // (the warp kernel fits two CTAs an SM: twice the warps to hide latency)
+  const int grid = narrow ? std::min(2 * sms, (count + cov::kWWarps - 1) / cov::kWWarps)
+                          : std::min(sms, count);
+  const int slots = narrow ? grid * cov::kWWarps : grid;
   std::vector<int> bin(count);
-  cov::lpt_assign(cost.data(), count, grid, bin.data(), nullptr);
+  cov::lpt_assign(cost.data(), count, slots, bin.data(), nullptr);
   // each CTA's matrices in decreasing cost order (the order LPT placed them)
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int a, int b) {
     return cost[a] > cost[b] || (cost[a] == cost[b] && a < b);
   });
-  std::vector<std::vector<int>> per(grid);
+  std::vector<std::vector<int>> per(slots);
   for (int i : order) per[bin[i]].push_back(i);
   pl->grid = grid;
-  pl->cta_begin.assign(grid + 1, 0);
-  for (int c = 0; c < grid; ++c) {
+  pl->cta_begin.assign(slots + 1, 0);
+  for (int c = 0; c < slots; ++c) {
     pl->cta_begin[c + 1] = pl->cta_begin[c] + (int)per[c].size();
     for (int i : per[c]) pl->order.push_back(i);
   }
@@ -623,7 +766,7 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   pl->off_order = off;
   off = al256(off + sizeof(int) * count);
   pl->off_begin = off;
-  off = al256(off + sizeof(int) * (grid + 1));
+  off = al256(off + sizeof(int) * (slots + 1));
   pl->total = off;
   *plan = pl;
   return COV_OK;
@@ -670,6 +813,20 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, s
     if (dev >= 0 && dev < 64) attr_done[dev] = true;
   }
   if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  if (plan->warp_kernel) {
+    const size_t wsmem = cov::kWWarps * cov::kWWarpBytes;
+    static bool wattr_done[64] = {false};
+    if (dev < 0 || dev >= 64 || !wattr_done[dev]) {
+      if (cudaFuncSetAttribute(cov::k_batched_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)wsmem) != cudaSuccess)
+        return COV_ECUDA;
+      if (dev >= 0 && dev < 64) wattr_done[dev] = true;
+    }
+    cov::k_batched_warp<<<plan->grid, cov::kWWarps * 32, wsmem, s>>>(
+        (const cov::BDesc *)(w + plan->off_desc), (const int *)(w + plan->off_order),
+        (const int *)(w + plan->off_begin), plan->mean);
+    return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
+  }
   cov::k_batched<<<plan->grid, cov::kBWarps * 32, smem, s>>>(
       (const cov::BDesc *)(w + plan->off_desc), (const int *)(w + plan->off_order),
       (const int *)(w + plan->off_begin), plan->mean);

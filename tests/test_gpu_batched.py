@@ -89,3 +89,42 @@ def test_batched_graph_capture(oracle_mod):
         torch.cuda.synchronize()
         for (At, Rt, P, Q), A in zip(items, host):
             assert rel_fro(Rt.cpu().numpy(), oracle_R(oracle_mod, A, P, Q)) < F32_TOL
+
+
+def narrow_shapes(count, seed):
+    """Members with M <= 32, N M <= 1024 and P, Q <= 16: the batch then runs
+    one warp per member."""
+    rng = np.random.default_rng(seed)
+    out = [(31, 32, 16, 16), (33, 31, 3, 16), (9, 1, 5, 1), (1, 1, 1, 1), (25, 25, 10, 10),
+           (64, 2, 7, 1), (17, 32, 9, 2)]
+    while len(out) < count:
+        N, M = int(rng.integers(1, 81)), int(rng.integers(1, 33))
+        if N * M > 1024:
+            continue
+        P = int(rng.integers(1, min(16, (N + 1) // 2) + 1))
+        Q = int(rng.integers(1, min(16, (M + 1) // 2) + 1))
+        out.append((N, M, P, Q))
+    return out
+
+
+def test_batched_narrow_members_gaussian(oracle_mod):
+    shapes = narrow_shapes(60, 21)
+    assert all(M <= 32 and N * M <= 1024 and P <= 16 and Q <= 16 for N, M, P, Q in shapes)
+    items, host = make_batch(shapes, "cn", 700)
+    run_plan(items)
+    for (At, Rt, P, Q), A in zip(items, host):
+        got = Rt.cpu().numpy()
+        assert rel_fro(got, oracle_R(oracle_mod, A, P, Q)) < F32_TOL, (A.shape, P, Q)
+        assert np.array_equal(got, got.conj().T)
+        assert np.all(got.diagonal().imag == 0)
+
+
+def test_batched_narrow_members_integer_exact(oracle_mod):
+    # small integers: every product, column sum, scan prefix and difference is
+    # an exact integer in FP32, so the SUM result is exact
+    shapes = narrow_shapes(30, 22)
+    items, host = make_batch(shapes, "int", 900)
+    run_plan(items, norm="sum")
+    for (At, Rt, P, Q), A in zip(items, host):
+        S = oracle_R(oracle_mod, A, P, Q, mean=False)
+        assert np.array_equal(Rt.cpu().numpy(), S.astype(np.complex64)), (A.shape, P, Q)
