@@ -527,6 +527,7 @@ def bench_batched(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
     plan = cov.BatchedPlan(items)
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
     plan.upload(ws)
+    tuning = plan.autotune(ws, reps=2)  # untimed: picks form, segment length, task shape
     s = torch.cuda.Stream()
     for _ in range(3):
         plan.run(ws, stream=s)
@@ -555,7 +556,8 @@ def bench_batched(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
             "distinct_products_per_s": um / (ms * 1e-3), "matrices_per_s": len(shapes) / (ms * 1e-3),
             "fp32_fma_frac": 8.0 * um / (ms * 1e-3) / fp32_peak,
             "input_bytes": sum(N * M * 8 for N, M, _, _ in shapes),
-            "err_vs_fp64_direct_rel_fro_max_of_8": max(errs), "graph_captured": True}
+            "err_vs_fp64_direct_rel_fro_max_of_8": max(errs), "graph_captured": True,
+            "tuning": tuning}
 
 
 def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
@@ -566,6 +568,7 @@ def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
     plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
     plan.upload(ws)
+    tuning = plan.autotune(ws, reps=2)  # untimed
     s = torch.cuda.Stream()
     for _ in range(3):
         plan.run(ws, stream=s)
@@ -586,7 +589,7 @@ def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
     um = R.shape[0] * cov.plan_info(25, 25, 10, 10)["distinct_products"]
     return {"apertures": R.shape[0], "ms_per_launch": ms, "apertures_per_s": R.shape[0] / (ms * 1e-3),
             "distinct_products_per_s": um / (ms * 1e-3), "fp32_fma_frac": 8.0 * um / (ms * 1e-3) / fp32_peak,
-            "r_bytes": R.numel() * 8, "graph_captured": True}
+            "r_bytes": R.numel() * 8, "graph_captured": True, "tuning": tuning}
 
 
 def bench_adjoint(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:

@@ -298,6 +298,42 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace,
                                 size_t ws_bytes, cov_stream_t stream);
 void cov_batched_plan_destroy(cov_batched_plan *plan);
 
+/* Tuned knobs of a batched plan (the segment length and task shape the
+ * autotuner picks):
+ *   form            0: one CTA per member in flight (any members);
+ *                   1: one warp per member (only when every member has
+ *                      M <= 32, N*M <= 1024 and P, Q <= 16);
+ *   reseed_interval form 0: the walk down each diagonal segment starts from
+ *                   a direct-sum seed every this many outputs (Section 4.3's
+ *                   segments cut shorter: more parallel seeds, fewer
+ *                   additions in a chain); 0 = one seed per segment; <= 16;
+ *   row_ranges      form 0: at most this many row ranges (1, 2 or 4) per
+ *                   column block of the inner-row product tasks.
+ * A new plan starts at form = 1 where allowed, else 0, reseed_interval 0,
+ * row_ranges 4. */
+typedef struct {
+  int32_t form;
+  int32_t reseed_interval;
+  int32_t row_ranges;
+} cov_batched_tuning_t;
+
+/* Host only. COV_EINVAL on null arguments. */
+cov_status cov_batched_get_tuning(const cov_batched_plan *plan, cov_batched_tuning_t *t);
+/* Host only: sets the knobs and rebuilds the schedule when the form changes
+ * (upload again before the next cov_estimate_batched). COV_EINVAL on a value
+ * outside the ranges above, or form 1 for a plan whose members do not all
+ * fit it. */
+cov_status cov_batched_set_tuning(cov_batched_plan *plan, const cov_batched_tuning_t *t);
+/* Times the candidate knob settings (form 1 where allowed; form 0 with
+ * reseed_interval 0, 2, 4 and row_ranges 2, 4) on the plan's own members,
+ * `reps` launches each after one warm-up on `stream`, keeps the fastest and
+ * uploads its tables into `workspace`. Writes every member's R (the last
+ * setting's result, all settings compute the same R up to rounding);
+ * synchronises the stream. COV_EWORKSPACE / COV_EINVAL as
+ * cov_estimate_batched; COV_ECUDA on a failed launch or event. */
+cov_status cov_batched_autotune(cov_batched_plan *plan, void *workspace, size_t ws_bytes, int reps,
+                                cov_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * Adjoint (not in the paper; the derivative of Eq. 2.2).
  * Given G = dL/dR (PQ x PQ, device, convention dL/dRe + i dL/dIm), writes

@@ -54,6 +54,14 @@ class Tuning(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class BatchedTuning(ctypes.Structure):
+    """Knobs of a batched plan: kernel form (0 CTA per member, 1 warp per
+    member), walk re-seed interval of form 0 (0: one seed per segment),
+    row ranges per column block of form 0 (cov_batched_tuning_t)."""
+    _fields_ = [("form", ctypes.c_int32), ("reseed_interval", ctypes.c_int32),
+                ("row_ranges", ctypes.c_int32)]
+
+
 class CovDesc(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("R", ctypes.c_void_p), ("lda", ctypes.c_int64),
                 ("N", ctypes.c_int32), ("M", ctypes.c_int32), ("P", ctypes.c_int32),
@@ -83,6 +91,9 @@ SIGNATURES = [
     ("cov_batched_upload", _I, [_VP, _VP, _SZ, _VP]),
     ("cov_estimate_batched", _I, [_VP, _VP, _SZ, _VP]),
     ("cov_batched_plan_destroy", None, [_VP]),
+    ("cov_batched_get_tuning", _I, [_VP, ctypes.POINTER(BatchedTuning)]),
+    ("cov_batched_set_tuning", _I, [_VP, ctypes.POINTER(BatchedTuning)]),
+    ("cov_batched_autotune", _I, [_VP, _VP, _SZ, _I, _VP]),
     ("cov_backward_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
     ("cov_estimate_backward", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _VP, _VP, _SZ, _VP]),
     ("cov_backward_strided_workspace_size", _I, [_I, _I64, _I64, _I, _I, ctypes.POINTER(_SZ)]),
@@ -339,6 +350,24 @@ class BatchedPlan:
     def run(self, workspace, stream=None) -> None:
         _check(self._lib.cov_estimate_batched(self.ptr, workspace.data_ptr(), workspace.numel(),
                                               _stream_ptr(stream)), "cov_estimate_batched")
+
+    @property
+    def tuning(self) -> dict:
+        t = BatchedTuning()
+        _check(self._lib.cov_batched_get_tuning(self.ptr, ctypes.byref(t)), "cov_batched_get_tuning")
+        return {"form": t.form, "reseed_interval": t.reseed_interval, "row_ranges": t.row_ranges}
+
+    def set_tuning(self, form: int, reseed_interval: int = 0, row_ranges: int = 4) -> None:
+        """Sets the knobs (rebuilding the schedule): upload() again before run()."""
+        t = BatchedTuning(form, reseed_interval, row_ranges)
+        _check(self._lib.cov_batched_set_tuning(self.ptr, ctypes.byref(t)), "cov_batched_set_tuning")
+
+    def autotune(self, workspace, reps: int = 3, stream=None) -> dict:
+        """Times the candidate knob settings on this plan's members (writing
+        their R), keeps the fastest and uploads it; returns it."""
+        _check(self._lib.cov_batched_autotune(self.ptr, workspace.data_ptr(), workspace.numel(), reps,
+                                              _stream_ptr(stream)), "cov_batched_autotune")
+        return self.tuning
 
     def __del__(self):
         if getattr(self, "ptr", None) is not None and self.ptr.value:

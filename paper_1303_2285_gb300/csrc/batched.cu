@@ -91,8 +91,12 @@ struct BPass {
   }
 };
 
+// L: re-seed interval of the walk (0: one seed per diagonal segment);
+// rs_max: at most this many row ranges per column block in the products
+// (1, 2 or 4) -- the tuned segment length and task shape.
 __global__ void __launch_bounds__(kBWarps * 32, 1)
-    k_batched(const BDesc *descs, const int *order, const int *cta_begin, int mean) {
+    k_batched(const BDesc *descs, const int *order, const int *cta_begin, int mean, int L,
+              int rs_max) {
   extern __shared__ __align__(16) unsigned char smem_b[];
   float2 *pool = (float2 *)smem_b;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
     const float rK = smallK ? 1.0f / (float)K : 1.0f;
     // row ranges of phase A: as many as keep 4 row chunks each (at most 4)
     int RS = 1;
-    while (RS < kBMaxRS && n_inner >= 32 * RS * 2) RS *= 2;
+    while (RS < rs_max && n_inner >= 32 * RS * 2) RS *= 2;
     // per-pass shared arrays (float2), the pass's combination index dl
     // fastest (threads of phases C and D take consecutive dl): core
     // [n_cb*RS][dl], cs [NFC*RS][dl], sin [NFR][dl], cv [Q][dl], rv [Q][NFR][dl]
@@ -390,26 +394,32 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
       }
       __syncthreads();
       // ---- D: seed, walk, write -------------------------------------------
-      // one thread per (combination, column offset j): the diagonal of block
-      // (j, j + dc). Its seed terms, the top fringe rows still in the box and
-      // the bottom ones already in, are the contiguous range rv[i0 .. i0+P-2]
-      // of the staged row sums, summed as two interleaved compensated chains.
-      // The mean's 1/K is a multiplication by the reciprocal (within 1.5 ulp
-      // of the quotient; R has (PQ)^2 elements, so this is per-element work).
-      for (int t = threadIdx.x; t < nDp * Q; t += blockDim.x) {
-        const int dl = t % nDp, j = t / nDp;
+      // one thread per (combination, column offset j, segment of L outputs;
+      // one segment when L = 0): the diagonal of block (j, j + dc) from
+      // output is on. The seed's terms, the top fringe rows still in the
+      // box and the bottom ones already in, are the contiguous range
+      // rv[is .. is+P-2] of the staged row sums, summed as two interleaved
+      // compensated chains. The mean's 1/K is a multiplication by the
+      // reciprocal (within 1.5 ulp of the quotient; R has (PQ)^2 elements,
+      // so this is per-element work).
+      const int nseg = L > 0 ? (P + L - 1) / L : 1;
+      for (int t = threadIdx.x; t < nDp * Q * nseg; t += blockDim.x) {
+        const int dl = t % nDp, rest = t / nDp, j = rest % Q, c = rest / Q;
         int dr, dc;
         ps.of(dl, dr, dc);
         if (j >= Q - dc) continue;
         const int adr = dr < 0 ? -dr : dr;
         const int i0 = dr < 0 ? -dr : 0, I = P - adr;
+        const int is = i0 + (L > 0 ? c * L : 0);
+        if (is >= i0 + I) continue;
+        const int ie = L > 0 && is + L < i0 + I ? is + L : i0 + I;
         const float2 *rvj = rv + j * NFR * nDp + dl;  // rv[j][n][dl] at rvj[n * nDp]
         Neu<float> orr, oii, o2r, o2i;
         orr.add(cv[j * nDp + dl].x);
         oii.add(cv[j * nDp + dl].y);
         {
-          const int ue = i0 + P - 1;
-          int u = i0;
+          const int ue = is + P - 1;
+          int u = is;
           for (; u + 2 <= ue; u += 2) {
             const float2 x = rvj[u * nDp], y = rvj[(u + 1) * nDp];
             orr.add(x.x);
@@ -425,9 +435,9 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           oii.merge(o2i.s, o2i.c);
         }
         // element (i, i + dr) of the block and its mirror; R has < 2^31 elements
-        int e1 = (i0 + P * j) * (int)DD + (i0 + dr) + P * (j + dc);
-        int e2 = ((i0 + dr) + P * (j + dc)) * (int)DD + i0 + P * j;
-        for (int i = i0; i < i0 + I; ++i) {
+        int e1 = (is + P * j) * (int)DD + (is + dr) + P * (j + dc);
+        int e2 = ((is + dr) + P * (j + dc)) * (int)DD + is + P * j;
+        for (int i = is; i < ie; ++i) {
           float re = orr.value(), im = oii.value();
           if (mean) {
             if (smallK) {
@@ -443,7 +453,7 @@ __global__ void __launch_bounds__(kBWarps * 32, 1)
           if (e1 != e2) d.R[e2] = make_float2(re, -im);
           e1 += (int)DD + 1;
           e2 += (int)DD + 1;
-          if (i + 1 < i0 + I) {  // walk: row i leaves the box, row i+N-P+1 enters
+          if (i + 1 < ie) {  // walk: row i leaves the box, row i+N-P+1 enters
             orr.add(-rvj[i * nDp].x);
             oii.add(-rvj[i * nDp].y);
             orr.add(rvj[(P - 1 + i) * nDp].x);
@@ -590,7 +600,11 @@ struct cov_batched_plan {
   std::vector<int> order;      // matrix indices, slot by slot
   std::vector<int> cta_begin;  // slots + 1 offsets into order
   int grid;
-  int warp_kernel;             // 1: one warp per member (all members narrow)
+  int sms;
+  int narrow_ok;               // every member fits k_batched_warp
+  int warp_kernel;             // tuned: 1 = one warp per member
+  int L;                       // tuned: re-seed interval of the CTA form's walk (0: none)
+  int rs_max;                  // tuned: row ranges per column block (1, 2, 4)
   int mean;
   size_t off_desc, off_order, off_begin, total;
 };
@@ -703,6 +717,51 @@ cov_status cov_aperture_descs(const void *image, cov_dtype dtype, int64_t H, int
   return COV_OK;
 }
 
+namespace {
+
+// The schedule of the plan's current form: member costs, grid, slots (CTAs,
+// or warps of the warp form), LPT assignment, each slot's members in
+// decreasing cost order.
+void build_schedule(cov_batched_plan *pl) {
+  const int count = (int)pl->descs.size();
+  std::vector<long long> cost(count);
+  for (int i = 0; i < count; ++i) {
+    const cov::BDesc &d = pl->descs[i];
+    if (pl->warp_kernel) {
+      // the warp form: distinct products plus the per-output scan and write
+      // steps
+      long long steps = 0;  // outputs i of every combination
+      for (int dc = 0; dc < d.Q; ++dc)
+        for (int dr = dc ? -(d.P - 1) : 0; dr < d.P; ++dr) steps += d.P - (dr < 0 ? -dr : dr);
+      cost[i] = cov::distinct_products(d.N, d.M, d.P, d.Q) / 8 + 40 * steps + 200;
+    } else {
+      cost[i] = (long long)batched_member_cost(d.N, d.M, d.P, d.Q);
+    }
+  }
+  // (the warp kernel fits two CTAs an SM: twice the warps to hide latency)
+  const int grid = pl->warp_kernel ? std::min(2 * pl->sms, (count + cov::kWWarps - 1) / cov::kWWarps)
+                                   : std::min(pl->sms, count);
+  const int slots = pl->warp_kernel ? grid * cov::kWWarps : grid;
+  std::vector<int> bin(count);
+  cov::lpt_assign(cost.data(), count, slots, bin.data(), nullptr);
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return cost[a] > cost[b] || (cost[a] == cost[b] && a < b);
+  });
+  std::vector<std::vector<int>> per(slots);
+  for (int i : order) per[bin[i]].push_back(i);
+  pl->grid = grid;
+  pl->order.clear();
+  pl->cta_begin.assign(slots + 1, 0);
+  for (int c = 0; c < slots; ++c) {
+    pl->cta_begin[c + 1] = pl->cta_begin[c] + (int)per[c].size();
+    for (int i : per[c]) pl->order.push_back(i);
+  }
+}
+
+}  // namespace
+
 cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype, cov_algo algo,
                                    cov_norm norm, cov_batched_plan **plan) {
   if (!descs || count < 1 || !plan || (norm != COV_MEAN && norm != COV_SUM)) return COV_EINVAL;
@@ -717,56 +776,33 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   }
   cov_batched_plan *pl = new cov_batched_plan();
   pl->mean = norm == COV_MEAN ? 1 : 0;
+  pl->sms = sms;
   pl->descs.resize(count);
-  std::vector<long long> cost(count);
+  bool narrow = true;  // every member small enough for one warp
   for (int i = 0; i < count; ++i) {
     const cov_desc &d = descs[i];
     pl->descs[i] = {(const float2 *)d.A, (float2 *)d.R, d.lda, d.N, d.M, d.P, d.Q};
-    cost[i] = (long long)batched_member_cost(d.N, d.M, d.P, d.Q);
+    narrow = narrow && d.M <= cov::kWMaxM && d.P <= cov::kWMaxPQ && d.Q <= cov::kWMaxPQ &&
+             d.N * d.M <= cov::kWMaxElems;
   }
-  // narrow members only: one warp per member (k_batched_warp), schedule over
-  // the warps; its cost per member is the distinct products plus the
-  // per-output scan and write steps
-  bool narrow = true;
-  for (int i = 0; i < count; ++i)
-    narrow = narrow && descs[i].M <= cov::kWMaxM && descs[i].P <= cov::kWMaxPQ &&
-             descs[i].Q <= cov::kWMaxPQ && descs[i].N * descs[i].M <= cov::kWMaxElems;
-  pl->warp_kernel = narrow ? 1 : 0;
-  if (narrow)
-    for (int i = 0; i < count; ++i) {
-      const cov_desc &d = descs[i];
-      long long steps = 0;  // outputs i of every combination
-      for (int dc = 0; dc < d.Q; ++dc)
-        for (int dr = dc ? -(d.P - 1) : 0; dr < d.P; ++dr) steps += d.P - (dr < 0 ? -dr : dr);
-      cost[i] = cov::distinct_products(d.N, d.M, d.P, d.Q) / 8 + 40 * steps + 200;
-    }
-  // (the warp kernel fits two CTAs an SM: twice the warps to hide latency)
-  const int grid = narrow ? std::min(2 * sms, (count + cov::kWWarps - 1) / cov::kWWarps)
-                          : std::min(sms, count);
-  const int slots = narrow ? grid * cov::kWWarps : grid;
-  std::vector<int> bin(count);
-  cov::lpt_assign(cost.data(), count, slots, bin.data(), nullptr);
-  // each CTA's matrices in decreasing cost order (the order LPT placed them)
-  std::vector<int> order(count);
-  for (int i = 0; i < count; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int a, int b) {
-    return cost[a] > cost[b] || (cost[a] == cost[b] && a < b);
-  });
-  std::vector<std::vector<int>> per(slots);
-  for (int i : order) per[bin[i]].push_back(i);
-  pl->grid = grid;
-  pl->cta_begin.assign(slots + 1, 0);
-  for (int c = 0; c < slots; ++c) {
-    pl->cta_begin[c + 1] = pl->cta_begin[c] + (int)per[c].size();
-    for (int i : per[c]) pl->order.push_back(i);
-  }
+  pl->narrow_ok = narrow ? 1 : 0;
+  // defaults (cov_batched_autotune times the alternatives)
+  pl->warp_kernel = pl->narrow_ok;
+  pl->L = 0;
+  pl->rs_max = cov::kBMaxRS;
+  build_schedule(pl);
+  // the tables are laid out for the larger of the two forms' slot counts
+  const int max_slots = std::max(std::min(sms, count),
+                                 narrow ? std::min(2 * sms, (count + cov::kWWarps - 1) / cov::kWWarps) *
+                                              cov::kWWarps
+                                        : 0);
   size_t off = cov::kWsHeader;
   pl->off_desc = off;
   off = al256(off + sizeof(cov::BDesc) * count);
   pl->off_order = off;
   off = al256(off + sizeof(int) * count);
   pl->off_begin = off;
-  off = al256(off + sizeof(int) * (slots + 1));
+  off = al256(off + sizeof(int) * (max_slots + 1));
   pl->total = off;
   *plan = pl;
   return COV_OK;
@@ -829,10 +865,76 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, s
   }
   cov::k_batched<<<plan->grid, cov::kBWarps * 32, smem, s>>>(
       (const cov::BDesc *)(w + plan->off_desc), (const int *)(w + plan->off_order),
-      (const int *)(w + plan->off_begin), plan->mean);
+      (const int *)(w + plan->off_begin), plan->mean, plan->L, plan->rs_max);
   return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
 }
 
 void cov_batched_plan_destroy(cov_batched_plan *plan) { delete plan; }
+
+cov_status cov_batched_get_tuning(const cov_batched_plan *plan, cov_batched_tuning_t *t) {
+  if (!plan || !t) return COV_EINVAL;
+  t->form = plan->warp_kernel;
+  t->reseed_interval = plan->L;
+  t->row_ranges = plan->rs_max;
+  return COV_OK;
+}
+
+cov_status cov_batched_set_tuning(cov_batched_plan *plan, const cov_batched_tuning_t *t) {
+  if (!plan || !t) return COV_EINVAL;
+  if (t->form < 0 || t->form > 1 || (t->form == 1 && !plan->narrow_ok)) return COV_EINVAL;
+  if (t->reseed_interval < 0 || t->reseed_interval > cov::kBMaxPQ) return COV_EINVAL;
+  if (t->row_ranges != 1 && t->row_ranges != 2 && t->row_ranges != 4) return COV_EINVAL;
+  const bool rebuild = t->form != plan->warp_kernel;
+  plan->warp_kernel = t->form;
+  plan->L = t->reseed_interval;
+  plan->rs_max = t->row_ranges;
+  if (rebuild) build_schedule(plan);
+  return COV_OK;
+}
+
+cov_status cov_batched_autotune(cov_batched_plan *plan, void *workspace, size_t ws_bytes, int reps,
+                                cov_stream_t stream) {
+  if (!plan || !workspace || reps < 1) return COV_EINVAL;
+  if (ws_bytes < plan->total || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  // candidates: the warp form where every member fits it; the CTA form with
+  // segments of the whole diagonal or of 2 or 4 outputs, and 2 or 4 row
+  // ranges
+  std::vector<cov_batched_tuning_t> cand;
+  if (plan->narrow_ok) cand.push_back({1, 0, cov::kBMaxRS});
+  for (int L : {0, 2, 4})
+    for (int rs : {2, 4}) cand.push_back({0, L, rs});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return COV_ECUDA;
+  }
+  cov_status st = COV_OK;
+  float best_ms = 0.f;
+  cov_batched_tuning_t best = cand[0];
+  for (size_t k = 0; k < cand.size() && st == COV_OK; ++k) {
+    if ((st = cov_batched_set_tuning(plan, &cand[k])) != COV_OK) break;
+    if ((st = cov_batched_upload(plan, workspace, ws_bytes, stream)) != COV_OK) break;
+    if ((st = cov_estimate_batched(plan, workspace, ws_bytes, stream)) != COV_OK) break;  // warm-up
+    if (cudaEventRecord(e0, s) != cudaSuccess) { st = COV_ECUDA; break; }
+    for (int r = 0; r < reps && st == COV_OK; ++r) st = cov_estimate_batched(plan, workspace, ws_bytes, stream);
+    if (st != COV_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = COV_ECUDA;
+      break;
+    }
+    if (k == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = cand[k];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != COV_OK) return st;
+  if ((st = cov_batched_set_tuning(plan, &best)) != COV_OK) return st;
+  return cov_batched_upload(plan, workspace, ws_bytes, stream);
+}
 
 }  // extern "C"

@@ -128,3 +128,47 @@ def test_batched_narrow_members_integer_exact(oracle_mod):
     for (At, Rt, P, Q), A in zip(items, host):
         S = oracle_R(oracle_mod, A, P, Q, mean=False)
         assert np.array_equal(Rt.cpu().numpy(), S.astype(np.complex64)), (A.shape, P, Q)
+
+
+@pytest.mark.parametrize("L,rs", [(0, 1), (1, 4), (3, 2), (16, 4), (2, 1)])
+def test_batched_cta_form_knobs(oracle_mod, L, rs):
+    shapes = random_shapes(24, 31) + [(256, 200, 16, 16), (40, 33, 16, 3)]
+    items, host = make_batch(shapes, "cn", 1100)
+    plan = cov.BatchedPlan(items)
+    plan.set_tuning(0, L, rs)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    plan.run(ws)
+    torch.cuda.synchronize()
+    cov.check_device_status(ws)
+    for (At, Rt, P, Q), A in zip(items, host):
+        got = Rt.cpu().numpy()
+        assert rel_fro(got, oracle_R(oracle_mod, A, P, Q)) < F32_TOL, (A.shape, P, Q, L, rs)
+        assert np.array_equal(got, got.conj().T)
+
+
+def test_batched_narrow_both_forms_and_autotune(oracle_mod):
+    shapes = narrow_shapes(40, 41)
+    items, host = make_batch(shapes, "cn", 1300)
+    plan = cov.BatchedPlan(items)
+    assert plan.tuning["form"] == 1
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    for form, L in [(1, 0), (0, 0), (0, 4)]:
+        plan.set_tuning(form, L, 4)
+        plan.upload(ws)
+        for _, Rt, _, _ in items:
+            Rt.fill_(complex(np.nan, np.nan))
+        plan.run(ws)
+        torch.cuda.synchronize()
+        cov.check_device_status(ws)
+        for (At, Rt, P, Q), A in zip(items, host):
+            assert rel_fro(Rt.cpu().numpy(), oracle_R(oracle_mod, A, P, Q)) < F32_TOL, (form, L)
+    best = plan.autotune(ws, reps=2)
+    assert best["form"] in (0, 1) and best["row_ranges"] in (2, 4)
+    for _, Rt, _, _ in items:
+        Rt.fill_(complex(np.nan, np.nan))
+    plan.run(ws)
+    torch.cuda.synchronize()
+    cov.check_device_status(ws)
+    for (At, Rt, P, Q), A in zip(items, host):
+        assert rel_fro(Rt.cpu().numpy(), oracle_R(oracle_mod, A, P, Q)) < F32_TOL
