@@ -73,8 +73,10 @@ typedef enum {
    * M >= 2Q-1 and P, Q <= 32 (COV_EUNSUPPORTED otherwise). */
   COV_RECURRENCE = 1,
   /* Dense form R = X X^H on the block-Hankel data matrix X (PQ x K, Eq. 2.2)
-   * on tcgen05 tensor cores, with split (hi + lo) operands and FP32
-   * accumulation. COV_C64 only. */
+   * on tcgen05 tensor cores, with split operands and FP32 accumulation.
+   * COV_C64 only. TF32X3: x = hi + lo in TF32, products hh + hl + lh.
+   * BF16X3: x = hi + mid + lo in BF16, products hh + hm + mh + mm + hl + lh
+   * (the terms down to 2^-16 of |x y|). */
   COV_GEMM_TF32X3 = 2,
   COV_GEMM_BF16X3 = 3,
   /* Plain per-element sums of Eq. 2.2 in FP64 (the straightforward serial

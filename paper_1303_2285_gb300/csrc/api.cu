@@ -145,6 +145,7 @@ cov_status cov_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int 
       *bytes = kWsHeader;
       return COV_OK;
     case COV_GEMM_TF32X3:
+    case COV_GEMM_BF16X3:
       if (dtype != COV_C64 || !gemm_shape_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
       *bytes = gemm_workspace_size(N, M, P, Q);
       return COV_OK;
@@ -189,14 +190,19 @@ cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M,
       if (launch_direct(d, dtype == COV_C128, s) != cudaSuccess) return COV_ECUDA;
       return COV_OK;
     }
-    case COV_GEMM_TF32X3: {
+    case COV_GEMM_TF32X3:
+    case COV_GEMM_BF16X3: {
       if (dtype != COV_C64 || !gemm_shape_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
       const int sms = device_sms();
       if (sms <= 0) return COV_ECUDA;
       bool ws_ok = false;
-      if (launch_gemm_tf32x3(A, N, M, lda, P, Q, R, norm == COV_MEAN ? 1 : 0, workspace, ws_bytes,
-                             sms, s, &ws_ok) != cudaSuccess)
-        return COV_ECUDA;
+      const cudaError_t e =
+          algo == COV_GEMM_BF16X3
+              ? launch_gemm_bf16x3(A, N, M, lda, P, Q, R, norm == COV_MEAN ? 1 : 0, workspace,
+                                   ws_bytes, sms, s, &ws_ok)
+              : launch_gemm_tf32x3(A, N, M, lda, P, Q, R, norm == COV_MEAN ? 1 : 0, workspace,
+                                   ws_bytes, sms, s, &ws_ok);
+      if (e != cudaSuccess) return COV_ECUDA;
       return ws_ok ? COV_OK : COV_EWORKSPACE;
     }
     default:

@@ -57,5 +57,8 @@ size_t gemm_workspace_size(long long N, long long M, int P, int Q);
 cudaError_t launch_gemm_tf32x3(const void *A, long long N, long long M, long long lda, int P, int Q,
                                void *R, int mean, void *workspace, size_t ws_bytes, int sms,
                                cudaStream_t s, bool *ws_ok);
+cudaError_t launch_gemm_bf16x3(const void *A, long long N, long long M, long long lda, int P, int Q,
+                               void *R, int mean, void *workspace, size_t ws_bytes, int sms,
+                               cudaStream_t s, bool *ws_ok);
 
 }  // namespace cov

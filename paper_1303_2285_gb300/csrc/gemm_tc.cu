@@ -22,6 +22,7 @@
 // whose region does not fit the ring build the operands from A in global
 // memory instead.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -40,15 +41,25 @@ constexpr int kGStages = 4;      // operand stages in flight
 constexpr int kGFillWarps = 8;   // operand builders; one more warp issues the MMAs
 constexpr int kGFillThreads = kGFillWarps * 32;
 constexpr int kGThreads = kGFillThreads + 32;
-constexpr int kGTileBytes = kGT * kGKW * 4;  // 8 KB per operand tile
-constexpr int kGStageBytes = 4 * kGTileBytes;  // A_hi, A_lo, B_hi, B_lo
+// Operand formats: TF32x3 (two TF32 parts per value, products hh + hl + lh,
+// K = 8 per MMA) and BF16x3 (three BF16 parts hi, mid, lo; products hh +
+// hm + mh + mm + hl + lh, K = 16 per MMA). A stage holds the parts of A and
+// of B, each a 128 x 16 tile.
+template <bool BF> struct GFmt {
+  static constexpr int kElem = BF ? 2 : 4;
+  static constexpr int kParts = BF ? 3 : 2;
+  static constexpr int kTileBytes = kGT * kGKW * kElem;  // 4 KB (BF16), 8 KB (TF32)
+  static constexpr int kStageBytes = 2 * kParts * kTileBytes;
+  static constexpr unsigned kSBO = 8 * kGKW * kElem;      // bytes between 8-row groups
+};
+constexpr int kGStageBytesMax = GFmt<false>::kStageBytes;  // 32 KB
 constexpr unsigned long long kGWaitNs = 2000000000ull;
 constexpr int kGRegMaxStages = 12;         // A regions in flight (at most)
 constexpr int kGRegRingBytes = 49152;      // the region ring
 constexpr int kGRegMaxBytes = 16384;       // one region: P rows x RWf floats
 constexpr unsigned kGRunCol = 256;         // TMEM columns of the running sum
 constexpr int kGBars = 2 * kGStages + 2 + 2 * kGRegMaxStages + 1;
-constexpr size_t kGSmemBytes = (size_t)kGStages * kGStageBytes + (size_t)kGRegRingBytes + 512;
+constexpr size_t kGSmemBytes = (size_t)kGStages * kGStageBytesMax + (size_t)kGRegRingBytes + 512;
 
 struct GemmParams {
   const float2 *A;
@@ -65,13 +76,13 @@ struct GemmParams {
   int RS, RSLOT;     // region slots in the ring (RS steps of prefetch) and slot bytes
 };
 
-__device__ __forceinline__ uint64_t smem_desc(unsigned addr) {
+__device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned sbo) {
   // K-major, no swizzle: core matrices of 8 rows x 16 bytes; 128 B between
-  // core matrices along K (leading), 512 B along M/N (stride: the 4 core
-  // matrices of a 16-window row group); version 1.
+  // core matrices along K (leading), `sbo` bytes along M/N (stride: the core
+  // matrices of a 16-window row group: 4 for TF32, 2 for BF16); version 1.
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
   d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((512u >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
@@ -97,9 +108,10 @@ __device__ __forceinline__ void tile_of(int t, int nt, int &ti, int &tj) {
 // rows are fixed for the whole kernel, so their (component, i, j) are decoded
 // once.
 struct GItem {
-  int ok, comp, i, col, qoff, soff;  // col: A column of the chunk's first window; soff: tile offset
+  int ok, comp, i, col, qoff, soff;  // col: A column of the chunk's first window; soff: tile byte offset
 };
 
+template <bool BF>
 __device__ __forceinline__ void build_items(const GemmParams &p, int tile_row0, GItem (&it)[2]) {
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
@@ -109,7 +121,10 @@ __device__ __forceinline__ void build_items(const GemmParams &p, int tile_row0, 
     const int r8 = item & 7, chunk = (item >> 5) & 3, rg = ((item >> 7) << 2) | ((item >> 3) & 3);
     const int row = rg * 8 + r8;
     const int r = tile_row0 + row;
-    it[u].soff = rg * 128 + chunk * 32 + r8 * 4;  // (rg*512 + chunk*128 + r8*16) bytes / 4
+    // K-major core matrices of 8 rows x 16 bytes: a 4-window chunk is one
+    // core matrix column (TF32) or half of one (BF16)
+    it[u].soff = BF ? rg * 256 + (chunk >> 1) * 128 + r8 * 16 + (chunk & 1) * 8
+                    : rg * 512 + chunk * 128 + r8 * 16;
     it[u].ok = r < 2 * p.D;
     const int a = r % p.D;
     it[u].comp = r >= p.D ? 1 : 0;
@@ -119,8 +134,48 @@ __device__ __forceinline__ void build_items(const GemmParams &p, int tile_row0, 
   }
 }
 
+// The split parts of four consecutive values into the part tiles at dst
+// (part k at dst + k * tile bytes), at byte offset soff.
+//  TF32: hi = the value rounded to TF32, lo = the rest rounded to TF32.
+//  BF16: hi = RN_bf16(x), mid = RN_bf16(x - hi), lo = RN_bf16(x - hi - mid)
+//        (each difference exact in FP32).
+template <bool BF>
+__device__ __forceinline__ void store_parts(const float (&v)[4], unsigned char *dst, int soff) {
+  if constexpr (BF) {
+    unsigned short h[4], m[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const __nv_bfloat16 bh = __float2bfloat16_rn(v[e]);
+      const float r1 = v[e] - __bfloat162float(bh);
+      const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
+      const float r2 = r1 - __bfloat162float(bm);
+      h[e] = __bfloat16_as_ushort(bh);
+      m[e] = __bfloat16_as_ushort(bm);
+      l[e] = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+    }
+    constexpr int T = GFmt<true>::kTileBytes;
+    *(uint2 *)(dst + soff) = make_uint2(h[0] | ((unsigned)h[1] << 16), h[2] | ((unsigned)h[3] << 16));
+    *(uint2 *)(dst + T + soff) = make_uint2(m[0] | ((unsigned)m[1] << 16), m[2] | ((unsigned)m[3] << 16));
+    *(uint2 *)(dst + 2 * T + soff) =
+        make_uint2(l[0] | ((unsigned)l[1] << 16), l[2] | ((unsigned)l[3] << 16));
+  } else {
+    float4 h, l;
+    h.x = tf32_rna(v[0]);
+    h.y = tf32_rna(v[1]);
+    h.z = tf32_rna(v[2]);
+    h.w = tf32_rna(v[3]);
+    l.x = tf32_rna(v[0] - h.x);
+    l.y = tf32_rna(v[1] - h.y);
+    l.z = tf32_rna(v[2] - h.z);
+    l.w = tf32_rna(v[3] - h.w);
+    *(float4 *)(dst + soff) = h;
+    *(float4 *)(dst + GFmt<false>::kTileBytes + soff) = l;
+  }
+}
+
+template <bool BF>
 __device__ __forceinline__ void fill_tile(const GemmParams &p, const GItem (&it)[2], int pw, int q0,
-                                          float *hi, float *lo) {
+                                          unsigned char *dst) {
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -134,24 +189,15 @@ __device__ __forceinline__ void fill_tile(const GemmParams &p, const GItem (&it)
         }
       }
     }
-    float4 h, l;
-    h.x = tf32_rna(v[0]);
-    h.y = tf32_rna(v[1]);
-    h.z = tf32_rna(v[2]);
-    h.w = tf32_rna(v[3]);
-    l.x = tf32_rna(v[0] - h.x);
-    l.y = tf32_rna(v[1] - h.y);
-    l.z = tf32_rna(v[2] - h.z);
-    l.w = tf32_rna(v[3] - h.w);
-    *(float4 *)(hi + it[u].soff) = h;
-    *(float4 *)(lo + it[u].soff) = l;
+    store_parts<BF>(v, dst, it[u].soff);
   }
 }
 
 // The same operand tile from the staged A region: reg[r * RWf + 2c + comp]
 // holds component comp of A[pw + r][q0 + c].
+template <bool BF>
 __device__ __forceinline__ void fill_tile_smem(const GemmParams &p, const GItem (&it)[2], int q0,
-                                               const float *reg, float *hi, float *lo) {
+                                               const float *reg, unsigned char *dst) {
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -161,17 +207,7 @@ __device__ __forceinline__ void fill_tile_smem(const GemmParams &p, const GItem 
       for (int e = 0; e < 4; ++e)
         if (q0 + it[u].qoff + e < p.W) v[e] = src[2 * e];  // window q must exist
     }
-    float4 h, l;
-    h.x = tf32_rna(v[0]);
-    h.y = tf32_rna(v[1]);
-    h.z = tf32_rna(v[2]);
-    h.w = tf32_rna(v[3]);
-    l.x = tf32_rna(v[0] - h.x);
-    l.y = tf32_rna(v[1] - h.y);
-    l.z = tf32_rna(v[2] - h.z);
-    l.w = tf32_rna(v[3] - h.w);
-    *(float4 *)(hi + it[u].soff) = h;
-    *(float4 *)(lo + it[u].soff) = l;
+    store_parts<BF>(v, dst, it[u].soff);
   }
 }
 
@@ -180,6 +216,15 @@ __device__ __forceinline__ void mma_tf32(unsigned tmem, uint64_t ad, uint64_t bd
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// kind::f16 with A and B both BF16 (K = 16), FP32 accumulation
+__device__ __forceinline__ void mma_bf16(unsigned tmem, uint64_t ad, uint64_t bd, unsigned idesc,
+                                         unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
@@ -241,13 +286,15 @@ __device__ __forceinline__ void flush_acc(unsigned tmem, unsigned acc_col, bool 
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+template <bool BF>
 __global__ void __launch_bounds__(kGThreads, 1)
-    k_gemm_tf32x3(const GemmParams p, const __grid_constant__ CUtensorMap tmap) {
+    k_gemm_split(const GemmParams p, const __grid_constant__ CUtensorMap tmap) {
+  using F = GFmt<BF>;
   extern __shared__ __align__(1024) unsigned char smem_g[];
-  // operand stages x [A_hi, A_lo, B_hi, B_lo], the A-region ring, then the
+  // operand stages x [A parts, B parts], the A-region ring, then the
   // barriers and the TMEM address
-  float *stage_base = (float *)smem_g;
-  unsigned char *reg_base = smem_g + kGStages * kGStageBytes;
+  unsigned char *stage_base = smem_g;
+  unsigned char *reg_base = smem_g + kGStages * kGStageBytesMax;
   uint64_t *bars = (uint64_t *)(reg_base + kGRegRingBytes);
   uint64_t *full = bars;                          // [stages] built: one arrival per filler warp
   uint64_t *empty = full + kGStages;              // [stages] read by the tensor core (commit)
@@ -305,8 +352,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
     if (p.use_tma && tid == 0)
       for (; issued < p.RS && issued < nk; ++issued) issue_region(issued, (int)issued);
     GItem ia[2], ib[2];
-    build_items(p, ti * kGT, ia);
-    build_items(p, tj * kGT, ib);
+    build_items<BF>(p, ti * kGT, ia);
+    build_items<BF>(p, tj * kGT, ib);
     long long flushed = 0;  // chunks added into the running sum
     // step k's ring slot and its phase parity, and its window row / column
     // step, kept incrementally (no divisions in the loop)
@@ -337,18 +384,16 @@ __global__ void __launch_bounds__(kGThreads, 1)
         ok = false;
         break;
       }
-      float *ahi = stage_base + st * (kGStageBytes / 4);
-      float *alo = ahi + kGTileBytes / 4;
-      float *bhi = alo + kGTileBytes / 4;
-      float *blo = bhi + kGTileBytes / 4;
+      unsigned char *apart = stage_base + st * F::kStageBytes;
+      unsigned char *bpart = apart + F::kParts * F::kTileBytes;
       const int q0 = qs * kGKW;
       if (p.use_tma) {
         const float *reg = (const float *)(reg_base + rslot * p.RSLOT);
-        fill_tile_smem(p, ia, q0, reg, ahi, alo);
-        if (!diag) fill_tile_smem(p, ib, q0, reg, bhi, blo);
+        fill_tile_smem<BF>(p, ia, q0, reg, apart);
+        if (!diag) fill_tile_smem<BF>(p, ib, q0, reg, bpart);
       } else {
-        fill_tile(p, ia, pw, q0, ahi, alo);
-        if (!diag) fill_tile(p, ib, pw, q0, bhi, blo);
+        fill_tile<BF>(p, ia, pw, q0, apart);
+        if (!diag) fill_tile<BF>(p, ib, pw, q0, bpart);
       }
       // generic-proxy writes visible to the tensor core, then hand over
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -400,8 +445,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
     }
   } else if (lane == 0) {
     // ---- MMA issuer -----------------------------------------------------------
-    // D = f32 (bit 4), A = B = tf32 (2), both K-major, N = 128, M = 128
-    const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    // D = f32 (bit 4), A = B = tf32 (2) or bf16 (1), both K-major, N = 128,
+    // M = 128
+    const unsigned fmt = BF ? 1u : 2u;
+    const unsigned idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
     for (long long k = 0; k < nk; ++k) {
       const int st = (int)(k % kGStages);
       if (!mbar_wait(&full[st], (unsigned)((k / kGStages) & 1), kGWaitNs)) {
@@ -411,17 +458,28 @@ __global__ void __launch_bounds__(kGThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long chunk = k / kGChunk;
       const bool chunk_start = (k % kGChunk) == 0;
-      const float *ahi = stage_base + st * (kGStageBytes / 4);
-      const unsigned uah = smem_u32(ahi), ual = uah + kGTileBytes;
-      const unsigned ubh = diag ? uah : uah + 2 * kGTileBytes, ubl = diag ? ual : uah + 3 * kGTileBytes;
+      const unsigned T = F::kTileBytes, sbo = F::kSBO;
+      const unsigned ua0 = smem_u32(stage_base + st * F::kStageBytes);  // A part 0
+      const unsigned ub0 = diag ? ua0 : ua0 + F::kParts * T;           // B part 0
       const unsigned dacc = tmem + (unsigned)(chunk & 1) * 128;
+      if constexpr (BF) {
+        // one K = 16 slice: hh + hm + mh + mm + hl + lh
+        const unsigned acc0 = chunk_start ? 0u : 1u;
+        mma_bf16(dacc, smem_desc(ua0, sbo), smem_desc(ub0, sbo), idesc, acc0);
+        mma_bf16(dacc, smem_desc(ua0, sbo), smem_desc(ub0 + T, sbo), idesc, 1u);
+        mma_bf16(dacc, smem_desc(ua0 + T, sbo), smem_desc(ub0, sbo), idesc, 1u);
+        mma_bf16(dacc, smem_desc(ua0 + T, sbo), smem_desc(ub0 + T, sbo), idesc, 1u);
+        mma_bf16(dacc, smem_desc(ua0, sbo), smem_desc(ub0 + 2 * T, sbo), idesc, 1u);
+        mma_bf16(dacc, smem_desc(ua0 + 2 * T, sbo), smem_desc(ub0, sbo), idesc, 1u);
+      } else {
 #pragma unroll
-      for (int s = 0; s < kGKW / 8; ++s) {
-        const unsigned o = s * 256;  // two core matrices (8 TF32) along K per MMA
-        const unsigned acc0 = (!chunk_start || s > 0) ? 1u : 0u;
-        mma_tf32(dacc, smem_desc(uah + o), smem_desc(ubh + o), idesc, acc0);
-        mma_tf32(dacc, smem_desc(uah + o), smem_desc(ubl + o), idesc, 1u);
-        mma_tf32(dacc, smem_desc(ual + o), smem_desc(ubh + o), idesc, 1u);
+        for (int s = 0; s < kGKW / 8; ++s) {
+          const unsigned o = s * 256;  // two core matrices (8 TF32) along K per MMA
+          const unsigned acc0 = (!chunk_start || s > 0) ? 1u : 0u;
+          mma_tf32(dacc, smem_desc(ua0 + o, sbo), smem_desc(ub0 + o, sbo), idesc, acc0);
+          mma_tf32(dacc, smem_desc(ua0 + o, sbo), smem_desc(ub0 + T + o, sbo), idesc, 1u);
+          mma_tf32(dacc, smem_desc(ua0 + T + o, sbo), smem_desc(ub0 + o, sbo), idesc, 1u);
+        }
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -546,9 +604,10 @@ size_t gemm_workspace_size(long long N, long long M, int P, int Q) {
   return ws;
 }
 
-cudaError_t launch_gemm_tf32x3(const void *A, long long N, long long M, long long lda, int P, int Q,
-                               void *R, int mean, void *workspace, size_t ws_bytes, int sms,
-                               cudaStream_t s, bool *ws_ok) {
+template <bool BF>
+static cudaError_t launch_gemm_split(const void *A, long long N, long long M, long long lda, int P,
+                                     int Q, void *R, int mean, void *workspace, size_t ws_bytes,
+                                     int sms, cudaStream_t s, bool *ws_ok) {
   GemmParams g;
   size_t need;
   gemm_plan(N, M, P, Q, sms < kGMaxSms ? sms : kGMaxSms, g, need);
@@ -583,16 +642,28 @@ cudaError_t launch_gemm_tf32x3(const void *A, long long N, long long M, long lon
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-    e = cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_gemm_split<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_done[dev] = true;
   }
   if ((e = cudaMemsetAsync(workspace, 0, 4, s)) != cudaSuccess) return e;
-  k_gemm_tf32x3<<<g.ntiles * g.nsplit, kGThreads, smem, s>>>(g, tmap);
+  k_gemm_split<BF><<<g.ntiles * g.nsplit, kGThreads, smem, s>>>(g, tmap);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const long long DD = (long long)g.D * g.D;
   k_gemm_assemble<<<(unsigned)((DD + 255) / 256), 256, 0, s>>>(g);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tf32x3(const void *A, long long N, long long M, long long lda, int P, int Q,
+                               void *R, int mean, void *workspace, size_t ws_bytes, int sms,
+                               cudaStream_t s, bool *ws_ok) {
+  return launch_gemm_split<false>(A, N, M, lda, P, Q, R, mean, workspace, ws_bytes, sms, s, ws_ok);
+}
+
+cudaError_t launch_gemm_bf16x3(const void *A, long long N, long long M, long long lda, int P, int Q,
+                               void *R, int mean, void *workspace, size_t ws_bytes, int sms,
+                               cudaStream_t s, bool *ws_ok) {
+  return launch_gemm_split<true>(A, N, M, lda, P, Q, R, mean, workspace, ws_bytes, sms, s, ws_ok);
 }
 
 }  // namespace cov
