@@ -74,21 +74,26 @@ __device__ __forceinline__ int row_class(int n, int P, int Hn) {
 }
 
 // T[(rc * NCC + cc) * ND + Delta], Delta = (dr + P - 1) + (2P - 1)(dc + Q - 1).
-// One CTA per Delta. The admissible offsets of a class are a prefix (top
-// classes), the full range (inner class) or a suffix (bottom classes) of
-// [0, P-1] (columns alike), so every entry is a sum of column prefix or
-// suffix sums over a prefix or suffix of the columns: no differences, no
-// cancellation. h[i][j] = H[(i,j)][(i+dr, j+dc)], zero where (i+dr, j+dc)
-// leaves the window.
-__global__ void __launch_bounds__(256) k_adjs_weights(const StParams p0) {
+// One warp per Delta, kStWW warps a CTA. The admissible offsets of a class
+// are a prefix (top classes), the full range (inner class) or a suffix
+// (bottom classes) of [0, P-1] (columns alike), so every entry is a sum of
+// column prefix or suffix sums over a prefix or suffix of the columns: no
+// differences, no cancellation. h[i][j] = H[(i,j)][(i+dr, j+dc)], zero where
+// (i+dr, j+dc) leaves the window. The mean's 1/K is a multiplication by the
+// FP32 reciprocal (within 1.5 ulp of the quotient).
+constexpr int kStWW = 8;
+
+__global__ void __launch_bounds__(kStWW * 32) k_adjs_weights(const StParams p0) {
   const StParams p = member(p0);
   extern __shared__ __align__(16) unsigned char smem_w[];
   const int P = p.P, Q = p.Q, D = P * Q;
-  float2 *pre = (float2 *)smem_w;  // [Q][P]: pre[j][r] = sum_{i <= r} h[i][j]
-  float2 *suf = pre + P * Q;       // [Q][P]: suf[j][r] = sum_{i >= r} h[i][j]
-  const int di = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int di = blockIdx.x * kStWW + warp;
+  if (di >= p.ND) return;  // whole warps; no CTA barrier below
+  float2 *pre = (float2 *)smem_w + (size_t)warp * 2 * D;  // [Q][P]: sum_{i <= r} h[i][j]
+  float2 *suf = pre + D;                                    // [Q][P]: sum_{i >= r} h[i][j]
   const int dr = di % (2 * P - 1) - (P - 1), dc = di / (2 * P - 1) - (Q - 1);
-  for (int e = threadIdx.x; e < P * Q; e += blockDim.x) {
+  for (int e = lane; e < D; e += 32) {
     const int i = e % P, j = e / P;
     float2 h = make_float2(0.f, 0.f);
     if (i + dr >= 0 && i + dr < P && j + dc >= 0 && j + dc < Q) {
@@ -99,8 +104,8 @@ __global__ void __launch_bounds__(256) k_adjs_weights(const StParams p0) {
     pre[e] = h;
     suf[e] = h;
   }
-  __syncthreads();
-  for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+  __syncwarp();
+  for (int j = lane; j < Q; j += 32) {
     for (int i = 1; i < P; ++i) {
       pre[j * P + i].x += pre[j * P + i - 1].x;
       pre[j * P + i].y += pre[j * P + i - 1].y;
@@ -110,36 +115,23 @@ __global__ void __launch_bounds__(256) k_adjs_weights(const StParams p0) {
       suf[j * P + i].y += suf[j * P + i + 1].y;
     }
   }
-  __syncthreads();
+  __syncwarp();
   const float inv = p.mean ? 1.0f / (float)p.K : 1.0f;
-  const bool exact = !p.mean || p.K <= (1LL << 24);
-  for (int rc = threadIdx.x; rc < p.NRC; rc += blockDim.x) {
+  for (int rc = lane; rc < p.NRC; rc += 32) {
     // v[j]: the row class's range summed in column j
     const float2 *src = rc <= P - 1 ? pre + rc : suf + (rc - P + 1);
     float2 *out = p.T + (long long)rc * p.NCC * p.ND + di;
-    auto put = [&](int cc, float2 v) {
-      if (p.mean) {
-        if (exact) {
-          v.x = v.x / (float)p.K;
-          v.y = v.y / (float)p.K;
-        } else {
-          v.x *= inv;
-          v.y *= inv;
-        }
-      }
-      out[(long long)cc * p.ND] = v;
-    };
     float2 acc = make_float2(0.f, 0.f);
     for (int j = 0; j < Q; ++j) {  // column classes 0..Q-1: prefixes j' <= cc
       acc.x += src[j * P].x;
       acc.y += src[j * P].y;
-      put(j, acc);
+      out[(long long)j * p.ND] = make_float2(acc.x * inv, acc.y * inv);
     }
     acc = make_float2(0.f, 0.f);
     for (int j = Q - 1; j >= 1; --j) {  // classes Q..2Q-2: suffixes j' >= cc - Q + 1
       acc.x += src[j * P].x;
       acc.y += src[j * P].y;
-      put(Q - 1 + j, acc);
+      out[(long long)(Q - 1 + j) * p.ND] = make_float2(acc.x * inv, acc.y * inv);
     }
   }
 }
@@ -220,7 +212,8 @@ __global__ void __launch_bounds__(256) k_adjs_inner(const StParams p0) {
 }
 
 // Fringe elements (outside the inner box), one warp each: lanes take the
-// column lags (coalesced loads of A), a loop takes the row lags, weights of
+// column lags (coalesced loads of A), a loop takes the row lags (a lane's
+// weights are consecutive in the table, four to a 32-byte sector), weights of
 // the element's row and column class from the table, then a warp sum.
 __global__ void __launch_bounds__(256) k_adjs_fringe(const StParams p0, long long n_fringe) {
   const StParams p = member(p0);
@@ -304,9 +297,17 @@ cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, lo
   p.sG = sG;
   p.sdA = sdA;
   p.sT = (long long)p.ND * p.NRC * p.NCC;
-  const size_t wsm = (size_t)2 * P * Q * sizeof(float2);
-  k_adjs_weights<<<dim3((unsigned)p.ND, (unsigned)batch), 256, wsm, s>>>(p);
-  cudaError_t e = cudaGetLastError();
+  const size_t wsm = (size_t)kStWW * 2 * P * Q * sizeof(float2);
+  cudaError_t e;
+  static size_t wattr_done = 0;
+  if (wsm > 48 * 1024 && wsm > wattr_done) {
+    e = cudaFuncSetAttribute(k_adjs_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
+    if (e != cudaSuccess) return e;
+    wattr_done = wsm;
+  }
+  k_adjs_weights<<<dim3((unsigned)((p.ND + kStWW - 1) / kStWW), (unsigned)batch), kStWW * 32, wsm,
+                   s>>>(p);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n_in = p.Hn - (P - 1), m_in = p.W - (Q - 1);
   const long long tiles =
