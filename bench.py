@@ -771,7 +771,9 @@ def profile_case(case: str) -> int:
     """Small cases of the secondary kernels for ncu captures: 600 uneven
     matrices through the batched launch (seed 3), the dense TF32x3 form on the
     bench workload, the stencil adjoint of a batch of eight 256 x 256 inputs
-    with a 12 x 12 window."""
+    with a 12 x 12 window, the 30 x 30 apertures of 25 x 25 (stride 10,
+    10 x 10 window) of a 315 x 315 image through the one-warp-per-member
+    kernel."""
     import torch
 
     import cov_workloads as wl
@@ -782,6 +784,13 @@ def profile_case(case: str) -> int:
             A = torch.from_numpy(wl.complex_normal((N, M), wl.BATCHED_SEED * 100003 + k, "c64")).cuda()
             items.append((A, torch.empty((P * Q, P * Q), dtype=torch.complex64, device="cuda"), P, Q))
         plan = cov.BatchedPlan(items)
+        ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+        plan.upload(ws)
+        for _ in range(3):
+            plan.run(ws)
+    elif case == "apertures":
+        img = torch.from_numpy(wl.complex_normal((315, 315), 77, "c64")).cuda()
+        plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
         ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
         plan.upload(ws)
         for _ in range(3):
@@ -822,7 +831,7 @@ def main():
     ap.add_argument("--knobs", default=None,
                     help="G,TRB,L,K: use these knobs (lag group, rows per task, re-seed interval, "
                          "kernels 1|4) instead of autotuning")
-    ap.add_argument("--profile-case", choices=("batched", "gemm", "adjoint"), default=None,
+    ap.add_argument("--profile-case", choices=("batched", "gemm", "adjoint", "apertures"), default=None,
                     help="run a few launches of one secondary kernel on a small case (for ncu) "
                          "and exit")
     args = ap.parse_args()
