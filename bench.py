@@ -167,7 +167,7 @@ def dist_setup():
 # of this file that runs anything under oracle/.
 # ---------------------------------------------------------------------------
 def cpu_baseline_leg(A_np, P, Q, um_full, K_full, budget_s: float, gpu_check=None,
-                     rows=None) -> dict:
+                     rows=None, single_thread=False) -> dict:
     """Times the oracle on the first `rows` rows of A (chosen to take about
     budget_s when None) and extrapolates to the full job by window count."""
     import numpy as np
@@ -177,9 +177,9 @@ def cpu_baseline_leg(A_np, P, Q, um_full, K_full, budget_s: float, gpu_check=Non
     threads = os.cpu_count() or 1
     N, M = A_np.shape
 
-    def run(r):
+    def run(r, nthreads=threads):
         t0 = time.perf_counter()
-        R = oracle.cov_window(A_np[:r], P, Q, threads=threads)
+        R = oracle.cov_window(A_np[:r], P, Q, threads=nthreads)
         return time.perf_counter() - t0, R
 
     if rows is None:
@@ -191,6 +191,18 @@ def cpu_baseline_leg(A_np, P, Q, um_full, K_full, budget_s: float, gpu_check=Non
            "sample": (f"first {rows} of {N} rows of the same input ({k_s} of {K_full} window "
                       f"positions), full-job time extrapolated by window count"),
            "sample_seconds": round(t, 3), "rows": rows}
+    if single_thread and threads > 1:
+        # The same oracle on one core (its threaded form splits rows of R with the
+        # same per-element order, so both give the same R), sampled for a quarter of the budget.
+        def run1(r):
+            return run(r, 1)
+        rows1 = calibrate_rows(A_np, P, Q, budget_s / 4, run1)
+        t1, _ = run1(rows1)
+        k1 = (rows1 - P + 1) * (M - Q + 1)
+        out["single_thread"] = {
+            "value": um_full / (t1 * K_full / k1), "unit": UNIT, "cores": 1,
+            "sample": f"first {rows1} of {N} rows ({k1} window positions)",
+            "sample_seconds": round(t1, 3)}
     if gpu_check is not None:
         G = gpu_check(A_np[:rows])
         err = float(np.linalg.norm(G - R_s) / np.linalg.norm(R_s))
@@ -498,7 +510,8 @@ def bench_ours(args, rank, world, local):
         def gpu_check(Asub):
             At = torch.from_numpy(np.ascontiguousarray(Asub)).cuda()
             return cov.estimate(At, w.P, w.Q, algo="recurrence").cpu().numpy().astype(np.complex128)
-        line["cpu_baseline"] = cpu_baseline_leg(A_np, w.P, w.Q, um, w.K, args.cpu_seconds, gpu_check)
+        line["cpu_baseline"] = cpu_baseline_leg(A_np, w.P, w.Q, um, w.K, args.cpu_seconds, gpu_check,
+                                                  single_thread=True)
     if args.extras:
         line["rows"] = extras(args, cov, torch, np, wl, mk_events, stream)
         line["rows"]["batched_4096_uneven_f32"] = bench_batched(cov, torch, np, wl, mk_events, stream,
