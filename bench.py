@@ -43,8 +43,8 @@ FALLBACK_HBM_GBS = 6800.0
 # kernel, hash of the combination path's kernel sources at capture time):
 # null once those sources have changed.
 NCU_TRAFFIC = {  # bytes per launch; profiles/k_fused_*.md, profiles/k_products_inner_*.md
-    ("cn_1024x1024_w16_f32", "k_fused", "ccf283ea2f438579"): 8561408,
-    ("cn_1024x1024_w16_f32", "k_products_inner", "ccf283ea2f438579"): 8438016,
+    ("cn_1024x1024_w16_f32", "k_fused", "96da72e2c97e5ecd"): 8561408,
+    ("cn_1024x1024_w16_f32", "k_products_inner", "96da72e2c97e5ecd"): 8438016,
 }
 KERNEL_SOURCES = ("cov_device.cuh", "cov_internal.h", "rec_common.cuh", "rec_products.cuh",
                   "rec_products.cu", "rec_fringe.cuh", "rec_fringe.cu", "rec_reduce.cuh",

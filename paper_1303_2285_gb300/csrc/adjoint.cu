@@ -15,6 +15,7 @@
 #include "../../include/cov.h"
 #include "cov_device.cuh"
 #include "cov_internal.h"
+#include "smem_attr.h"
 #include "plan.h"
 
 namespace cov {
@@ -217,13 +218,8 @@ cov_status cov_estimate_backward_ex(const void *A, const void *G, cov_dtype dtyp
   const int D = P * Q;
   const size_t smem = ((size_t)cov::kAdjTA * D + (size_t)P * (cov::kAdjTW + Q - 1)) * sizeof(float2);
   if (smem > 227 * 1024) return COV_EUNSUPPORTED;
-  static size_t attr_done = 0;
-  if (smem > 48 * 1024 && smem > attr_done) {
-    if (cudaFuncSetAttribute(cov::k_adj_hx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return COV_ECUDA;
-    attr_done = smem;
-  }
+  if (cov::ensure_dyn_smem((const void *)cov::k_adj_hx, smem, false) != cudaSuccess)
+    return COV_ECUDA;
   const long long nqc = (p.W + cov::kAdjTW - 1) / cov::kAdjTW;
   const long long grid1 = nqc * p.Hn * ((D + cov::kAdjTA - 1) / cov::kAdjTA);
   cov::k_adj_hx<<<(unsigned)grid1, 256, smem, s>>>(p);

@@ -26,6 +26,7 @@
 #include "../../include/cov.h"
 #include "cov_device.cuh"
 #include "cov_internal.h"
+#include "smem_attr.h"
 
 namespace cov {
 
@@ -299,12 +300,8 @@ cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, lo
   p.sT = (long long)p.ND * p.NRC * p.NCC;
   const size_t wsm = (size_t)kStWW * 2 * P * Q * sizeof(float2);
   cudaError_t e;
-  static size_t wattr_done = 0;
-  if (wsm > 48 * 1024 && wsm > wattr_done) {
-    e = cudaFuncSetAttribute(k_adjs_weights, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
-    if (e != cudaSuccess) return e;
-    wattr_done = wsm;
-  }
+  e = ensure_dyn_smem((const void *)k_adjs_weights, wsm, false);
+  if (e != cudaSuccess) return e;
   k_adjs_weights<<<dim3((unsigned)((p.ND + kStWW - 1) / kStWW), (unsigned)batch), kStWW * 32, wsm,
                    s>>>(p);
   e = cudaGetLastError();
@@ -314,12 +311,8 @@ cudaError_t launch_stencil_adjoint(const void *A, const void *G, long long N, lo
       (long long)((n_in + kStTR - 1) / kStTR) * ((m_in + kStTC - 1) / kStTC);
   const size_t smem =
       ((size_t)(kStTR + 2 * P - 2) * (kStTC + 2 * Q - 2) + (size_t)p.ND) * sizeof(float2);
-  static size_t attr_done = 0;
-  if (smem > 48 * 1024 && smem > attr_done) {
-    e = cudaFuncSetAttribute(k_adjs_inner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = smem;
-  }
+  e = ensure_dyn_smem((const void *)k_adjs_inner, smem, false);
+  if (e != cudaSuccess) return e;
   k_adjs_inner<<<dim3((unsigned)tiles, (unsigned)batch), 256, smem, s>>>(p);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const long long n_fringe = 2LL * (P - 1) * M + (long long)n_in * 2 * (Q - 1);

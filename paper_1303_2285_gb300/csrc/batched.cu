@@ -36,6 +36,7 @@
 #include "../../include/cov.h"
 #include "cov_device.cuh"
 #include "cov_internal.h"
+#include "smem_attr.h"
 #include "plan.h"
 
 namespace cov {
@@ -839,25 +840,13 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, s
   cudaStream_t s = (cudaStream_t)stream;
   char *w = (char *)workspace;
   const size_t smem = cov::kBSmemBytes;
-  static bool attr_done[64] = {false};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return COV_ECUDA;
-  if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-    if (cudaFuncSetAttribute(cov::k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-      return COV_ECUDA;
-    if (dev >= 0 && dev < 64) attr_done[dev] = true;
-  }
+  if (cov::ensure_dyn_smem((const void *)cov::k_batched, smem, false) != cudaSuccess)
+    return COV_ECUDA;
   if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
   if (plan->warp_kernel) {
     const size_t wsmem = cov::kWWarps * cov::kWWarpBytes;
-    static bool wattr_done[64] = {false};
-    if (dev < 0 || dev >= 64 || !wattr_done[dev]) {
-      if (cudaFuncSetAttribute(cov::k_batched_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)wsmem) != cudaSuccess)
-        return COV_ECUDA;
-      if (dev >= 0 && dev < 64) wattr_done[dev] = true;
-    }
+    if (cov::ensure_dyn_smem((const void *)cov::k_batched_warp, wsmem, false) != cudaSuccess)
+      return COV_ECUDA;
     cov::k_batched_warp<<<plan->grid, cov::kWWarps * 32, wsmem, s>>>(
         (const cov::BDesc *)(w + plan->off_desc), (const int *)(w + plan->off_order),
         (const int *)(w + plan->off_begin), plan->mean);

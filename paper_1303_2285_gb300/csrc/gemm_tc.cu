@@ -31,6 +31,7 @@
 #include "cov_device.cuh"
 #include "cov_launch.h"
 #include "cov_internal.h"
+#include "smem_attr.h"
 #include "plan.h"
 
 namespace cov {
@@ -637,15 +638,8 @@ static cudaError_t launch_gemm_split(const void *A, long long N, long long M, lo
   if (g.RS > kGRegMaxStages) g.RS = kGRegMaxStages;
   if (g.RS < 3) g.use_tma = 0;
   const size_t smem = kGSmemBytes;
-  static bool attr_done[64] = {false};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = ensure_dyn_smem((const void *)k_gemm_split<BF>, smem, false);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-    e = cudaFuncSetAttribute(k_gemm_split<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) attr_done[dev] = true;
-  }
   if ((e = cudaMemsetAsync(workspace, 0, 4, s)) != cudaSuccess) return e;
   k_gemm_split<BF><<<g.ntiles * g.nsplit, kGThreads, smem, s>>>(g, tmap);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -7,6 +7,7 @@
 
 #include "cov_device.cuh"
 #include "cov_internal.h"
+#include "smem_attr.h"
 
 namespace cov {
 
@@ -37,42 +38,11 @@ static cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
-// Raises a kernel's dynamic shared-memory limit once per device and size
-// (host-side cache, so repeated calls issue no attribute call).
-struct SmemAttrEntry {
-  const void *fn;
-  int dev;
-  size_t smem;
-};
-
+// Raises a kernel's dynamic shared-memory limit once per device and size and
+// gives every kernel of the path the same (largest) shared-memory carveout, so
+// that the SMs are not reconfigured between consecutive kernels.
 template <typename K> static cudaError_t ensure_smem_attr(K kern, size_t smem) {
-  static SmemAttrEntry table[256];
-  static int used = 0;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const void *fn = (const void *)kern;
-  int slot = -1;
-  for (int i = 0; i < used; ++i)
-    if (table[i].fn == fn && table[i].dev == dev) {
-      if (table[i].smem >= smem) return cudaSuccess;
-      slot = i;
-      break;
-    }
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  if (slot < 0) {
-    // Same shared-memory carveout for every kernel of the path, so that the
-    // SMs are not reconfigured between consecutive kernels.
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-  }
-  if (slot < 0 && used < 256) slot = used++;
-  if (slot >= 0) table[slot] = {fn, dev, smem};
-  return cudaSuccess;
+  return ensure_dyn_smem((const void *)kern, smem, true);
 }
 
 }  // namespace cov
