@@ -48,3 +48,18 @@ def test_too_small_output_array():
     assert lib.cov_aperture_descs(0x1000, 0, 30, 30, 30, 10, 10, 10, 10, 2, 2, 0x2000, arr, 2,
                                   ctypes.byref(n)) == 1
     assert n.value == 9
+
+
+def test_quarter_million_apertures_plan():
+    # The large image-processing case of Section 2.3: an 8000 x 8000 image cut
+    # into about 250,000 overlapping apertures. R offsets pass 2^31 elements,
+    # so descriptor addresses must be 64-bit; the plan is built on the host.
+    img, R = 0x10000000, 0x7000000000
+    arr = cov.aperture_descs(img, "c64", 8000, 8000, 8000, (25, 25), (16, 16), 10, 10, R)
+    n = len(arr)
+    assert n == 499 * 499
+    assert arr[n - 1].R == R + (n - 1) * 100 * 100 * 8
+    assert arr[n - 1].A == img + (498 * 16 * 8000 + 498 * 16) * 8
+    plan = cov.BatchedPlan(None, descs=arr)
+    assert plan.tuning["form"] == 1
+    assert plan.workspace_bytes >= n * ctypes.sizeof(cov.CovDesc)
