@@ -517,7 +517,7 @@ def bench_ours(args, rank, world, local):
         line["rows"]["batched_4096_uneven_f32"] = bench_batched(cov, torch, np, wl, mk_events, stream,
                                                                 fp32_peak)
         line["rows"]["apertures_100x100_of_25x25_w10_f32"] = bench_apertures(
-            cov, torch, np, wl, mk_events, stream, fp32_peak)
+            cov, torch, np, wl, mk_events, stream, fp32_peak, hbm)
         line["rows"]["diff_b64_256x256_w12_f32"] = bench_adjoint(cov, torch, np, wl, mk_events, stream,
                                                                  fp32_peak)
         line["rows"]["gemm_tf32x3_" + DEFAULT_WORKLOAD] = bench_gemm(cov, torch, np, wl, mk_events, stream)
@@ -575,7 +575,7 @@ def bench_batched(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
             "tuning": tuning}
 
 
-def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
+def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak, hbm) -> dict:
     """Every 25 x 25 aperture at stride 10 of a 1015 x 1015 image (100 x 100
     apertures), 10 x 10 window, read in place by one graph-captured launch."""
     H = W = 1015
@@ -604,7 +604,8 @@ def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
     um = R.shape[0] * cov.plan_info(25, 25, 10, 10)["distinct_products"]
     return {"apertures": R.shape[0], "ms_per_launch": ms, "apertures_per_s": R.shape[0] / (ms * 1e-3),
             "distinct_products_per_s": um / (ms * 1e-3), "fp32_fma_frac": 8.0 * um / (ms * 1e-3) / fp32_peak,
-            "r_bytes": R.numel() * 8, "graph_captured": True, "tuning": tuning}
+            "r_bytes": R.numel() * 8, "r_write_hbm_frac": R.numel() * 8 / (ms * 1e-3) / hbm,
+            "graph_captured": True, "tuning": tuning}
 
 
 def bench_adjoint(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
