@@ -306,7 +306,8 @@ _autograd_fn = None
 
 def covariance(A, P: int, Q: int, norm: str = "mean"):
     """Differentiable estimate: R = covariance(A, P, Q); backward runs the
-    library's adjoint ((G + G^H) X, gather col2im). complex64 CUDA tensors."""
+    library's adjoint (the stencil form where it applies, else (G + G^H) X
+    with a gather col2im). complex64 CUDA tensors."""
     global _autograd_fn
     if _autograd_fn is None:
         _autograd_fn = _make_autograd()
