@@ -49,6 +49,18 @@ def test_oracle_matches_numpy_bruteforce(oracle_mod, N, M, P, Q):
         assert rel_err(Rs, brute_force(A, P, Q, mean=False)) < 1e-14
 
 
+def test_oracle_exhaustive_up_to_10x10(oracle_mod):
+    # every shape N, M <= 10 and every window P <= N, Q <= M, three seeds
+    for N in range(1, 11):
+        for M in range(1, 11):
+            for seed in (0, 1, 2):
+                A = wl.complex_normal((N, M), 2000 + 100 * N + 10 * M + seed)
+                for P in range(1, N + 1):
+                    for Q in range(1, M + 1):
+                        assert rel_err(oracle_mod.cov_window(A, P, Q), brute_force(A, P, Q)) < 1e-14, \
+                            (N, M, P, Q, seed)
+
+
 def test_oracle_matches_bruteforce_medium(oracle_mod):
     A = wl.complex_normal((40, 33), 7)
     for P, Q in ((8, 8), (5, 11), (13, 2)):
