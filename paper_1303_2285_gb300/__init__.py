@@ -146,6 +146,17 @@ def load(build_if_missing: bool = True):
     return _lib
 
 
+_C_NAMES = frozenset(n for n, _, _ in SIGNATURES)
+
+
+def __getattr__(name: str):
+    """Every C entry point under its own name (``paper_1303_2285_gb300.cov_estimate_ex``
+    and so on): the typed ctypes function of the loaded library."""
+    if name in _C_NAMES:
+        return getattr(load(), name)
+    raise AttributeError(f"module {__name__!r} has no attribute {name!r}")
+
+
 def _check(code: int, what: str):
     if code != 0:
         raise CovError(code, what)

@@ -29,6 +29,12 @@ def test_library_exports_every_declared_function():
     for n in names:
         assert hasattr(lib, n), n
         assert n in bound, f"{n} has no binding"
+    assert bound == set(names), "binding names a function the header does not declare"
+    # the package exposes each entry point under the C name
+    for n in names:
+        assert getattr(cov, n) is getattr(lib, n)
+    with pytest.raises(AttributeError):
+        cov.cov_not_a_function
 
 
 def test_status_strings_and_version():
