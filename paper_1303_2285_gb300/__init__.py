@@ -20,8 +20,11 @@ from typing import Optional
 from . import _build
 
 __all__ = ["load", "estimate", "estimate_into", "workspace_size", "plan_info",
-           "check_device_status", "CovError", "ALGOS", "STATUS", "autotune", "tuning_get",
-           "tuning_set", "tuning_clear", "tuning_save", "tuning_load"]
+           "check_device_status", "CovError", "ALGOS", "NORMS", "DTYPES", "STATUS", "autotune",
+           "tuning_get", "tuning_set", "tuning_clear", "tuning_save", "tuning_load",
+           "covariance", "estimate_backward", "estimate_backward_batch",
+           "backward_workspace_size", "BatchedPlan", "aperture_descs", "aperture_batch",
+           "selftest_timeout", "set_stage_events", "SIGNATURES"]
 
 ALGOS = {"auto": 0, "recurrence": 1, "gemm_tf32x3": 2, "gemm_bf16x3": 3, "direct": 4}
 NORMS = {"mean": 0, "sum": 1}
