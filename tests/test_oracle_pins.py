@@ -326,3 +326,71 @@ def test_backward_of_linear_functional(oracle_mod):
     t = 1e-4
     d = (L(A + t * E) - L(A - t * E)) / (2 * t)
     assert abs(d - float(np.real(np.sum(np.conj(dA) * E)))) < 1e-8 * max(1.0, abs(d))
+
+
+# ----------------------------------------------------------------------------
+# Planted mistakes in the adjoint: a NumPy copy of the oracle's adjoint, with
+# one mistake at a time, must fail the finite-difference pin (a Hermitian G)
+# or the linear-functional pin (a general G).
+# ----------------------------------------------------------------------------
+def py_backward(A, G, P, Q, mistake=None):
+    A = np.asarray(A, np.complex128)
+    N, M = A.shape
+    K = (N - P + 1) * (M - Q + 1)
+    if mistake == "g_only":
+        H = 2.0 * G / K                       # drops the Hermitian part of G
+    elif mistake == "no_K":
+        H = G + G.conj().T
+    else:
+        H = (G + G.conj().T) / K
+    dA = np.zeros((N, M), np.complex128)
+    for p in range(N - P + 1):
+        for q in range(M - Q + 1):
+            x = A[p:p + P, q:q + Q].flatten(order="F")
+            y = H @ (x.conj() if mistake == "conj_x" else x)
+            if mistake == "transposed_h":
+                y = H.T @ x
+            dA[p:p + P, q:q + Q] += y.reshape((P, Q), order="F")
+    return dA
+
+
+def adjoint_pins_pass(oracle_mod, backward) -> bool:
+    N, M, P, Q = 5, 6, 2, 3
+    A = wl.complex_normal((N, M), 71)
+    # finite differences of ||R - T||_F^2 (G = 2 (R - T), Hermitian)
+    T = oracle_mod.cov_window(wl.complex_normal((N, M), 72), P, Q)
+    G = 2.0 * (oracle_mod.cov_window(A, P, Q) - T)
+    dA = backward(A, G, P, Q)
+    h = 1e-6
+    fd = np.zeros((N, M), np.complex128)
+    for n in range(N):
+        for m in range(M):
+            for unit in (1.0, 1j):
+                E = np.zeros((N, M), np.complex128)
+                E[n, m] = unit * h
+                d = (_loss(oracle_mod, A + E, T, P, Q) - _loss(oracle_mod, A - E, T, P, Q)) / (2 * h)
+                fd[n, m] += d * (1.0 if unit == 1.0 else 1j)
+    if rel_err(dA, fd) >= 1e-7:
+        return False
+    # L = Re <G, R> for a general G, along a random direction
+    G = wl.complex_normal((P * Q, P * Q), 75)
+    E = wl.complex_normal((N, M), 76)
+    dA = backward(A, G, P, Q)
+
+    def L(X):
+        return float(np.real(np.sum(np.conj(G) * oracle_mod.cov_window(X, P, Q))))
+
+    t = 1e-4
+    d = (L(A + t * E) - L(A - t * E)) / (2 * t)
+    return abs(d - float(np.real(np.sum(np.conj(dA) * E)))) < 1e-8 * max(1.0, abs(d))
+
+
+def test_planted_adjoint_mistakes_are_caught(oracle_mod):
+    A = wl.complex_normal((6, 5), 73)
+    G = wl.complex_normal((6, 6), 74)
+    assert rel_err(py_backward(A, G, 3, 2), oracle_mod.cov_backward(A, G, 3, 2)) < 1e-14
+    assert adjoint_pins_pass(oracle_mod, oracle_mod.cov_backward)
+    assert adjoint_pins_pass(oracle_mod, py_backward)
+    for mistake in ("g_only", "no_K", "conj_x", "transposed_h"):
+        assert not adjoint_pins_pass(oracle_mod,
+                                     lambda A, G, P, Q, m=mistake: py_backward(A, G, P, Q, m)), mistake
