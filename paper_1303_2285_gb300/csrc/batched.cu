@@ -773,7 +773,7 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
     cudaGetLastError();
-    sms = 148;  // no device visible: plan for a typical SM count
+    sms = 152;  // no device visible (host-only use): plan for a GB300 (152 SMs)
   }
   cov_batched_plan *pl = new cov_batched_plan();
   pl->mean = norm == COV_MEAN ? 1 : 0;
