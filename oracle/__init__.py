@@ -14,6 +14,9 @@ Contents
 * ``combinations``  -- the counting and indexing of Section 3 and 4.
 * ``algorithm1``    -- Algorithm 1 in the paper's own steps (pure Python).
 * ``exact``         -- exact Gaussian-integer evaluation of Eq. 2.2.
+* ``gram``          -- Eq. 2.2 as the Gram product X X^H of the window vectors
+                       (BLAS zherk, FP64): the full-size reference where the
+                       window loop would take minutes.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against a closed form, an invariant, a library routine or brute force; none

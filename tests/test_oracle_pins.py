@@ -81,10 +81,30 @@ def test_integer_inputs_exact(oracle_mod, N, M, P, Q):
     assert np.array_equal(S.imag, np.array(Cim, float))
     R = oracle_mod.cov_window(A, P, Q, mean=True)
     K = (N - P + 1) * (M - Q + 1)
-    want_re = np.array([[float(Fraction(v, K)) for v in row] for row in Cre])
-    want_im = np.array([[float(Fraction(v, K)) for v in row] for row in Cim])
-    assert np.array_equal(R.real, want_re)
-    assert np.array_equal(R.imag, want_im)
+    # the exact mean (Fractions) rounded once to FP64 is what an exact sum
+    # followed by one IEEE division by K gives
+    Fre, Fim = exact.covariance_exact(are, aim, P, Q, mean=True)
+    for row_f, row_c in zip(Fre, Cre):
+        assert row_f == [Fraction(v, K) for v in row_c]
+    assert np.array_equal(R.real, np.array([[float(v) for v in row] for row in Fre]))
+    assert np.array_equal(R.imag, np.array([[float(v) for v in row] for row in Fim]))
+    Sre, Sim = exact.covariance_exact(are, aim, P, Q, mean=False)
+    assert (Sre, Sim) == (Cre, Cim)
+
+
+@pytest.mark.parametrize("N,M,P,Q", [(6, 5, 2, 3), (8, 9, 3, 4), (10, 4, 10, 1)])
+def test_exact_window_sum_matches_integer_bruteforce(N, M, P, Q):
+    # NumPy int64 products of the explicitly built window matrix: exact
+    A = wl.integer_valued((N, M), 77 + N * M)
+    W = np.lib.stride_tricks.sliding_window_view(A, (P, Q)).transpose(0, 1, 3, 2)
+    X = W.reshape(-1, P * Q).T
+    Xr, Xi = X.real.astype(np.int64), X.imag.astype(np.int64)
+    want_re = Xr @ Xr.T + Xi @ Xi.T         # Re(x_a conj(x_b))
+    want_im = Xi @ Xr.T - Xr @ Xi.T         # Im(x_a conj(x_b))
+    Cre, Cim = exact.window_sum_exact([[int(v) for v in r] for r in A.real],
+                                      [[int(v) for v in r] for r in A.imag], P, Q)
+    assert np.array_equal(np.array(Cre, dtype=np.int64), want_re)
+    assert np.array_equal(np.array(Cim, dtype=np.int64), want_im)
 
 
 # ----------------------------------------------------------------------------
@@ -187,6 +207,44 @@ def test_paper_printed_counts():
         assert len(cb.unique_combinations(e["P"], e["Q"])) == e["count"]
     for e in g["sm_over_um_hat"]:
         assert cb.sm_over_um_hat(e["N"], e["M"], e["P"], e["Q"]) == Fraction(e["value"])
+
+
+def test_sm_naive_against_the_printed_ratio_and_a_count():
+    # Eq. 4.1 over the upper bound of Eq. 4.7 is the ratio of Eq. 4.8, and the
+    # paper prints its value 45.125 for N = M = 32, P = Q = 13 (Eq. 4.9)
+    with open(os.path.join(GOLDEN, "paper_counts.json")) as f:
+        g = json.load(f)
+    for e in g["sm_over_um_hat"]:
+        N, M, P, Q = e["N"], e["M"], e["P"], e["Q"]
+        assert Fraction(cb.sm_naive(N, M, P, Q)) / cb.um_hat(N, M, P, Q) == Fraction(e["value"])
+    for N, M, P, Q in ((20, 20, 8, 8), (64, 64, 8, 8), (37, 11, 5, 9), (1024, 1024, 16, 16)):
+        assert Fraction(cb.sm_naive(N, M, P, Q)) / cb.um_hat(N, M, P, Q) == \
+            cb.sm_over_um_hat(N, M, P, Q)
+
+    # a count of the multiplications that forming every outer product x x^H
+    # makes, over the positions Section 4.1 counts (N - P down, M - Q right)
+    class Counted:
+        n = 0
+
+        def __init__(self, v):
+            self.v = v
+
+        def __mul__(self, other):
+            Counted.n += 1
+            return Counted(self.v * other.v)
+
+        def conjugate(self):
+            return Counted(self.v.conjugate())
+
+    for N, M, P, Q in ((5, 4, 2, 2), (6, 7, 3, 2), (4, 4, 1, 3)):
+        Counted.n = 0
+        A = wl.complex_normal((N, M), 5)
+        for p in range(N - P):
+            for q in range(M - Q):
+                x = np.array([Counted(complex(A[p + a % P, q + a // P])) for a in range(P * Q)],
+                             dtype=object)
+                np.outer(x, np.conjugate(x))
+        assert Counted.n == cb.sm_naive(N, M, P, Q)
 
 
 @pytest.mark.parametrize("N,M,P,Q", [(64, 64, 8, 8), (1024, 1024, 16, 16),
@@ -394,3 +452,54 @@ def test_planted_adjoint_mistakes_are_caught(oracle_mod):
     for mistake in ("g_only", "no_K", "conj_x", "transposed_h"):
         assert not adjoint_pins_pass(oracle_mod,
                                      lambda A, G, P, Q, m=mistake: py_backward(A, G, P, Q, m)), mistake
+
+
+# ----------------------------------------------------------------------------
+# The Gram form of Eq. 2.2 (oracle/gram.py), the full-size reference.
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("N,M,P,Q", [s for s in SMALL_SHAPES if s[0] * s[1] >= 6])
+def test_gram_form_matches_window_loop_and_bruteforce(oracle_mod, N, M, P, Q):
+    from oracle.gram import cov_gram
+    A = wl.complex_normal((N, M), 3000 + N * M)
+    R = oracle_mod.cov_window(A, P, Q)
+    for g in (1, 2, 0):  # one window row per group, two, the default
+        G = cov_gram(A, P, Q, rows_per_group=g)
+        assert rel_err(G, R) < 1e-14
+        assert rel_err(G, brute_force(A, P, Q)) < 1e-14
+        assert np.array_equal(G, G.conj().T)
+    assert rel_err(cov_gram(A, P, Q, mean=False), brute_force(A, P, Q, mean=False)) < 1e-14
+
+
+def test_gram_form_medium_and_workload_shaped(oracle_mod):
+    from oracle.gram import cov_gram
+    A = wl.complex_normal((40, 33), 7)
+    for P, Q in ((8, 8), (5, 11), (13, 2), (40, 33), (1, 1)):
+        assert rel_err(cov_gram(A, P, Q, rows_per_group=3), oracle_mod.cov_window(A, P, Q)) < 1e-14
+    # the SAR-like recipe (sum of exponentials plus noise), smaller
+    S, _ = wl.sar_like(48, 40, 2, dtype="c128")
+    assert rel_err(cov_gram(S, 12, 10), oracle_mod.cov_window(S, 12, 10)) < 1e-14
+
+
+@pytest.mark.parametrize("N,M,P,Q", [(30, 20, 4, 3), (30, 20, 7, 7), (30, 20, 30, 20),
+                                     (17, 9, 1, 1), (12, 25, 6, 12)])
+def test_gram_form_integer_inputs_bit_exact(oracle_mod, N, M, P, Q):
+    # every partial sum of Gaussian integers is an exact integer in FP64, so
+    # any summation order gives the exact sum and one IEEE division by K
+    from oracle.gram import cov_gram
+    A = wl.integer_valued((N, M), 4000 + N + M)
+    for g in (1, 5, 0):
+        assert np.array_equal(cov_gram(A, P, Q, rows_per_group=g), oracle_mod.cov_window(A, P, Q))
+        assert np.array_equal(cov_gram(A, P, Q, mean=False, rows_per_group=g),
+                              oracle_mod.cov_window(A, P, Q, mean=False))
+
+
+def test_gram_form_closed_forms():
+    from oracle.gram import cov_gram
+    for P, Q in ((1, 1), (3, 2), (9, 7), (4, 5)):
+        assert np.array_equal(cov_gram(np.full((9, 7), 3 + 4j), P, Q),
+                              np.full((P * Q, P * Q), 25.0 + 0j))
+    c, om, nu = 0.7 - 0.2j, 0.9, -2.1
+    A = wl.single_exponential(20, 16, c, om, nu)
+    P, Q = 5, 4
+    v = np.array([np.exp(1j * (om * (a % P) + nu * (a // P))) for a in range(P * Q)])
+    assert rel_err(cov_gram(A, P, Q), abs(c) ** 2 * np.outer(v, v.conj())) < 1e-14
