@@ -85,10 +85,11 @@ typedef enum {
   COV_DIRECT = 4
 } cov_algo;
 
-/* Human-readable name of a status code (static string). */
+/* Human-readable name of a status code (static string). A property of the
+ * library; the paper has no counterpart. */
 const char *cov_status_string(cov_status s);
 
-/* Library version as 10000*major + 100*minor + patch. */
+/* Library version as 10000*major + 100*minor + patch (no paper counterpart). */
 int cov_version(void);
 
 /* ---------------------------------------------------------------------------
@@ -113,7 +114,10 @@ cov_status cov_plan_info(int64_t N, int64_t M, int P, int Q, cov_plan_info_t *ou
 
 /* Bytes of device workspace cov_estimate_ex needs for this problem (0 is
  * possible). Host only. COV_EINVAL on a bad shape, COV_EUNSUPPORTED if the
- * algorithm cannot take it. */
+ * algorithm cannot take it. For COV_RECURRENCE the workspace holds the
+ * partial sums of each unique combination's products (Eq. 3.3-3.6: per
+ * combination, per row block and column block of A) and the box-row and
+ * box-column sums the diagonal walk of Section 3.3 reads. */
 cov_status cov_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
                               cov_algo algo, size_t *bytes);
 
@@ -137,6 +141,28 @@ cov_status cov_estimate_ex(const void *A, cov_dtype dtype, int64_t N, int64_t M,
 cov_status cov_estimate(const void *A, cov_dtype dtype, int64_t N, int64_t M, int P,
                         int Q, void *R, cov_stream_t stream);
 
+/* Interleaved complex elements of the typed entry points (the layout of
+ * CUDA's float2 and double2). */
+typedef struct {
+  float re, im;
+} cov_c64_t;
+typedef struct {
+  double re, im;
+} cov_c128_t;
+
+/* Typed short forms of Eq. 2.1-2.2 (Section 2.2): R (PQ x PQ, device) = the
+ * mean over all window positions of x x^H for the N x M input A (device,
+ * leading dimension M), COV_AUTO. The same call as cov_estimate with
+ * COV_C64 / COV_C128: the workspace comes from the stream-ordered allocator
+ * (cudaMallocAsync / cudaFreeAsync on `stream`, served by the stream's
+ * memory pool). Callers that must not allocate use cov_estimate_ex with a
+ * workspace of their own, or cov_estimate_noalloc. COV_EINVAL on a null
+ * pointer or a bad shape (N, M, P, Q < 1, P > N, Q > M). */
+cov_status cov_estimate_c64(const cov_c64_t *A, int64_t N, int64_t M, int P, int Q, cov_c64_t *R,
+                            cov_stream_t stream);
+cov_status cov_estimate_c128(const cov_c128_t *A, int64_t N, int64_t M, int P, int Q,
+                             cov_c128_t *R, cov_stream_t stream);
+
 /* Size of the static device scratch array behind cov_estimate_noalloc. */
 #define COV_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 
@@ -152,9 +178,12 @@ cov_status cov_estimate(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
  * until the process exits. The caller still passes A and R (device, as for
  * cov_estimate_ex). Nothing is allocated or freed: no cudaMalloc, cudaFree
  * or allocating library routine is called.
- * - The first call made while a given device is current looks up the array's
- *   device address on that device (cudaGetSymbolAddress) and caches it; make
- *   that first call before any stream capture.
+ * - The first call made in a given CUDA context (the device's primary
+ *   context, or a driver context the caller made current) looks up the
+ *   array's device address in that context (cudaGetSymbolAddress) and caches
+ *   it under the context's ID; make that first call before any stream
+ *   capture. A new context (for example after cudaDeviceReset) gets a new
+ *   lookup on its first call.
  * - Problems whose scratch need exceeds COV_NOALLOC_SCRATCH_BYTES (see
  *   cov_workspace_size with COV_RECURRENCE) are rejected with COV_EWORKSPACE
  *   before any work is queued; COV_EUNSUPPORTED for shapes COV_RECURRENCE
@@ -167,10 +196,28 @@ cov_status cov_estimate_noalloc(const void *A, cov_dtype dtype, int64_t N, int64
                                 int64_t lda, int P, int Q, void *R, cov_norm norm,
                                 cov_stream_t stream);
 
+/* The status word of cov_estimate_noalloc's static scratch array (in the
+ * current context): reads it, clears it and returns COV_OK, COV_ETIMEOUT (a
+ * kernel of the last call gave up a bounded wait; R is then incomplete) or
+ * COV_EDEVICE; COV_ECUDA if the copy fails. Synchronises `stream`. Each
+ * cov_estimate_noalloc call clears the word first, so check it after the
+ * call whose result is to be trusted and before the next one. Allocates
+ * nothing. No paper counterpart. */
+cov_status cov_noalloc_check_status(cov_stream_t stream);
+
 /* Reads (and then clears) the status word a previous call left at the start
  * of `workspace`. Synchronises `stream`. Returns COV_OK, COV_ETIMEOUT or
  * COV_EDEVICE; COV_ECUDA if the copy itself fails. */
 cov_status cov_check_device_status(void *workspace, cov_stream_t stream);
+
+/* Measured rate of the FMA pipe the combination path runs on (instrumentation,
+ * not in the paper): COV_C64 times paired FP32 FMAs (fma.rn.f32x2, as the
+ * product kernels issue them), COV_C128 FP64 FMAs, in a kernel of independent
+ * FMA chains on every SM, `reps` (1..100) timed launches after one warm-up;
+ * *fma_per_s = lane FMAs per second of the fastest launch (2 FLOP each).
+ * Synchronises `stream`; no device memory is used. */
+cov_status cov_measure_fma_rate(cov_dtype dtype, int reps, double *fma_per_s,
+                                cov_stream_t stream);
 
 /* Failure-detection self-test (not in the paper). Launches one warp that
  * waits, through the library's bounded mbarrier wait, on a barrier nothing
@@ -286,7 +333,13 @@ cov_status cov_aperture_descs(const void *image, cov_dtype dtype, int64_t H, int
 /* Validates `count` descriptors (HOST array, copied) and builds the task
  * schedule. Only COV_C64 with COV_RECURRENCE (or COV_AUTO) is supported; every
  * member must satisfy the COV_RECURRENCE shape rule. On success *plan owns
- * host memory until cov_batched_plan_destroy. */
+ * host memory until cov_batched_plan_destroy. The schedule is balanced for
+ * the SM count of the device current at creation (152, GB300's, when no
+ * device is visible); cov_batched_upload, cov_estimate_batched and
+ * cov_batched_autotune return COV_EUNSUPPORTED on a device with another SM
+ * count (re-create the plan there). This departs from a device-side
+ * descriptor table read at launch: the plan keeps the descriptors on the
+ * host, where the schedule is built once, and uploads its tables. */
 cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype,
                                    cov_algo algo, cov_norm norm, cov_batched_plan **plan);
 cov_status cov_batched_workspace_size(const cov_batched_plan *plan, size_t *bytes);

@@ -84,7 +84,11 @@ SIGNATURES = [
     ("cov_estimate_ex", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _VP, _I, _I, _VP, _SZ, _VP]),
     ("cov_estimate", _I, [_VP, _I, _I64, _I64, _I, _I, _VP, _VP]),
     ("cov_check_device_status", _I, [_VP, _VP]),
+    ("cov_estimate_c64", _I, [_VP, _I64, _I64, _I, _I, _VP, _VP]),
+    ("cov_estimate_c128", _I, [_VP, _I64, _I64, _I, _I, _VP, _VP]),
     ("cov_estimate_noalloc", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _VP, _I, _VP]),
+    ("cov_noalloc_check_status", _I, [_VP]),
+    ("cov_measure_fma_rate", _I, [_I, _I, ctypes.POINTER(ctypes.c_double), _VP]),
     ("cov_set_stage_events", _I, [ctypes.POINTER(_VP), _I]),
     ("cov_batched_plan_create", _I, [ctypes.POINTER(CovDesc), _I, _I, _I, _I,
                                      ctypes.POINTER(_VP)]),

@@ -223,6 +223,16 @@ cov_status cov_estimate(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
   return st;
 }
 
+cov_status cov_estimate_c64(const cov_c64_t *A, int64_t N, int64_t M, int P, int Q, cov_c64_t *R,
+                            cov_stream_t stream) {
+  return cov_estimate(A, COV_C64, N, M, P, Q, R, stream);
+}
+
+cov_status cov_estimate_c128(const cov_c128_t *A, int64_t N, int64_t M, int P, int Q,
+                             cov_c128_t *R, cov_stream_t stream) {
+  return cov_estimate(A, COV_C128, N, M, P, Q, R, stream);
+}
+
 cov_status cov_set_stage_events(void *const *events, int n_events) {
   if (!events) {
     g_stage_events.on = false;

@@ -815,10 +815,24 @@ cov_status cov_batched_workspace_size(const cov_batched_plan *plan, size_t *byte
   return COV_OK;
 }
 
+// COV_OK when the current device has the SM count the plan's schedule was
+// balanced for; COV_EUNSUPPORTED on another device (re-create the plan there).
+static cov_status plan_matches_device(const cov_batched_plan *pl) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return COV_ECUDA;
+  }
+  return sms == pl->sms ? COV_OK : COV_EUNSUPPORTED;
+}
+
 cov_status cov_batched_upload(const cov_batched_plan *plan, void *workspace, size_t ws_bytes,
                               cov_stream_t stream) {
   if (!plan || !workspace) return COV_EINVAL;
   if (ws_bytes < plan->total || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  const cov_status dst = plan_matches_device(plan);
+  if (dst != COV_OK) return dst;
   cudaStream_t s = (cudaStream_t)stream;
   char *w = (char *)workspace;
   if (cudaMemcpyAsync(w + plan->off_desc, plan->descs.data(), sizeof(cov::BDesc) * plan->descs.size(),
@@ -837,6 +851,8 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, s
                                 cov_stream_t stream) {
   if (!plan || !workspace) return COV_EINVAL;
   if (ws_bytes < plan->total || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  const cov_status dst = plan_matches_device(plan);
+  if (dst != COV_OK) return dst;
   cudaStream_t s = (cudaStream_t)stream;
   char *w = (char *)workspace;
   const size_t smem = cov::kBSmemBytes;
@@ -885,6 +901,8 @@ cov_status cov_batched_autotune(cov_batched_plan *plan, void *workspace, size_t 
                                 cov_stream_t stream) {
   if (!plan || !workspace || reps < 1) return COV_EINVAL;
   if (ws_bytes < plan->total || ((uintptr_t)workspace & 255) != 0) return COV_EWORKSPACE;
+  const cov_status dst = plan_matches_device(plan);
+  if (dst != COV_OK) return dst;
   cudaStream_t s = (cudaStream_t)stream;
   // candidates: the warp form where every member fits it; the CTA form with
   // segments of the whole diagonal or of 2 or 4 outputs, and 2 or 4 row
