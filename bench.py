@@ -2,10 +2,12 @@
 """Benchmark of the covariance-method hot path on GB300.
 
 Prints ONE JSON line. A step is one call of the combination path
-(COV_RECURRENCE) on the bench workload: the plan, the staging of A, every
-distinct product, the seeds, the diagonal walk and the write of R. Inputs are
-resident in HBM when the timed region starts; L2 is flushed (256 MiB write)
-before every timed step, outside the timed events.
+(COV_RECURRENCE) on the bench workload, by default the largest single-GPU
+one: the 2048 x 512 SAR-like complex64 input with a 32 x 32 window (R is
+1024 x 1024). The step covers the plan, the staging of A, every distinct
+product, the seeds, the diagonal walk and the write of R. Inputs are resident
+in HBM when the timed region starts; L2 is flushed (256 MiB write) before
+every timed step, outside the timed events.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -32,7 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "R elements/s and distinct products/s vs plain FP64 GPU path; % roofline; err vs FP64"
 UNIT = "distinct products/s"
-DEFAULT_WORKLOAD = "cn_1024x1024_w16_f32"
+DEFAULT_WORKLOAD = "sar_2048x512_w32_f32"
+GEMM_WORKLOAD = "cn_1024x1024_w16_f32"
 FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128   # FP32 FMA lanes per SM (4 SMSPs x 32)
 FALLBACK_SM_MAX_MHZ = 2070.0
@@ -167,9 +170,12 @@ def dist_setup():
 # of this file that runs anything under oracle/.
 # ---------------------------------------------------------------------------
 def cpu_baseline_leg(A_np, P, Q, um_full, K_full, budget_s: float, gpu_check=None,
-                     rows=None, single_thread=False) -> dict:
+                     rows=None, single_thread=False, R_gpu_full=None) -> dict:
     """Times the oracle on the first `rows` rows of A (chosen to take about
-    budget_s when None) and extrapolates to the full job by window count."""
+    budget_s when None) and extrapolates to the full job by window count.
+    With R_gpu_full (the GPU's R of the whole input, host), also compares it
+    element by element with the oracle's full R (the Gram form of Eq. 2.2,
+    FP64; untimed)."""
     import numpy as np
 
     import oracle
@@ -203,6 +209,18 @@ def cpu_baseline_leg(A_np, P, Q, um_full, K_full, budget_s: float, gpu_check=Non
             "value": um_full / (t1 * K_full / k1), "unit": UNIT, "cores": 1,
             "sample": f"first {rows1} of {N} rows ({k1} window positions)",
             "sample_seconds": round(t1, 3)}
+    if R_gpu_full is not None:
+        from oracle.gram import cov_gram
+        t0 = time.perf_counter()
+        Ro = cov_gram(A_np, P, Q)
+        to = time.perf_counter() - t0
+        Rg = np.asarray(R_gpu_full).astype(np.complex128)
+        out["gpu_err_vs_oracle_full_R"] = {
+            "rel_fro": float(np.linalg.norm(Rg - Ro) / np.linalg.norm(Ro)),
+            "max_abs_rel_to_max": float(np.abs(Rg - Ro).max() / np.abs(Ro).max()),
+            "elements": int(Ro.size),
+            "oracle": "oracle.gram.cov_gram: Eq. 2.2 as X X^H over all window positions, FP64 (BLAS zherk)",
+            "oracle_seconds": round(to, 2)}
     if gpu_check is not None:
         G = gpu_check(A_np[:rows])
         err = float(np.linalg.norm(G - R_s) / np.linalg.norm(R_s))
@@ -221,30 +239,49 @@ def calibrate_rows(A_np, P, Q, budget_s, run) -> int:
 
 
 def bench_reference(args, rank, world):
+    """The oracle as it stands on the host cores. One step = one oracle call on
+    a fixed sample of the workload (its first rows), so that every timed step
+    really runs and the whole run takes a minute or two; value = the full
+    job's distinct products per second, the sample's time scaled by window
+    count (the oracle's cost is proportional to the windows it visits)."""
+    import oracle
     import cov_workloads as wl
     if rank != 0:
         return 0
+    oracle.build()
     w = wl.WORKLOADS[args.workload]
     A_np = wl.workload_input(w)
     um = _um(w)
-    budget = min(3.0, 150.0 / max(1, args.steps + args.warmup))
-    vals = []
-    last = None
-    rows = None
+    threads = os.cpu_count() or 1
+    per_step = min(4.0, 90.0 / max(1, args.steps + args.warmup))
+
+    def run(r, nthreads=threads):
+        t0 = time.perf_counter()
+        R = oracle.cov_window(A_np[:r], w.P, w.Q, threads=nthreads)
+        return time.perf_counter() - t0, R
+
+    rows = calibrate_rows(A_np, w.P, w.Q, per_step, run)
+    k_s = (rows - w.P + 1) * (w.M - w.Q + 1)
+    times = []
+    wall0 = time.perf_counter()
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline_leg(A_np, w.P, w.Q, um, w.K, budget, rows=rows)
-        rows = r["rows"]
+        t, _ = run(rows)
         if k >= args.warmup:
-            vals.append(r["value"])
-        last = r
-    value = statistics.median(vals)
-    t_step = um / value
+            times.append(t)
+    wall = time.perf_counter() - wall0
+    t_step = statistics.mean(times)
+    value = um * (k_s / w.K) / t_step
+    sample = (f"first {rows} of {w.N} rows of the same input ({k_s} of {w.K} window positions) "
+              f"per step; value scales the step time to the full job by window count")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(w),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+            "step_definition": "one oracle call on the sample below (all steps run; none is extrapolated)",
+            "full_job_ms_extrapolated": t_step * (w.K / k_s) * 1e3,
+            "wall_s_incl_warmup": wall,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -350,15 +387,14 @@ def bench_ours(args, rank, world, local):
         time.sleep(0.3)
     barrier()
     codes = 0
-    wall0 = time.perf_counter()
+    t_enq = time.perf_counter()
     for k in range(K):
         codes |= flush_l2(k + 1)
         starts[k].record(stream)
         codes |= fn(*cargs)
         ends[k].record(stream)
-    enqueue_s = time.perf_counter() - wall0
+    enqueue_s = time.perf_counter() - t_enq
     barrier()
-    wall = time.perf_counter() - wall0
     if codes != 0:
         raise RuntimeError(f"cov_estimate_ex failed in the timed loop (status bits {codes})")
     clocks = sampler.stop(local) if rank == 0 else None
@@ -446,6 +482,7 @@ def bench_ours(args, rank, world, local):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     f_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
     fp32_peak = sms * FP32_LANES_PER_SM * 2 * f_max * 1e6  # FLOP/s
+    fma_rate = measure_fma_rates(cov)
     fp64 = w.dtype == "c128"
     k1_ms = statistics.mean(stage_ms[0])
     k1_flops = 8.0 * (um if fused else info["products_inner"])  # 4 FMA per complex product
@@ -458,7 +495,9 @@ def bench_ours(args, rank, world, local):
                     f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {f_max:.0f} MHz "
                     f"({'MEASURED_PEAKS.json sm_max_mhz' if 'sm_max_mhz' in peaks else 'recipe max clock'})"
                     + ("; this workload computes in FP64: the FP32 figure is an upper bound" if fp64 else "")),
-                "algorithmic_flops_per_launch": k1_flops, "launch_ms": k1_ms}
+                "algorithmic_flops_per_launch": k1_flops, "launch_ms": k1_ms,
+                "measured_fp32_fma_tflops": 2 * fma_rate["f32"] / 1e12,
+                "frac_of_measured_fp32_fma": achieved / (2 * fma_rate["f32"])}
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9
     bytes_io = w.N * w.M * A.element_size() + D * D * R.element_size()
     t_roof = max(4.0 * um / (fp32_peak / 2), bytes_io / hbm)
@@ -502,7 +541,6 @@ def bench_ours(args, rank, world, local):
                                       stage4_ms)},
         "roofline": roofline, "step_roofline": step_roofline, "e2e": e2e,
         "gpu_launches": (1 if fused else 4) * K, "clocks": clocks,
-        "wall_ms_incl_l2_flush": wall * 1e3,
         "host_enqueue_us_per_step": enqueue_s * 1e6 / K,
     }
 
@@ -511,7 +549,8 @@ def bench_ours(args, rank, world, local):
             At = torch.from_numpy(np.ascontiguousarray(Asub)).cuda()
             return cov.estimate(At, w.P, w.Q, algo="recurrence").cpu().numpy().astype(np.complex128)
         line["cpu_baseline"] = cpu_baseline_leg(A_np, w.P, w.Q, um, w.K, args.cpu_seconds, gpu_check,
-                                                  single_thread=True)
+                                                  single_thread=True, R_gpu_full=Rn)
+        line["err_vs_oracle"] = line["cpu_baseline"]["gpu_err_vs_oracle_full_R"]
     if args.extras:
         line["rows"] = extras(args, cov, torch, np, wl, mk_events, stream)
         line["rows"]["batched_4096_uneven_f32"] = bench_batched(cov, torch, np, wl, mk_events, stream,
@@ -520,14 +559,28 @@ def bench_ours(args, rank, world, local):
             cov, torch, np, wl, mk_events, stream, fp32_peak, hbm)
         line["rows"]["diff_b64_256x256_w12_f32"] = bench_adjoint(cov, torch, np, wl, mk_events, stream,
                                                                  fp32_peak)
-        line["rows"]["gemm_tf32x3_" + DEFAULT_WORKLOAD] = bench_gemm(cov, torch, np, wl, mk_events, stream)
-        line["rows"]["gemm_bf16x3_" + DEFAULT_WORKLOAD] = bench_gemm(cov, torch, np, wl, mk_events, stream,
-                                                                     "gemm_bf16x3")
+        line["rows"]["gemm_tf32x3_" + GEMM_WORKLOAD] = bench_gemm(cov, torch, np, wl, mk_events, stream)
+        line["rows"]["gemm_bf16x3_" + GEMM_WORKLOAD] = bench_gemm(cov, torch, np, wl, mk_events, stream,
+                                                                  "gemm_bf16x3")
     print(json.dumps(line))
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def measure_fma_rates(cov) -> dict:
+    """Lane FMAs per second of the FP32 (paired) and FP64 pipes, measured by
+    the library's FMA-chain kernel on this GPU (cov_measure_fma_rate)."""
+    import torch
+    lib = cov.load()
+    out = {}
+    for name, code in (("f32", 0), ("f64", 1)):
+        v = ctypes.c_double(0)
+        if lib.cov_measure_fma_rate(code, 5, ctypes.byref(v), torch.cuda.current_stream().cuda_stream):
+            raise RuntimeError("cov_measure_fma_rate failed")
+        out[name] = v.value
+    return out
 
 
 def bench_batched(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
@@ -684,7 +737,7 @@ TF32_OVER_BF16_NOMINAL = 1.1 / 2.25  # dense tensor rates per GPU (recipe's nomi
 def bench_gemm(cov, torch, np, wl, mk_events, stream, algo: str = "gemm_tf32x3") -> dict:
     """Dense form R = X X^H on tcgen05 on the bench workload: TF32 x3 (three
     split products, K = 8 MMAs) or BF16 x3 (six split products, K = 16)."""
-    w = wl.WORKLOADS[DEFAULT_WORKLOAD]
+    w = wl.WORKLOADS[GEMM_WORKLOAD]
     A = torch.from_numpy(wl.workload_input(w)).cuda()
     D = w.P * w.Q
     R = torch.empty((D, D), dtype=torch.complex64, device="cuda")
@@ -729,7 +782,14 @@ def extras(args, cov, torch, np, wl, mk_events, stream) -> dict:
     of n calls (device time only, no host gaps; inputs stay L2-resident)."""
     out = {}
     lib = cov.load()
-    for name in ("plain_64x64_w8_f64", "sar_2048x512_w32_f32"):
+    fma_rates = measure_fma_rates(cov)
+    out["measured_fma_rates"] = {"fp32_tflops": 2 * fma_rates["f32"] / 1e12,
+                                 "fp64_tflops": 2 * fma_rates["f64"] / 1e12,
+                                 "how": "cov_measure_fma_rate: independent FMA chains on every SM, "
+                                        "best of 5 launches, CUDA events"}
+    for name in ("plain_64x64_w8_f64", "cn_1024x1024_w16_f32", "sar_2048x512_w32_f32"):
+        if name == args.workload:
+            continue
         w = wl.WORKLOADS[name]
         dt = torch.complex64 if w.dtype == "c64" else torch.complex128
         A = torch.from_numpy(wl.workload_input(w)).cuda()
@@ -772,8 +832,13 @@ def extras(args, cov, torch, np, wl, mk_events, stream) -> dict:
         torch.cuda.synchronize()
         dms = e2[0].elapsed_time(e2[1])
         Rn, Rdn = R.cpu().numpy().astype(np.complex128), Rd.cpu().numpy().astype(np.complex128)
+        row_fp64 = w.dtype == "c128"
+        rate = fma_rates["f64" if row_fp64 else "f32"]
         out[name] = {"ms_per_call": ms, "timing": f"median of {reps} replays of a {n}-call CUDA graph, L2 warm",
                      "tuning": knobs,
+                     "fma_pipe": "FP64" if row_fp64 else "FP32",
+                     "measured_fma_tflops": 2 * rate / 1e12,
+                     "frac_of_measured_fma_peak": 4.0 * info["distinct_products"] / (ms * 1e-3) / rate,
                      "distinct_products_per_s": info["distinct_products"] / (ms * 1e-3),
                      "r_elements_per_s": D * D / (ms * 1e-3), "fp64_direct_ms": dms,
                      "speedup_vs_fp64_direct": dms / ms,
@@ -781,7 +846,7 @@ def extras(args, cov, torch, np, wl, mk_events, stream) -> dict:
     return out
 
 
-def profile_case(case: str) -> int:
+def profile_case(case: str, knobs=None) -> int:
     """Small cases of the secondary kernels for ncu captures: 600 uneven
     matrices through the batched launch (seed 3), the dense TF32x3 form on the
     bench workload, the stencil adjoint of a batch of eight 256 x 256 inputs
@@ -792,7 +857,23 @@ def profile_case(case: str) -> int:
 
     import cov_workloads as wl
     import paper_1303_2285_gb300 as cov
-    if case == "batched":
+    if case in ("sar", "cn"):
+        # the bench's single-matrix step: the combination path on the SAR-like
+        # 2048 x 512 input (32 x 32 window) or the 1024 x 1024 one (16 x 16)
+        w = wl.WORKLOADS["sar_2048x512_w32_f32" if case == "sar" else "cn_1024x1024_w16_f32"]
+        if knobs:
+            g_, trb_, l_, k_ = (int(x) for x in knobs.split(","))
+            cov.tuning_set(w.dtype, w.N, w.M, w.P, w.Q, {"lag_group": g_, "rows_per_task": trb_,
+                                                         "reseed_interval": l_, "kernels": k_})
+        A = torch.from_numpy(wl.workload_input(w)).cuda()
+        R = torch.empty((w.P * w.Q, w.P * w.Q), dtype=torch.complex64, device="cuda")
+        ws = torch.empty(cov.workspace_size(w.dtype, w.N, w.M, w.P, w.Q, "recurrence"),
+                         dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            cov.estimate_into(A, R, w.P, w.Q, algo="recurrence", workspace=ws)
+        torch.cuda.synchronize()
+        cov.check_device_status(ws)
+    elif case == "batched":
         items = []
         for k, (N, M, P, Q) in enumerate(wl.batched_shapes(600, wl.BATCHED_SEED)):
             A = torch.from_numpy(wl.complex_normal((N, M), wl.BATCHED_SEED * 100003 + k, "c64")).cuda()
@@ -810,7 +891,7 @@ def profile_case(case: str) -> int:
         for _ in range(3):
             plan.run(ws)
     elif case == "gemm":
-        w = wl.WORKLOADS[DEFAULT_WORKLOAD]
+        w = wl.WORKLOADS[GEMM_WORKLOAD]
         A = torch.from_numpy(wl.workload_input(w)).cuda()
         for _ in range(2):
             cov.estimate(A, w.P, w.Q, algo="gemm_tf32x3")
@@ -845,14 +926,15 @@ def main():
     ap.add_argument("--knobs", default=None,
                     help="G,TRB,L,K: use these knobs (lag group, rows per task, re-seed interval, "
                          "kernels 1|4) instead of autotuning")
-    ap.add_argument("--profile-case", choices=("batched", "gemm", "adjoint", "apertures"), default=None,
+    ap.add_argument("--profile-case", choices=("sar", "cn", "batched", "gemm", "adjoint", "apertures"),
+                    default=None,
                     help="run a few launches of one secondary kernel on a small case (for ncu) "
                          "and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.profile_case:
-        return profile_case(args.profile_case)
+        return profile_case(args.profile_case, args.knobs)
     rank, world, local = dist_setup()
     if args.impl == "reference":
         return bench_reference(args, rank, world)

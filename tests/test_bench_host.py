@@ -28,7 +28,10 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference"
     assert d["unit"] == "distinct products/s" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
-    assert d["config"]["workload"] == "cn_1024x1024_w16_f32"
+    assert d["config"]["workload"] == "sar_2048x512_w32_f32"
+    # every timed step ran: the steps' time fits inside the run's own wall clock
+    assert d["ms_per_step"] * d["steps"] <= d["wall_s_incl_warmup"] * 1e3
+    assert d["full_job_ms_extrapolated"] >= d["ms_per_step"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
@@ -58,3 +61,20 @@ def test_cpu_baseline_leg_reports_all_cores_and_one_core():
     if out["cores"] > 1:
         st = out["single_thread"]
         assert st["cores"] == 1 and st["value"] > 0 and st["unit"] == out["unit"]
+
+
+def test_cpu_baseline_leg_full_r_error_against_the_oracle():
+    import bench
+    import oracle
+    from oracle import combinations as cb
+    N, M, P, Q = 30, 28, 5, 4
+    A = wl.complex_normal((N, M), 11)
+    K = (N - P + 1) * (M - Q + 1)
+    R = oracle.cov_window(A, P, Q)
+    out = bench.cpu_baseline_leg(A, P, Q, cb.um_enumerated(N, M, P, Q), K, 0.1,
+                                 R_gpu_full=R.astype(np.complex64))
+    e = out["gpu_err_vs_oracle_full_R"]
+    assert e["elements"] == (P * Q) ** 2
+    assert 0 < e["rel_fro"] < 1e-7  # only the complex64 rounding of R
+    out = bench.cpu_baseline_leg(A, P, Q, cb.um_enumerated(N, M, P, Q), K, 0.1, R_gpu_full=2 * R)
+    assert abs(out["gpu_err_vs_oracle_full_R"]["rel_fro"] - 1.0) < 1e-12
