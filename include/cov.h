@@ -255,7 +255,12 @@ cov_status cov_set_stage_events(void *const *events, int n_events);
  *                   barriers (COV_C64 only), 4 = four kernels chained by
  *                   programmatic dependent launch (the only form for
  *                   COV_C128), 0 = the default (COV_C64: 1 while
- *                   |UC| * 2(P-1) <= 32768, else 4).
+ *                   |UC| * 2(P-1) <= 32768, else 4);
+ *   tile_cols       columns of A per shared-memory tile of the product
+ *                   kernel: 32 or 64 (a narrower tile holds more rows, so
+ *                   rows_per_task can be larger), 0 = the default (32 where
+ *                   a 64-column tile would hold fewer than 96 rows besides
+ *                   its halo, else 64).
  * A process-wide host cache maps (dtype, N, M, P, Q, SM count of the current
  * device) to knobs; planning (cov_workspace_size, cov_estimate_ex,
  * cov_estimate, cov_estimate_noalloc) uses the cached knobs for that key, else
@@ -268,6 +273,7 @@ typedef struct {
   int32_t rows_per_task;
   int32_t reseed_interval;
   int32_t kernels;
+  int32_t tile_cols;
 } cov_tuning_t;
 
 /* Knobs planning would use for this shape now (*out); *cached (optional)
@@ -281,7 +287,8 @@ cov_status cov_tuning_set(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
                           const cov_tuning_t *t);
 void cov_tuning_clear(void);
 /* Writes the cache to a text file (one line per entry: dtype-bytes N M P Q
- * SMs and the four knobs) / merges such a file into it (*n_loaded = entries read).
+ * SMs and the five knobs; lines with the first four knobs only are read with
+ * tile_cols = 0) / merges such a file into it (*n_loaded = entries read).
  * COV_EINVAL if the file cannot be written or read or has a malformed line. */
 cov_status cov_tuning_save(const char *path);
 cov_status cov_tuning_load(const char *path, int *n_loaded);
@@ -292,8 +299,8 @@ cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, in
                                        size_t *bytes);
 /* Times COV_RECURRENCE candidates on the caller's data with CUDA events on
  * `stream` (one warm-up and `reps` timed calls each, 1 <= reps <= 1000):
- * first lag_group x rows_per_task, then reseed_interval at the best of
- * those, then (COV_C64) one kernel against four; stores the fastest in the cache and returns it in *best (optional)
+ * first lag_group x tile_cols x rows_per_task, then reseed_interval at the
+ * best of those, then (COV_C64) one kernel against four; stores the fastest in the cache and returns it in *best (optional)
  * with its mean milliseconds per call in *best_ms (optional). Overwrites R
  * (with the correct mean-normalised estimate) and the workspace; synchronises
  * `stream`; not capturable. A candidate whose device status word reports a

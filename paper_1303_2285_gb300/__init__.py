@@ -49,9 +49,11 @@ class PlanInfo(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     """Knobs of the combination path: lags per group, rows per product task,
-    walk re-seed interval, kernels per call (1 fused or 4) (cov_tuning_t)."""
+    walk re-seed interval, kernels per call (1 fused or 4), columns per
+    shared-memory tile (32 or 64) (cov_tuning_t)."""
     _fields_ = [("lag_group", ctypes.c_int32), ("rows_per_task", ctypes.c_int32),
-                ("reseed_interval", ctypes.c_int32), ("kernels", ctypes.c_int32)]
+                ("reseed_interval", ctypes.c_int32), ("kernels", ctypes.c_int32),
+                ("tile_cols", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -295,7 +295,8 @@ cov_status cov_estimate_shard(const void *A, cov_dtype dtype, int64_t N, int64_t
 
 // autotune candidates
 static const int kTuneG[3] = {4, 8, 16};
-static const int kTuneTRB[7] = {16, 24, 32, 48, 64, 96, 128};
+static const int kTuneTRB[9] = {16, 24, 32, 48, 64, 96, 128, 160, 192};
+static const int kTuneTC[2] = {64, 32};
 static const int kTuneL[5] = {2, 4, 8, 16, 32};
 
 cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
@@ -309,11 +310,12 @@ cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, in
   plan_recurrence(N, M, M, P, Q, elem, sms, p, ws, nullptr);
   size_t mx = ws.total;
   for (int gi = 0; gi < 3; ++gi)
-    for (int ti = 0; ti < 7; ++ti) {
-      const Tuning c = {kTuneG[gi], kTuneTRB[ti], 8, 0};
-      plan_recurrence(N, M, M, P, Q, elem, sms, p, ws, &c);
-      if (ws.total > mx) mx = ws.total;
-    }
+    for (int ti = 0; ti < 9; ++ti)
+      for (int ci = 0; ci < 2; ++ci) {
+        const Tuning c = {kTuneG[gi], kTuneTRB[ti], 8, 0, kTuneTC[ci]};
+        plan_recurrence(N, M, M, P, Q, elem, sms, p, ws, &c);
+        if (ws.total > mx) mx = ws.total;
+      }
   *bytes = mx;
   return COV_OK;
 }
@@ -321,7 +323,8 @@ cov_status cov_autotune_workspace_size(cov_dtype dtype, int64_t N, int64_t M, in
 static bool tuning_valid(const cov_tuning_t &t, int elem) {
   const bool g_ok = t.lag_group == 4 || t.lag_group == 8 || (t.lag_group == 16 && elem == 8);
   const bool k_ok = t.kernels == 0 || t.kernels == 4 || (t.kernels == 1 && elem == 8);
-  return g_ok && k_ok && t.rows_per_task >= 8 && t.rows_per_task <= 256 &&
+  const bool c_ok = t.tile_cols == 0 || t.tile_cols == 32 || t.tile_cols == 64;
+  return g_ok && k_ok && c_ok && t.rows_per_task >= 8 && t.rows_per_task <= 256 &&
          t.rows_per_task % 8 == 0 && t.reseed_interval >= 1 && t.reseed_interval <= kMaxPQ;
 }
 
@@ -340,6 +343,7 @@ cov_status cov_tuning_get(cov_dtype dtype, int64_t N, int64_t M, int P, int Q, c
   out->rows_per_task = p.TRB;
   out->reseed_interval = p.L;
   out->kernels = p.fused ? 1 : 4;
+  out->tile_cols = p.TC;
   return COV_OK;
 }
 
@@ -350,7 +354,8 @@ cov_status cov_tuning_set(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
   const int elem = dtype == COV_C128 ? 16 : 8;
   if (t && !tuning_valid(*t, elem)) return COV_EINVAL;
   if (t) {
-    const Tuning k = {t->lag_group, t->rows_per_task, t->reseed_interval, t->kernels};
+    const Tuning k = {t->lag_group, t->rows_per_task, t->reseed_interval, t->kernels,
+                      t->tile_cols};
     store_tuning(elem, N, M, P, Q, device_sms(), &k);
   } else {
     store_tuning(elem, N, M, P, Q, device_sms(), nullptr);
@@ -400,9 +405,10 @@ cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
     WsLayout ws;
     plan_recurrence(N, M, lda, P, Q, elem, sms, p, ws, &cand);
     if (ws.total > ws_bytes) return -1.f;
-    const Tuning eff = {p.G, p.TRB, p.L, p.fused ? 1 : 4};
+    const Tuning eff = {p.G, p.TRB, p.L, p.fused ? 1 : 4, p.TC};
     for (const Tuning &k : seen)
-      if (k.G == eff.G && k.TRB == eff.TRB && k.L == eff.L && k.K == eff.K) return -1.f;
+      if (k.G == eff.G && k.TRB == eff.TRB && k.L == eff.L && k.K == eff.K && k.TC == eff.TC)
+        return -1.f;
     seen.push_back(eff);
     cov_status st = run_recurrence(A, elem, N, M, lda, P, Q, R, COV_MEAN, workspace, ws_bytes,
                                    sms, s, &eff, nullptr);
@@ -424,23 +430,24 @@ cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
   RecParams p0;
   WsLayout ws0;
   plan_recurrence(N, M, lda, P, Q, elem, sms, p0, ws0, nullptr);
-  Tuning bestt = {0, 0, 0, 0};
+  Tuning bestt = {0, 0, 0, 0, 0};
   float bestv = -1.f;
-  // stage 1: lags per group and rows per task (the product kernel)
+  // stage 1: lags per group, rows per task and tile width (the product kernel)
   for (int gi = 0; gi < 3 && err == COV_OK; ++gi) {
     if (kTuneG[gi] == 16 && elem == 16) continue;
-    for (int ti = 0; ti < 7 && err == COV_OK; ++ti) {
-      const Tuning c = {kTuneG[gi], kTuneTRB[ti], p0.L, 0};
-      const float v = time_one(c);
-      if (v > 0.f && (bestv < 0.f || v < bestv)) {
-        bestv = v;
-        bestt = seen.back();
+    for (int ci = 0; ci < 2 && err == COV_OK; ++ci)
+      for (int ti = 0; ti < 9 && err == COV_OK; ++ti) {
+        const Tuning c = {kTuneG[gi], kTuneTRB[ti], p0.L, 0, kTuneTC[ci]};
+        const float v = time_one(c);
+        if (v > 0.f && (bestv < 0.f || v < bestv)) {
+          bestv = v;
+          bestt = seen.back();
+        }
       }
-    }
   }
   // stage 2: the walk's re-seed interval at the best stage-1 knobs
   for (int li = 0; li < 5 && err == COV_OK && bestv > 0.f; ++li) {
-    const Tuning c = {bestt.G, bestt.TRB, kTuneL[li], bestt.K};
+    const Tuning c = {bestt.G, bestt.TRB, kTuneL[li], bestt.K, bestt.TC};
     const float v = time_one(c);
     if (v > 0.f && v < bestv) {
       bestv = v;
@@ -449,7 +456,7 @@ cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
   }
   // stage 3: the other kernel form (FP32 only)
   if (err == COV_OK && bestv > 0.f && elem == 8) {
-    const Tuning c = {bestt.G, bestt.TRB, bestt.L, bestt.K == 1 ? 4 : 1};
+    const Tuning c = {bestt.G, bestt.TRB, bestt.L, bestt.K == 1 ? 4 : 1, bestt.TC};
     const float v = time_one(c);
     if (v > 0.f && v < bestv) {
       bestv = v;
@@ -466,6 +473,7 @@ cov_status cov_autotune(const void *A, cov_dtype dtype, int64_t N, int64_t M, in
     best->rows_per_task = bestt.TRB;
     best->reseed_interval = bestt.L;
     best->kernels = bestt.K;
+    best->tile_cols = bestt.TC;
   }
   if (best_ms) *best_ms = bestv;
   return COV_OK;

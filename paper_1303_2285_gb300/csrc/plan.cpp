@@ -53,7 +53,7 @@ int choose_group(int P, int Q, int elem) {
 
 void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int elem, int sms,
                      RecParams &p, WsLayout &ws, const Tuning *tune) {
-  Tuning t = {0, 0, 0, 0};
+  Tuning t = {0, 0, 0, 0, 0};
   if (tune) t = *tune;
   else lookup_tuning(elem, N, M, P, Q, sms, t);
   memset(&p, 0, sizeof(p));
@@ -72,25 +72,39 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.d_lo = group_lag_lo(P, Q);
   p.d_hi = group_lag_hi(P, Q, p.G);
   const int span = p.d_hi - p.d_lo;
-  // Tiles: 64 columns, smem pitch 80 (Q <= 17) or 96 (Q <= 33) complex
-  // elements; two buffers of STR rows each within the 227 KB of a CTA.
-  p.TC = 64;
-  p.CBT = 2;
-  p.PITCH = Q <= 17 ? 80 : 96;
+  // Tiles: TC = 64 or 32 columns (each a 32-column block a warp task
+  // covers), smem pitch TC + 16 (Q <= 17) or TC + 32 (Q <= 33) complex
+  // elements (the partner columns of every column lag); two buffers of STR
+  // rows each within the 227 KB of a CTA. A narrower tile holds more rows,
+  // so a task's row block (and each partial sum) covers more rows: the
+  // default is 32 columns where a 64-column tile would hold fewer than 96
+  // rows besides its halo.
+  const long long buf_bytes = (232448LL - 1024) / 2;
+  auto rows_for = [&](int tc) {
+    const int pitch = tc + (Q <= 17 ? 16 : 32);
+    long long rm = buf_bytes / ((long long)pitch * elem);
+    if (rm > 256) rm = 256;  // TMA box height
+    return rm - span;
+  };
+  p.TC = (t.TC == 32 || t.TC == 64) ? t.TC : (rows_for(64) < 96 ? 32 : 64);
+  p.CBT = p.TC / 32;
+  p.PITCH = p.TC + (Q <= 17 ? 16 : 32);
   p.n_cb = (int)((M + 31) / 32);
   p.n_ct = (int)((M + p.TC - 1) / p.TC);
-  const long long buf_bytes = (232448LL - 1024) / 2;
-  long long rows_max = buf_bytes / ((long long)p.PITCH * elem);
-  if (rows_max > 256) rows_max = 256;  // TMA box height
-  long long tr_max = rows_max - span;
+  long long tr_max = rows_for(p.TC);
   if (tr_max < 8) tr_max = 8;
-  int TRB = tr_max >= 48 ? 48 : (int)(tr_max / 8) * 8;
-  if (elem == 16 && sms > 0) {
-    // FP64: one SM's FP64 pipe is slow, so shorten the row blocks until the
-    // tasks (about row blocks x column blocks x lag groups) cover twice the
-    // SMs
+  // FP32: the longest row block up to 128 rows (fewer partial sums and task
+  // epilogues), shortened while the tasks (about row blocks x column blocks x
+  // lag groups) number fewer than 8 per SM; FP64: 48 rows, shortened until
+  // the tasks cover twice the SMs (one SM's FP64 pipe is slow, so every SM
+  // needs a task)
+  const long long trb_cap = elem == 8 ? 128 : 48;
+  int TRB = (int)((tr_max < trb_cap ? tr_max : trb_cap) / 8) * 8;
+  if (sms > 0) {
     const long long per_rb = (long long)((M + 31) / 32) * p.ngroups;
-    while (TRB > 8 && (long long)((p.n_inner + TRB - 1) / TRB) * per_rb < 2LL * sms) TRB -= 8;
+    const long long want = elem == 8 ? 8LL * sms : 2LL * sms;
+    const int floor_rows = elem == 8 ? 16 : 8;
+    while (TRB > floor_rows && (long long)((p.n_inner + TRB - 1) / TRB) * per_rb < want) TRB -= 8;
   }
   if (t.TRB >= 8 && t.TRB % 8 == 0 && t.TRB <= tr_max) TRB = t.TRB;
   if (TRB < 8) TRB = 8;
@@ -270,10 +284,10 @@ int save_tuning(const char *path) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   FILE *f = fopen(path, "w");
   if (!f) return -1;
-  fprintf(f, "# elem N M P Q sms G TRB L K\n");
+  fprintf(f, "# elem N M P Q sms G TRB L K TC\n");
   for (const TuneEntry &e : g_tune)
-    fprintf(f, "%d %lld %lld %d %d %d %d %d %d %d\n", e.elem, e.N, e.M, e.P, e.Q, e.sms, e.t.G,
-            e.t.TRB, e.t.L, e.t.K);
+    fprintf(f, "%d %lld %lld %d %d %d %d %d %d %d %d\n", e.elem, e.N, e.M, e.P, e.Q, e.sms, e.t.G,
+            e.t.TRB, e.t.L, e.t.K, e.t.TC);
   return fclose(f) == 0 ? 0 : -1;
 }
 
@@ -284,11 +298,12 @@ int load_tuning(const char *path) {
   int n = 0;
   while (fgets(line, sizeof(line), f)) {
     if (line[0] == '#') continue;
-    int elem, P, Q, sms, G, TRB, L, K;
+    int elem, P, Q, sms, G, TRB, L, K, TC = 0;
     long long N, M;
-    if (sscanf(line, "%d %lld %lld %d %d %d %d %d %d %d", &elem, &N, &M, &P, &Q, &sms, &G, &TRB, &L,
-               &K) == 10) {
-      const Tuning t = {G, TRB, L, K};
+    const int got = sscanf(line, "%d %lld %lld %d %d %d %d %d %d %d %d", &elem, &N, &M, &P, &Q,
+                           &sms, &G, &TRB, &L, &K, &TC);
+    if (got == 10 || got == 11) {  // files written before the TC knob have 10 fields
+      const Tuning t = {G, TRB, L, K, got == 11 ? TC : 0};
       store_tuning(elem, N, M, P, Q, sms, &t);
       ++n;
     } else {

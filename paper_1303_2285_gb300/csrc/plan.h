@@ -29,9 +29,10 @@ int choose_group(int P, int Q, int elem);
 
 // Tuned knobs of the combination path (0 = the plan's default): lags per
 // group G, rows per product task TRB, walk re-seed interval L, kernels per
-// call K (1 = the fused cooperative kernel, FP32 only; 4 = four kernels).
+// call K (1 = the fused cooperative kernel, FP32 only; 4 = four kernels),
+// columns per shared-memory tile TC (32 or 64).
 struct Tuning {
-  int G, TRB, L, K;
+  int G, TRB, L, K, TC;
 };
 
 // Fills every field of p that depends on the shape only (not the pointers);

@@ -165,21 +165,39 @@ static cudaError_t launch_fused_t(const RecParams &p, const CUtensorMap &tmap, i
   return cudaLaunchKernelEx(&cfg, kern, p, tmap);
 }
 
+// The pitch follows the tile width and Q (TC + 16 for Q <= 17, TC + 32
+// above), QMAX the column-lag register count of the fringe tasks (>= Q).
+template <int G, int PITCH>
+static cudaError_t launch_fused_q(const RecParams &p, const CUtensorMap &tmap, int num_sms,
+                                  cudaStream_t s) {
+  if constexpr (PITCH == 64 || PITCH == 96) {
+    return launch_fused_t<G, PITCH, 32>(p, tmap, num_sms, s);
+  } else {
+    switch (p.QMAXF) {
+      case 4:
+      case 8: return launch_fused_t<G, PITCH, 8>(p, tmap, num_sms, s);
+      case 16: return launch_fused_t<G, PITCH, 16>(p, tmap, num_sms, s);
+      case 32: return launch_fused_t<G, PITCH, 32>(p, tmap, num_sms, s);
+    }
+    return cudaErrorNotSupported;
+  }
+}
+
 template <int G>
 static cudaError_t launch_fused_g(const RecParams &p, const CUtensorMap &tmap, int num_sms,
                                   cudaStream_t s) {
-  if (p.PITCH == 96) return launch_fused_t<G, 96, 32>(p, tmap, num_sms, s);
-  switch (p.QMAXF) {
-    case 4:
-    case 8: return launch_fused_t<G, 80, 8>(p, tmap, num_sms, s);
-    case 16: return launch_fused_t<G, 80, 16>(p, tmap, num_sms, s);
-    case 32: return launch_fused_t<G, 80, 32>(p, tmap, num_sms, s);
+  switch (p.PITCH) {
+    case 48: return launch_fused_q<G, 48>(p, tmap, num_sms, s);
+    case 64: return launch_fused_q<G, 64>(p, tmap, num_sms, s);
+    case 80: return launch_fused_q<G, 80>(p, tmap, num_sms, s);
+    case 96: return launch_fused_q<G, 96>(p, tmap, num_sms, s);
   }
   return cudaErrorNotSupported;
 }
 
 bool fused_supported(const RecParams &p, bool fp64) {
-  return !fp64 && (p.G == 4 || p.G == 8 || p.G == 16) && (p.PITCH == 80 || p.PITCH == 96);
+  return !fp64 && (p.G == 4 || p.G == 8 || p.G == 16) &&
+         (p.PITCH == 48 || p.PITCH == 64 || p.PITCH == 80 || p.PITCH == 96);
 }
 
 cudaError_t launch_fused(const RecParams &p, const CUtensorMap &tmap, int num_sms, cudaStream_t s) {

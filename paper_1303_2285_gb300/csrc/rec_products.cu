@@ -48,8 +48,12 @@ static cudaError_t launch_products_p(const RecParams &p, const CUtensorMap &tmap
 template <typename T, int G>
 static cudaError_t launch_products(const RecParams &p, const CUtensorMap &tmap, int num_sms,
                                    cudaStream_t s) {
-  if (p.PITCH == 80) return launch_products_p<T, G, 80>(p, tmap, num_sms, s);
-  if (p.PITCH == 96) return launch_products_p<T, G, 96>(p, tmap, num_sms, s);
+  switch (p.PITCH) {
+    case 48: return launch_products_p<T, G, 48>(p, tmap, num_sms, s);
+    case 64: return launch_products_p<T, G, 64>(p, tmap, num_sms, s);
+    case 80: return launch_products_p<T, G, 80>(p, tmap, num_sms, s);
+    case 96: return launch_products_p<T, G, 96>(p, tmap, num_sms, s);
+  }
   return cudaErrorInvalidValue;
 }
 

@@ -188,6 +188,259 @@ __device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same reductions with one CTA (kRedThreads threads) per combination D,
+// for the stand-alone reduction kernel. The partials of D are read by many
+// threads at once (every load of a thread issued before its sums start), so a
+// combination costs about one memory latency instead of one per round of a
+// single warp's loop; the sums are then finished in shared memory:
+//  - core: each thread a compensated sum over a strided share of the core
+//    partials, merged over the warp and then over the CTA;
+//  - CS[fc] = sum over the row blocks of the fringe-column partials: S
+//    threads per fringe column, each a compensated sum over every S-th row
+//    block, merged per column;
+//  - S_in[fr] = sum over the column chunks of the fringe-row partials, S2
+//    threads per fringe row, merged per row;
+//  - the fringe-row x fringe-column products (each formed once) into a table;
+//  - CV[D][j] (warp 0: suffix / prefix scans over the fringe columns as in
+//    reduce_combo_warp) and RV[D][j][fr] (one thread per fringe row: a suffix
+//    pass over the left products, then a prefix over the right ones).
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 256;
+
+template <typename T> struct RedSmem {
+  // offsets in units of T of the regions of reduce_combo_cta's shared memory
+  int prod, cs_part, sin_part, cs, sin, core;
+  int total;
+  __host__ __device__ RedSmem(int NFR, int NFC, int S, int S2) {
+    prod = 0;                                 // [NFR][NFC | 1] complex
+    cs_part = prod + 2 * NFR * (NFC | 1);     // [S][NFC] x (re s, re c, im s, im c)
+    sin_part = cs_part + 4 * S * NFC;         // [S2][NFR] complex
+    cs = sin_part + 2 * S2 * NFR;             // [NFC] complex
+    sin = cs + 2 * NFC;                       // [NFR] complex
+    core = sin + 2 * NFR;                     // [warps] x (re s, re c, im s, im c)
+    total = core + 4 * (kRedThreads / 32);
+  }
+};
+
+// Row stride of the product table: odd in complex elements, so that the
+// threads of the scan (one fringe row each) read different banks.
+__host__ __device__ inline int red_prod_stride(int NFC) { return NFC | 1; }
+
+__host__ __device__ inline int red_cs_slices(int NFC, int n_rb) {
+  int S = NFC > 0 ? kRedThreads / NFC : 1;
+  if (S > n_rb) S = n_rb;
+  return S < 1 ? 1 : S;
+}
+__host__ __device__ inline int red_sin_slices(int NFR, int NCH) {
+  int S = NFR > 0 ? kRedThreads / NFR : 1;
+  if (S > NCH) S = NCH;
+  return S < 1 ? 1 : S;
+}
+template <typename T> __host__ __device__ inline size_t reduce_cta_smem_bytes(const RecParams &p) {
+  const RedSmem<T> L(p.NFR, p.NFC, red_cs_slices(p.NFC, p.n_rb), red_sin_slices(p.NFR, p.NCH));
+  return (size_t)L.total * sizeof(T);
+}
+
+template <typename T>
+__device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *sm) {
+  using C2 = typename C2t<T>::type;
+  const int P = p.P, Q = p.Q, NFR = p.NFR, NFC = p.NFC, NCH = p.NCH, n_rb = p.n_rb;
+  const int W = p.M - p.Q + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int S = red_cs_slices(NFC, n_rb), S2 = red_sin_slices(NFR, NCH);
+  const RedSmem<T> L(NFR, NFC, S, S2);
+  int dr, dc;
+  combo_of(P, D, dr, dc);
+  const int J = Q - dc;
+
+  // ---- 1. loads and per-thread sums --------------------------------------
+  // core partials [D][rb][cb]
+  Neu<T> cr, ci;
+  {
+    const long long nparts = (long long)n_rb * p.n_cb;
+    const C2 *cp = (const C2 *)p.core_part + (long long)D * nparts;
+    for (long long k0 = tid; k0 < nparts; k0 += 8LL * kRedThreads) {
+      C2 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        x[u] = (k0 + (long long)u * kRedThreads < nparts) ? cp[k0 + (long long)u * kRedThreads]
+                                                           : czero<C2>();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        cr.add(x[u].x);
+        ci.add(x[u].y);
+      }
+    }
+  }
+  // fringe-column partials [D][rb][fc]: thread (s, fc) sums rb = s, s+S, ...
+  if (tid < S * NFC) {
+    const int fc = tid % NFC, s0 = tid / NFC;
+    const C2 *cs = (const C2 *)p.colsum_part + (long long)D * n_rb * NFC + fc;
+    Neu<T> a, b;
+    for (int rb0 = s0; rb0 < n_rb; rb0 += 8 * S) {
+      C2 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        x[u] = rb0 + u * S < n_rb ? cs[(long long)(rb0 + u * S) * NFC] : czero<C2>();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a.add(x[u].x);
+        b.add(x[u].y);
+      }
+    }
+    T *o = sm + L.cs_part + 4 * (s0 * NFC + fc);
+    o[0] = a.s;
+    o[1] = a.c;
+    o[2] = b.s;
+    o[3] = b.c;
+  }
+  // fringe-row partials [D][chunk][fr]: thread (s, fr) sums chunks s, s+S2, ...
+  if (tid < S2 * NFR) {
+    const int fr = tid % NFR, s0 = tid / NFR;
+    const C2 *sp = (const C2 *)p.sin_part + (long long)D * NCH * NFR + fr;
+    T sr[2] = {T(0), T(0)}, si[2] = {T(0), T(0)};
+    for (int c0 = s0; c0 < NCH; c0 += 8 * S2) {
+      C2 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        x[u] = c0 + u * S2 < NCH ? sp[(long long)(c0 + u * S2) * NFR] : czero<C2>();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        sr[u & 1] += x[u].x;
+        si[u & 1] += x[u].y;
+      }
+    }
+    C2 o;
+    o.x = sr[0] + sr[1];
+    o.y = si[0] + si[1];
+    ((C2 *)(sm + L.sin_part))[s0 * NFR + fr] = o;
+  }
+  // the fringe-row x fringe-column products, each formed once: warp w takes
+  // the fringe rows w, w + 8, ...; lane k the left column k and the right
+  // column W + k (the lanes' loads of a row are contiguous)
+  {
+    const C2 *A = (const C2 *)p.A;
+    C2 *prod = (C2 *)(sm + L.prod);
+    const int PS = red_prod_stride(NFC);
+    if (lane < Q - 1) {
+#pragma unroll 2
+      for (int fr = warp; fr < NFR; fr += kRedThreads / 32) {
+        const int n = fr < P - 1 ? fr : (p.N - P + 1) + (fr - (P - 1));
+        const bool rowok = n + dr >= 0 && n + dr < p.N;
+        const C2 *An = A + (long long)n * p.lda;
+        const C2 *Ab = A + (long long)(n + dr) * p.lda + dc;
+        const bool rok = rowok && W + lane + dc < p.M;
+        C2 a0 = czero<C2>(), b0 = czero<C2>(), a1 = czero<C2>(), b1 = czero<C2>();
+        if (rowok) {
+          a0 = __ldg(An + lane);
+          b0 = __ldg(Ab + lane);
+        }
+        if (rok) {
+          a1 = __ldg(An + W + lane);
+          b1 = __ldg(Ab + W + lane);
+        }
+        C2 vl = czero<C2>(), vr = czero<C2>();
+        cmac_conj(vl, a0, b0);
+        cmac_conj(vr, a1, b1);
+        prod[fr * PS + lane] = vl;
+        prod[fr * PS + Q - 1 + lane] = vr;
+      }
+    }
+  }
+  // core: merge over the warp, one state per warp into shared memory
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const T s1 = __shfl_xor_sync(0xffffffffu, cr.s, o), c1 = __shfl_xor_sync(0xffffffffu, cr.c, o);
+    const T s2 = __shfl_xor_sync(0xffffffffu, ci.s, o), c2 = __shfl_xor_sync(0xffffffffu, ci.c, o);
+    cr.merge(s1, c1);
+    ci.merge(s2, c2);
+  }
+  if (lane == 0) {
+    T *o = sm + L.core + 4 * warp;
+    o[0] = cr.s;
+    o[1] = cr.c;
+    o[2] = ci.s;
+    o[3] = ci.c;
+  }
+  __syncthreads();
+
+  // ---- 2. merge the slices ------------------------------------------------
+  if (tid < NFC) {
+    Neu<T> a, b;
+    for (int s0 = 0; s0 < S; ++s0) {
+      const T *o = sm + L.cs_part + 4 * (s0 * NFC + tid);
+      a.merge(o[0], o[1]);
+      b.merge(o[2], o[3]);
+    }
+    C2 v;
+    v.x = a.value();
+    v.y = b.value();
+    ((C2 *)(sm + L.cs))[tid] = v;
+  } else if (tid >= 128 && tid - 128 < NFR) {
+    const int fr = tid - 128;
+    const C2 *sp = (const C2 *)(sm + L.sin_part);
+    C2 v = sp[fr];
+    for (int s0 = 1; s0 < S2; ++s0) {
+      v.x += sp[s0 * NFR + fr].x;
+      v.y += sp[s0 * NFR + fr].y;
+    }
+    ((C2 *)(sm + L.sin))[fr] = v;
+  }
+  __syncthreads();
+
+  // ---- 3. CV (warp 0) and RV (one thread per fringe row) -----------------
+  if (warp == 0) {
+    Neu<T> vr, vi;
+    for (int w = 0; w < kRedThreads / 32; ++w) {
+      const T *o = sm + L.core + 4 * w;
+      vr.merge(o[0], o[1]);
+      vi.merge(o[2], o[3]);
+    }
+    const C2 *CS = (const C2 *)(sm + L.cs);
+    const T lr = lane < Q - 1 ? CS[lane].x : T(0), li = lane < Q - 1 ? CS[lane].y : T(0);
+    const T rr = lane < Q - 1 ? CS[Q - 1 + lane].x : T(0), ri = lane < Q - 1 ? CS[Q - 1 + lane].y : T(0);
+    const T lsr = scan_suffix(lr, lane), lsi = scan_suffix(li, lane);
+    T rpr = scan_incl(rr, lane), rpi = scan_incl(ri, lane);
+    rpr = __shfl_up_sync(0xffffffffu, rpr, 1);  // exclusive
+    rpi = __shfl_up_sync(0xffffffffu, rpi, 1);
+    if (lane == 0) rpr = rpi = T(0);
+    if (lane < J) {
+      vr.add(lane < Q - 1 ? lsr : T(0));
+      vi.add(lane < Q - 1 ? lsi : T(0));
+      vr.add(rpr);
+      vi.add(rpi);
+      C2 o;
+      o.x = vr.value();
+      o.y = vi.value();
+      ((C2 *)p.colval)[(long long)D * Q + lane] = o;
+    }
+  } else if (tid >= 32 && tid - 32 < NFR) {
+    const int fr = tid - 32;
+    C2 *row = (C2 *)(sm + L.prod) + fr * red_prod_stride(NFC);
+    const C2 s_in = ((const C2 *)(sm + L.sin))[fr];
+    // suffix over the left fringe-column products, in place
+    C2 acc = czero<C2>();
+    for (int k = Q - 2; k >= 0; --k) {
+      acc.x += row[k].x;
+      acc.y += row[k].y;
+      row[k] = acc;
+    }
+    C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR + fr;
+    C2 pre = czero<C2>();
+    for (int j = 0; j < J; ++j) {
+      C2 o;
+      o.x = s_in.x + (j < Q - 1 ? row[j].x : T(0)) + pre.x;
+      o.y = s_in.y + (j < Q - 1 ? row[j].y : T(0)) + pre.y;
+      rv[(long long)j * NFR] = o;
+      if (j < Q - 1) {
+        pre.x += row[Q - 1 + j].x;
+        pre.y += row[Q - 1 + j].y;
+      }
+    }
+  }
+}
+
 // Reduction warp task w of the shard: [0, n_own) the combinations' CV, then
 // [n_own, 2 n_own) their RV.
 __host__ __device__ __forceinline__ int reduce_tasks(const RecParams &p) {

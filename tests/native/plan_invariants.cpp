@@ -41,8 +41,10 @@ static void check_plan(long long N, long long M, int P, int Q, int elem, const T
         "n_rb %d", p.n_rb);
   CHECK(p.TPT >= 1 && p.TPT <= 4 && p.TR == p.TRB * p.TPT, "TPT %d", p.TPT);
   CHECK((long long)p.n_rt * p.TPT >= p.n_rb, "n_rt %d", p.n_rt);
-  // column tiling: 64-column tiles of two 32-column blocks
-  CHECK(p.TC == 64 && p.CBT * 32 == p.TC, "TC %d", p.TC);
+  // column tiling: 64- or 32-column tiles of 32-column blocks
+  CHECK((p.TC == 64 || p.TC == 32) && p.CBT * 32 == p.TC, "TC %d", p.TC);
+  if (t && (t->TC == 32 || t->TC == 64)) CHECK(p.TC == t->TC, "TC %d not the knob's", p.TC);
+  CHECK(p.PITCH == p.TC + (Q <= 17 ? 16 : 32), "PITCH %d", p.PITCH);
   CHECK((long long)p.n_ct * p.TC >= M && (long long)p.n_cb * 32 >= M, "n_ct %d", p.n_ct);
   // the staged tile: rows r0 + d_lo .. r0 + TR - 1 + d_hi, columns c0 .. c0 + 63 + (Q - 1)
   CHECK(p.STR == p.TR + span, "STR %d", p.STR);
@@ -89,7 +91,8 @@ static void check_plan(long long N, long long M, int P, int Q, int elem, const T
 }
 
 int main() {
-  const Tuning knobs[4] = {{4, 16, 2, 4}, {8, 64, 8, 1}, {16, 128, 32, 0}, {16, 256, 1, 4}};
+  const Tuning knobs[6] = {{4, 16, 2, 4, 0},    {8, 64, 8, 1, 64},   {16, 128, 32, 0, 32},
+                           {16, 256, 1, 4, 64}, {16, 160, 4, 4, 32}, {8, 192, 16, 1, 32}};
   long long N = 0, M = 0;
   int P = 0, Q = 0, elem = 0;
   for (P = 1; P <= 32; P += (P < 8 ? 1 : 3))

@@ -15,16 +15,22 @@ pytestmark = pytest.mark.gpu
 from gpu_util import oracle_R, rel_fro, to_dev  # noqa: E402
 
 KNOBS = [
-    {"lag_group": 4, "rows_per_task": 8, "reseed_interval": 1, "kernels": 4},
-    {"lag_group": 8, "rows_per_task": 16, "reseed_interval": 2, "kernels": 4},
-    {"lag_group": 16, "rows_per_task": 24, "reseed_interval": 32, "kernels": 4},
-    {"lag_group": 4, "rows_per_task": 64, "reseed_interval": 3, "kernels": 4},
-    {"lag_group": 8, "rows_per_task": 128, "reseed_interval": 16, "kernels": 4},
-    {"lag_group": 16, "rows_per_task": 256, "reseed_interval": 5, "kernels": 4},
-    {"lag_group": 4, "rows_per_task": 8, "reseed_interval": 1, "kernels": 1},
-    {"lag_group": 8, "rows_per_task": 32, "reseed_interval": 4, "kernels": 1},
-    {"lag_group": 16, "rows_per_task": 128, "reseed_interval": 8, "kernels": 1},
-    {"lag_group": 16, "rows_per_task": 48, "reseed_interval": 32, "kernels": 1},
+    {"lag_group": 4, "rows_per_task": 8, "reseed_interval": 1, "kernels": 4, "tile_cols": 64},
+    {"lag_group": 8, "rows_per_task": 16, "reseed_interval": 2, "kernels": 4, "tile_cols": 64},
+    {"lag_group": 16, "rows_per_task": 24, "reseed_interval": 32, "kernels": 4, "tile_cols": 64},
+    {"lag_group": 4, "rows_per_task": 64, "reseed_interval": 3, "kernels": 4, "tile_cols": 64},
+    {"lag_group": 8, "rows_per_task": 128, "reseed_interval": 16, "kernels": 4, "tile_cols": 64},
+    {"lag_group": 16, "rows_per_task": 256, "reseed_interval": 5, "kernels": 4, "tile_cols": 64},
+    {"lag_group": 4, "rows_per_task": 8, "reseed_interval": 1, "kernels": 1, "tile_cols": 64},
+    {"lag_group": 8, "rows_per_task": 32, "reseed_interval": 4, "kernels": 1, "tile_cols": 64},
+    {"lag_group": 16, "rows_per_task": 128, "reseed_interval": 8, "kernels": 1, "tile_cols": 64},
+    {"lag_group": 16, "rows_per_task": 48, "reseed_interval": 32, "kernels": 1, "tile_cols": 64},
+    # 32-column tiles (taller row blocks fit)
+    {"lag_group": 4, "rows_per_task": 8, "reseed_interval": 2, "kernels": 4, "tile_cols": 32},
+    {"lag_group": 8, "rows_per_task": 192, "reseed_interval": 7, "kernels": 4, "tile_cols": 32},
+    {"lag_group": 16, "rows_per_task": 160, "reseed_interval": 16, "kernels": 4, "tile_cols": 32},
+    {"lag_group": 8, "rows_per_task": 40, "reseed_interval": 1, "kernels": 1, "tile_cols": 32},
+    {"lag_group": 16, "rows_per_task": 224, "reseed_interval": 32, "kernels": 1, "tile_cols": 32},
 ]
 
 

@@ -22,7 +22,7 @@ def test_defaults_not_cached():
 
 
 def test_set_get_remove():
-    k = {"lag_group": 4, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4}
+    k = {"lag_group": 4, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4, "tile_cols": 32}
     cov.tuning_set("c64", 300, 200, 8, 6, k)
     got, cached = cov.tuning_get("c64", 300, 200, 8, 6)
     assert cached and got == k
@@ -40,6 +40,7 @@ def test_set_get_remove():
     {"lag_group": 8, "rows_per_task": 264, "reseed_interval": 4, "kernels": 4},
     {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 0, "kernels": 4},
     {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 33, "kernels": 4},
+    {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4, "tile_cols": 48},
 ])
 def test_invalid_knobs_rejected(bad):
     with pytest.raises(cov.CovError) as e:
@@ -101,8 +102,8 @@ def test_autotune_workspace_bound():
 
 
 def test_save_load_round_trip(tmp_path):
-    a = {"lag_group": 4, "rows_per_task": 32, "reseed_interval": 2, "kernels": 1}
-    b = {"lag_group": 8, "rows_per_task": 64, "reseed_interval": 16, "kernels": 4}
+    a = {"lag_group": 4, "rows_per_task": 32, "reseed_interval": 2, "kernels": 1, "tile_cols": 64}
+    b = {"lag_group": 8, "rows_per_task": 64, "reseed_interval": 16, "kernels": 4, "tile_cols": 32}
     cov.tuning_set("c64", 512, 256, 12, 10, a)
     cov.tuning_set("c128", 100, 90, 5, 7, b)
     f = tmp_path / "tune.txt"
@@ -121,3 +122,31 @@ def test_load_errors(tmp_path):
     bad.write_text("# header\n8 100 100 4 4\n")
     with pytest.raises(cov.CovError):
         cov.tuning_load(str(bad))
+
+
+def test_tile_cols_knob_and_default():
+    # 2048 x 512 with a 32 x 32 window: a 64-column tile holds 87 rows besides
+    # its halo, so the default tile is 32 columns (and 128-row tasks fit)
+    knobs, cached = cov.tuning_get("c64", 2048, 512, 32, 32)
+    assert not cached and knobs["tile_cols"] == 32 and knobs["rows_per_task"] == 128
+    # 1024 x 1024 with 16 x 16 keeps 64-column tiles
+    assert cov.tuning_get("c64", 1024, 1024, 16, 16)[0]["tile_cols"] == 64
+    cov.tuning_set("c64", 2048, 512, 32, 32, {"lag_group": 16, "rows_per_task": 64,
+                                              "reseed_interval": 8, "kernels": 4, "tile_cols": 64})
+    got = cov.tuning_get("c64", 2048, 512, 32, 32)[0]
+    assert got["tile_cols"] == 64 and got["rows_per_task"] == 64
+
+
+def test_load_reads_four_knob_lines(tmp_path):
+    # a file written before the tile_cols knob: the same line without it
+    cov.tuning_set("c64", 512, 256, 12, 10, {"lag_group": 4, "rows_per_task": 32,
+                                             "reseed_interval": 2, "kernels": 1, "tile_cols": 64})
+    f = tmp_path / "old.txt"
+    cov.tuning_save(str(f))
+    cov.tuning_clear()
+    lines = [ln for ln in f.read_text().splitlines() if not ln.startswith("#")]
+    assert len(lines) == 1
+    f.write_text("# elem N M P Q sms G TRB L K\n" + " ".join(lines[0].split()[:10]) + "\n")
+    assert cov.tuning_load(str(f)) == 1
+    got, cached = cov.tuning_get("c64", 512, 256, 12, 10)
+    assert cached and got["lag_group"] == 4 and got["rows_per_task"] == 32
