@@ -195,7 +195,7 @@ __device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int 
 // combination costs about one memory latency instead of one per round of a
 // single warp's loop; the sums are then finished in shared memory:
 //  - core: each thread a compensated sum over a strided share of the core
-//    partials, merged over the warp and then over the CTA;
+//    partials, the 256 states merged by one warp;
 //  - CS[fc] = sum over the row blocks of the fringe-column partials: S
 //    threads per fringe column, each a compensated sum over every S-th row
 //    block, merged per column;
@@ -203,14 +203,16 @@ __device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int 
 //    threads per fringe row, merged per row;
 //  - the fringe-row x fringe-column products (each formed once) into a table;
 //  - CV[D][j] (warp 0: suffix / prefix scans over the fringe columns as in
-//    reduce_combo_warp) and RV[D][j][fr] (one thread per fringe row: a suffix
-//    pass over the left products, then a prefix over the right ones).
+//    reduce_combo_warp) and RV[D][j][fr] (four threads per fringe row, each a
+//    segment of the suffix over the left products and of the prefix over the
+//    right ones, carried across the segments through shared memory).
 // ---------------------------------------------------------------------------
 constexpr int kRedThreads = 256;
+constexpr int kRedSeg = 4;  // segments of the fringe-column scans per fringe row
 
 template <typename T> struct RedSmem {
   // offsets in units of T of the regions of reduce_combo_cta's shared memory
-  int prod, cs_part, sin_part, cs, sin, core;
+  int prod, cs_part, sin_part, cs, sin, core, tot, core_tot;
   int total;
   __host__ __device__ RedSmem(int NFR, int NFC, int S, int S2) {
     prod = 0;                                 // [NFR][NFC | 1] complex
@@ -218,13 +220,15 @@ template <typename T> struct RedSmem {
     sin_part = cs_part + 4 * S * NFC;         // [S2][NFR] complex
     cs = sin_part + 2 * S2 * NFR;             // [NFC] complex
     sin = cs + 2 * NFC;                       // [NFR] complex
-    core = sin + 2 * NFR;                     // [warps] x (re s, re c, im s, im c)
-    total = core + 4 * (kRedThreads / 32);
+    core = sin + 2 * NFR;                     // [threads] x (re s, re c, im s, im c)
+    tot = core + 4 * kRedThreads;             // [kRedSeg][NFR] x (left, right) complex
+    core_tot = tot + 4 * kRedSeg * NFR;       // (re s, re c, im s, im c)
+    total = core_tot + 4;
   }
 };
 
 // Row stride of the product table: odd in complex elements, so that the
-// threads of the scan (one fringe row each) read different banks.
+// threads that read along a row hit different banks.
 __host__ __device__ inline int red_prod_stride(int NFC) { return NFC | 1; }
 
 __host__ __device__ inline int red_cs_slices(int NFC, int n_rb) {
@@ -255,39 +259,45 @@ __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *s
   const int J = Q - dc;
 
   // ---- 1. loads and per-thread sums --------------------------------------
-  // core partials [D][rb][cb]
-  Neu<T> cr, ci;
+  // core partials [D][rb][cb]: thread tid takes tid, tid + 256, ...
   {
-    const long long nparts = (long long)n_rb * p.n_cb;
+    Neu<T> cr, ci;
+    const int nparts = n_rb * p.n_cb;
     const C2 *cp = (const C2 *)p.core_part + (long long)D * nparts;
-    for (long long k0 = tid; k0 < nparts; k0 += 8LL * kRedThreads) {
-      C2 x[8];
+    for (int k0 = tid; k0 < nparts; k0 += 4 * kRedThreads) {
+      C2 x[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        x[u] = (k0 + (long long)u * kRedThreads < nparts) ? cp[k0 + (long long)u * kRedThreads]
-                                                           : czero<C2>();
+      for (int u = 0; u < 4; ++u)
+        if (k0 + u * kRedThreads < nparts) x[u] = cp[k0 + u * kRedThreads];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        cr.add(x[u].x);
-        ci.add(x[u].y);
-      }
+      for (int u = 0; u < 4; ++u)
+        if (k0 + u * kRedThreads < nparts) {
+          cr.add(x[u].x);
+          ci.add(x[u].y);
+        }
     }
+    T *o = sm + L.core + 4 * tid;
+    o[0] = cr.s;
+    o[1] = cr.c;
+    o[2] = ci.s;
+    o[3] = ci.c;
   }
   // fringe-column partials [D][rb][fc]: thread (s, fc) sums rb = s, s+S, ...
   if (tid < S * NFC) {
     const int fc = tid % NFC, s0 = tid / NFC;
     const C2 *cs = (const C2 *)p.colsum_part + (long long)D * n_rb * NFC + fc;
     Neu<T> a, b;
-    for (int rb0 = s0; rb0 < n_rb; rb0 += 8 * S) {
-      C2 x[8];
+    for (int rb0 = s0; rb0 < n_rb; rb0 += 4 * S) {
+      C2 x[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        x[u] = rb0 + u * S < n_rb ? cs[(long long)(rb0 + u * S) * NFC] : czero<C2>();
+      for (int u = 0; u < 4; ++u)
+        if (rb0 + u * S < n_rb) x[u] = cs[(long long)(rb0 + u * S) * NFC];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        a.add(x[u].x);
-        b.add(x[u].y);
-      }
+      for (int u = 0; u < 4; ++u)
+        if (rb0 + u * S < n_rb) {
+          a.add(x[u].x);
+          b.add(x[u].y);
+        }
     }
     T *o = sm + L.cs_part + 4 * (s0 * NFC + fc);
     o[0] = a.s;
@@ -299,21 +309,22 @@ __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *s
   if (tid < S2 * NFR) {
     const int fr = tid % NFR, s0 = tid / NFR;
     const C2 *sp = (const C2 *)p.sin_part + (long long)D * NCH * NFR + fr;
-    T sr[2] = {T(0), T(0)}, si[2] = {T(0), T(0)};
-    for (int c0 = s0; c0 < NCH; c0 += 8 * S2) {
-      C2 x[8];
+    T sr = T(0), si = T(0);
+    for (int c0 = s0; c0 < NCH; c0 += 4 * S2) {
+      C2 x[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        x[u] = c0 + u * S2 < NCH ? sp[(long long)(c0 + u * S2) * NFR] : czero<C2>();
+      for (int u = 0; u < 4; ++u)
+        if (c0 + u * S2 < NCH) x[u] = sp[(long long)(c0 + u * S2) * NFR];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        sr[u & 1] += x[u].x;
-        si[u & 1] += x[u].y;
-      }
+      for (int u = 0; u < 4; ++u)
+        if (c0 + u * S2 < NCH) {
+          sr += x[u].x;
+          si += x[u].y;
+        }
     }
     C2 o;
-    o.x = sr[0] + sr[1];
-    o.y = si[0] + si[1];
+    o.x = sr;
+    o.y = si;
     ((C2 *)(sm + L.sin_part))[s0 * NFR + fr] = o;
   }
   // the fringe-row x fringe-column products, each formed once: warp w takes
@@ -348,24 +359,9 @@ __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *s
       }
     }
   }
-  // core: merge over the warp, one state per warp into shared memory
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const T s1 = __shfl_xor_sync(0xffffffffu, cr.s, o), c1 = __shfl_xor_sync(0xffffffffu, cr.c, o);
-    const T s2 = __shfl_xor_sync(0xffffffffu, ci.s, o), c2 = __shfl_xor_sync(0xffffffffu, ci.c, o);
-    cr.merge(s1, c1);
-    ci.merge(s2, c2);
-  }
-  if (lane == 0) {
-    T *o = sm + L.core + 4 * warp;
-    o[0] = cr.s;
-    o[1] = cr.c;
-    o[2] = ci.s;
-    o[3] = ci.c;
-  }
   __syncthreads();
 
-  // ---- 2. merge the slices ------------------------------------------------
+  // ---- 2. merge the slices and the core states --------------------------
   if (tid < NFC) {
     Neu<T> a, b;
     for (int s0 = 0; s0 < S; ++s0) {
@@ -386,14 +382,107 @@ __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *s
       v.y += sp[s0 * NFR + fr].y;
     }
     ((C2 *)(sm + L.sin))[fr] = v;
+  } else if (warp == kRedThreads / 32 - 1) {
+    Neu<T> vr, vi;
+    for (int t = lane; t < kRedThreads; t += 32) {
+      const T *o = sm + L.core + 4 * t;
+      vr.merge(o[0], o[1]);
+      vi.merge(o[2], o[3]);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const T s1 = __shfl_xor_sync(0xffffffffu, vr.s, o), c1 = __shfl_xor_sync(0xffffffffu, vr.c, o);
+      const T s2 = __shfl_xor_sync(0xffffffffu, vi.s, o), c2 = __shfl_xor_sync(0xffffffffu, vi.c, o);
+      vr.merge(s1, c1);
+      vi.merge(s2, c2);
+    }
+    if (lane == 0) {
+      T *o = sm + L.core_tot;
+      o[0] = vr.s;
+      o[1] = vr.c;
+      o[2] = vi.s;
+      o[3] = vi.c;
+    }
   }
   __syncthreads();
 
-  // ---- 3. CV (warp 0) and RV (one thread per fringe row) -----------------
+  // ---- 3. RV: thread (q, fr) = segment q of fringe row fr's scans ---------
+  const int NL = Q - 1;                              // fringe columns per side
+  const int SEG = (NL + kRedSeg - 1) / kRedSeg;      // columns per segment
+  const int q = tid / 64, fr = tid % 64;
+  const int k0 = q * SEG, k1 = (k0 + SEG < NL) ? k0 + SEG : NL;
+  const C2 *row = (const C2 *)(sm + L.prod) + fr * red_prod_stride(NFC);
+  C2 *tot = (C2 *)(sm + L.tot);
+  if (fr < NFR) {
+    C2 sl = czero<C2>(), sr = czero<C2>();
+    for (int k = k0; k < k1; ++k) {
+      sl.x += row[k].x;
+      sl.y += row[k].y;
+      sr.x += row[NL + k].x;
+      sr.y += row[NL + k].y;
+    }
+    tot[2 * (q * NFR + fr)] = sl;
+    tot[2 * (q * NFR + fr) + 1] = sr;
+  }
+  __syncthreads();
+  if (fr < NFR) {
+    // carries: the left sums of the later segments (suffix) and the right
+    // sums of the earlier ones (prefix)
+    C2 cl = czero<C2>(), cr = czero<C2>();
+    for (int qq = kRedSeg - 1; qq > q; --qq) {
+      cl.x += tot[2 * (qq * NFR + fr)].x;
+      cl.y += tot[2 * (qq * NFR + fr)].y;
+    }
+    for (int qq = 0; qq < q; ++qq) {
+      cr.x += tot[2 * (qq * NFR + fr) + 1].x;
+      cr.y += tot[2 * (qq * NFR + fr) + 1].y;
+    }
+    const C2 s_in = ((const C2 *)(sm + L.sin))[fr];
+    C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR + fr;
+    // prefix of the right products at j = k0 is cr; the suffix of the left
+    // ones at j = k is cl + the segment's left values from k on
+    C2 suf[8];
+    {
+      C2 acc = cl;
+#pragma unroll
+      for (int u = 7; u >= 0; --u) {
+        if (k0 + u < k1) {
+          acc.x += row[k0 + u].x;
+          acc.y += row[k0 + u].y;
+        }
+        suf[u] = acc;
+      }
+    }
+    C2 pre = cr;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = k0 + u;
+      if (j < k1) {
+        if (j < J) {
+          C2 o;
+          o.x = s_in.x + suf[u].x + pre.x;
+          o.y = s_in.y + suf[u].y + pre.y;
+          rv[(long long)j * NFR] = o;
+        }
+        pre.x += row[NL + j].x;
+        pre.y += row[NL + j].y;
+      }
+    }
+    // the last column offset j = Q - 1 (only dc = 0 has it): no left fringe
+    // column in its box, every right one
+    if (q == kRedSeg - 1 && J == Q) {
+      C2 o;
+      o.x = s_in.x + T(0) + pre.x;
+      o.y = s_in.y + T(0) + pre.y;
+      rv[(long long)(Q - 1) * NFR] = o;
+    }
+  }
+
+  // ---- 4. CV (warp 0) ----------------------------------------------------
   if (warp == 0) {
     Neu<T> vr, vi;
-    for (int w = 0; w < kRedThreads / 32; ++w) {
-      const T *o = sm + L.core + 4 * w;
+    {
+      const T *o = sm + L.core_tot;
       vr.merge(o[0], o[1]);
       vi.merge(o[2], o[3]);
     }
@@ -414,29 +503,6 @@ __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *s
       o.x = vr.value();
       o.y = vi.value();
       ((C2 *)p.colval)[(long long)D * Q + lane] = o;
-    }
-  } else if (tid >= 32 && tid - 32 < NFR) {
-    const int fr = tid - 32;
-    C2 *row = (C2 *)(sm + L.prod) + fr * red_prod_stride(NFC);
-    const C2 s_in = ((const C2 *)(sm + L.sin))[fr];
-    // suffix over the left fringe-column products, in place
-    C2 acc = czero<C2>();
-    for (int k = Q - 2; k >= 0; --k) {
-      acc.x += row[k].x;
-      acc.y += row[k].y;
-      row[k] = acc;
-    }
-    C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR + fr;
-    C2 pre = czero<C2>();
-    for (int j = 0; j < J; ++j) {
-      C2 o;
-      o.x = s_in.x + (j < Q - 1 ? row[j].x : T(0)) + pre.x;
-      o.y = s_in.y + (j < Q - 1 ? row[j].y : T(0)) + pre.y;
-      rv[(long long)j * NFR] = o;
-      if (j < Q - 1) {
-        pre.x += row[Q - 1 + j].x;
-        pre.y += row[Q - 1 + j].y;
-      }
     }
   }
 }
@@ -474,19 +540,21 @@ __device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, u
   C2 *CVs = RVs + D2 * NFR;              // [2P-1]
   const C2 *rowval = (const C2 *)p.rowval;
   const C2 *colval = (const C2 *)p.colval;
-  // stage: every thread issues all of its loads before storing any
+  // stage: warp w takes the rows di = w, w + nw, ... of the (2P-1) x NFR
+  // block of RV (lanes along a row's contiguous fringe rows); every thread
+  // issues all of its loads before storing any
   {
-    constexpr int U = 16;  // (2P-1)(2P-2) <= 63*62 < 16*256 <= U*blockDim
-    C2 v[U];
-    const int total = D2 * NFR;
+    constexpr int MAXI = 8;  // 2P - 1 <= 63 rows over at least 8 warps
+    const int nw = (int)blockDim.x >> 5, warp = (int)threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C2 v[MAXI][2];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = threadIdx.x + u * (int)blockDim.x;
-      v[u] = czero<C2>();
-      if (idx < total) {
-        const int di = idx / NFR, f = idx - di * NFR, dr = di - (P - 1);
-        if (!(dc == 0 && dr < 0))
-          v[u] = rowval[((long long)combo_index(P, dr, dc) * p.Q + bj) * NFR + f];
+    for (int u = 0; u < MAXI; ++u) {
+      const int di = warp + u * nw, dr = di - (P - 1);
+      v[u][0] = v[u][1] = czero<C2>();
+      if (di < D2 && !(dc == 0 && dr < 0)) {
+        const C2 *src = rowval + ((long long)combo_index(P, dr, dc) * p.Q + bj) * NFR;
+        if (lane < NFR) v[u][0] = src[lane];
+        if (lane + 32 < NFR) v[u][1] = src[lane + 32];
       }
     }
     C2 cvv = czero<C2>();
@@ -495,9 +563,12 @@ __device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, u
       if (!(dc == 0 && dr < 0)) cvv = colval[(long long)combo_index(P, dr, dc) * p.Q + bj];
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = threadIdx.x + u * (int)blockDim.x;
-      if (idx < total) RVs[idx] = v[u];
+    for (int u = 0; u < MAXI; ++u) {
+      const int di = warp + u * nw;
+      if (di < D2) {
+        if (lane < NFR) RVs[di * NFR + lane] = v[u][0];
+        if (lane + 32 < NFR) RVs[di * NFR + lane + 32] = v[u][1];
+      }
     }
     if (threadIdx.x < D2) CVs[threadIdx.x] = cvv;
   }
@@ -565,30 +636,31 @@ __device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, u
   const long long DD = (long long)P * p.Q;
   C2 *R = (C2 *)p.R;
   const long long ra = (long long)P * bj, cb = (long long)P * (bj + dc);
+  const int nw = (int)blockDim.x >> 5, warp = (int)threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // row i of the block by warps, its columns by lanes (coalesced rows of R)
   if (dc > 0) {
-    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
-      const int i = e / P, ii = e - i * P;
-      R[(ra + i) * DD + cb + ii] = B[i * PP + ii];
-    }
-    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
-      const int ii = e / P, i = e - ii * P;
-      C2 v = B[i * PP + ii];
-      v.y = -v.y;
-      R[(cb + ii) * DD + ra + i] = v;
-    }
-  } else {
-    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
-      const int i = e / P, ii = e - i * P;
-      C2 v;
-      if (ii >= i) {
-        v = B[i * PP + ii];
-      } else {
-        v = B[ii * PP + i];
+    for (int i = warp; i < P; i += nw)
+      for (int ii = lane; ii < P; ii += 32) R[(ra + i) * DD + cb + ii] = B[i * PP + ii];
+    // the conjugate mirror: row ii of block (bj + dc, bj) is column ii of B
+    for (int ii = warp; ii < P; ii += nw)
+      for (int i = lane; i < P; i += 32) {
+        C2 v = B[i * PP + ii];
         v.y = -v.y;
+        R[(cb + ii) * DD + ra + i] = v;
       }
-      if (i == ii) v.y = T(0);
-      R[(ra + i) * DD + ra + ii] = v;
-    }
+  } else {
+    for (int i = warp; i < P; i += nw)
+      for (int ii = lane; ii < P; ii += 32) {
+        C2 v;
+        if (ii >= i) {
+          v = B[i * PP + ii];
+        } else {
+          v = B[ii * PP + i];
+          v.y = -v.y;
+        }
+        if (i == ii) v.y = T(0);
+        R[(ra + i) * DD + ra + ii] = v;
+      }
   }
 }
 
