@@ -365,14 +365,21 @@ void cov_batched_plan_destroy(cov_batched_plan *plan);
  *   form            0: one CTA per member in flight (any members);
  *                   1: one warp per member (only when every member has
  *                      M <= 32, N*M <= 1024 and P, Q <= 16);
+ *                   2: one CTA per small member in flight, every output a
+ *                      separable box sum of its combination's product image
+ *                      (column sums walked down the diagonal, window sums
+ *                      across the lanes), the upper triangle staged in
+ *                      shared memory and R written in whole rows (only when
+ *                      every member has M <= 32, N*M <= 1024, P, Q <= 16
+ *                      and PQ <= 100: the apertures of Section 2.3);
  *   reseed_interval form 0: the walk down each diagonal segment starts from
  *                   a direct-sum seed every this many outputs (Section 4.3's
  *                   segments cut shorter: more parallel seeds, fewer
  *                   additions in a chain); 0 = one seed per segment; <= 16;
  *   row_ranges      form 0: at most this many row ranges (1, 2 or 4) per
  *                   column block of the inner-row product tasks.
- * A new plan starts at form = 1 where allowed, else 0, reseed_interval 0,
- * row_ranges 4. */
+ * A new plan starts at form = 2 where allowed, else 1 where allowed, else 0,
+ * reseed_interval 0, row_ranges 4. */
 typedef struct {
   int32_t form;
   int32_t reseed_interval;
@@ -386,7 +393,7 @@ cov_status cov_batched_get_tuning(const cov_batched_plan *plan, cov_batched_tuni
  * outside the ranges above, or form 1 for a plan whose members do not all
  * fit it. */
 cov_status cov_batched_set_tuning(cov_batched_plan *plan, const cov_batched_tuning_t *t);
-/* Times the candidate knob settings (form 1 where allowed; form 0 with
+/* Times the candidate knob settings (forms 2 and 1 where allowed; form 0 with
  * reseed_interval 0, 2, 4 and row_ranges 2, 4) on the plan's own members,
  * `reps` launches each after one warm-up on `stream`, keeps the fastest and
  * uploads its tables into `workspace`. Writes every member's R (the last

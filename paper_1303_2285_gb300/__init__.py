@@ -61,7 +61,8 @@ class Tuning(ctypes.Structure):
 
 class BatchedTuning(ctypes.Structure):
     """Knobs of a batched plan: kernel form (0 CTA per member, 1 warp per
-    member), walk re-seed interval of form 0 (0: one seed per segment),
+    member, 2 box sums of small members in shared memory), walk re-seed
+    interval of form 0 (0: one seed per segment),
     row ranges per column block of form 0 (cov_batched_tuning_t)."""
     _fields_ = [("form", ctypes.c_int32), ("reseed_interval", ctypes.c_int32),
                 ("row_ranges", ctypes.c_int32)]

@@ -591,6 +591,191 @@ __global__ void __launch_bounds__(kWWarps * 32, 2)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batches of small members (M <= 32, N M <= 1024, P, Q <= 16, PQ <= 100;
+// the apertures of an image, Section 2.3): one CTA (8 warps) per member in
+// flight, several CTAs an SM. The member's A is staged in shared memory;
+// warp w takes the combinations w, w + 8, ... of Eq. 3.3 and, per
+// combination (dr, dc), computes every owned output (i, j) (Eq. 3.7-3.8) as
+// a separable box sum of its product image:
+//  - lanes own columns m; the column sums V(m) over the box rows of the first
+//    output i0 are seeded directly, the products of the rows that later leave
+//    the box are kept (per warp, in shared memory), and the walk down the
+//    diagonal adds the entering row's products and subtracts the kept ones
+//    (every distinct product of Eq. 3.5 formed once);
+//  - per output i, the sums over the box columns j .. j + Wd - 1 are window
+//    sums across the lanes, built by doubling (windows of 1, 2, 4, ... lanes,
+//    one shuffle each) and composed from the binary digits of Wd, so no
+//    difference of prefix sums is formed.
+// The outputs go to a shared-memory table of the upper triangle (combination
+// by combination, i then j); the CTA then writes R row by row, both
+// triangles, coalesced, scaling by the FP32 reciprocal of K.
+// ---------------------------------------------------------------------------
+constexpr int kXWarps = 8;
+constexpr int kXMaxM = 32;
+constexpr int kXMaxPQ = 16;
+constexpr int kXMaxD = 100;        // PQ: the output table holds PQ (PQ + 1) / 2 entries
+constexpr int kXMaxElems = 1024;   // N * M
+
+__host__ __device__ inline int box_table_entries(int P, int Q) { return P * Q * (P * Q + 1) / 2; }
+// Shared memory of one member: the kept products [warps][P-1][32], A, the
+// output table and the combinations' table offsets.
+__host__ __device__ inline size_t box_smem_bytes(int NM, int P, int Q) {
+  const int uc = P * Q + (P - 1) * (Q - 1);
+  return ((size_t)kXWarps * (P - 1) * 32 + (size_t)NM + (size_t)box_table_entries(P, Q)) *
+             sizeof(float2) +
+         (size_t)uc * sizeof(int);
+}
+
+// Offset in the output table of combination (dr, dc)'s outputs: the
+// combinations in the order of combo_index, each with (P - |dr|) x (Q - dc)
+// entries.
+__device__ __forceinline__ int box_table_offset(int P, int Q, int dr, int dc) {
+  if (dc == 0) return Q * (dr * P - dr * (dr - 1) / 2);
+  const int first = Q * P * (P + 1) / 2 + P * P * ((dc - 1) * Q - dc * (dc - 1) / 2);
+  const int before = dr <= 0 ? (P + dr - 1) * (P + dr) / 2 : P * (P - 1) / 2 + dr * P - dr * (dr - 1) / 2;
+  return first + (Q - dc) * before;
+}
+
+// Sum of v over lanes lane .. lane + Wd - 1, for the lanes whose window ends
+// at lane 31 or before (the other lanes receive unspecified values): windows
+// of 1, 2, 4, ... lanes by doubling (one 64-bit shuffle and one packed FP32x2
+// add each), composed from the binary digits of Wd.
+__device__ __forceinline__ unsigned long long add_f32x2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float2 lane_window_sum(float2 v, int Wd) {
+  unsigned long long w = pk2(v.x, v.y);
+  if ((Wd & (Wd - 1)) == 0) {  // a power of two: doubling alone
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if ((1 << k) < Wd) w = add_f32x2(w, __shfl_down_sync(0xffffffffu, w, 1 << k));
+    return upk2(w);
+  }
+  unsigned long long r = 0ull;
+  int off = 0;
+  bool first = true;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int b = 1 << k;
+    if (b > Wd) break;
+    if (Wd & b) {
+      const unsigned long long t = off == 0 ? w : __shfl_down_sync(0xffffffffu, w, off);
+      r = first ? t : add_f32x2(r, t);
+      first = false;
+      off += b;
+    }
+    if (2 * b <= Wd) w = add_f32x2(w, __shfl_down_sync(0xffffffffu, w, b));
+  }
+  return upk2(r);
+}
+
+__device__ __forceinline__ float2 prod_conj(float2 a, float2 b) {
+  float2 v = make_float2(0.f, 0.f);
+  cmac_conj(v, a, b);
+  return v;
+}
+
+__global__ void __launch_bounds__(kXWarps * 32, 3)
+    k_batched_box(const BDesc *descs, const int *order, const int *slot_begin, int mean) {
+  extern __shared__ __align__(16) unsigned char smem_x[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int mi = slot_begin[blockIdx.x]; mi < slot_begin[blockIdx.x + 1]; ++mi) {
+    const BDesc d = descs[order[mi]];
+    const int N = d.N, M = d.M, P = d.P, Q = d.Q;
+    const int H = N - P + 1, Wd = M - Q + 1, DD = P * Q, nUC = DD + (P - 1) * (Q - 1);
+    float2 *keep = (float2 *)smem_x + warp * (P - 1) * 32 + lane;  // [warp][P-1][32]
+    float2 *As = (float2 *)smem_x + kXWarps * (P - 1) * 32;     // [N][M]
+    float2 *OT = As + N * M;                       // upper-triangle outputs
+    int *offs = (int *)(OT + box_table_entries(P, Q));
+    __syncthreads();  // the previous member's reads of shared memory are done
+    for (int r = warp; r < N; r += kXWarps)
+      if (lane < M) As[r * M + lane] = __ldg(d.A + (long long)r * d.lda + lane);
+    for (int c = tid; c < nUC; c += kXWarps * 32) {
+      int dr, dc;
+      combo_of(P, c, dr, dc);
+      offs[c] = box_table_offset(P, Q, dr, dc);
+    }
+    __syncthreads();
+    // ---- box sums of every combination ------------------------------------
+    for (int c = warp; c < nUC; c += kXWarps) {
+      int dr, dc;
+      combo_of(P, c, dr, dc);
+      const int i0 = dr < 0 ? -dr : 0, I = P - (dr < 0 ? -dr : dr), J = Q - dc;
+      const bool mok = lane < M - dc;  // the column's partner m + dc lies in A
+      const float2 *pa = As + i0 * M + (mok ? lane : 0);
+      const float2 *pb = As + (i0 + dr) * M + (mok ? lane + dc : 0);
+      // seed: the box rows r = 0 .. H-1 of output i0; rows r < I-1 leave the
+      // box later and are kept
+      float2 V = make_float2(0.f, 0.f), V2 = make_float2(0.f, 0.f);
+      if (mok) {
+        for (int r = 0; r < I - 1; ++r) {
+          const float2 x = prod_conj(pa[r * M], pb[r * M]);
+          keep[r * 32] = x;
+          V.x += x.x;
+          V.y += x.y;
+        }
+        int r = I - 1 > 0 ? I - 1 : 0;
+        for (; r + 1 < H; r += 2) {
+          cmac_conj(V, pa[r * M], pb[r * M]);
+          cmac_conj(V2, pa[(r + 1) * M], pb[(r + 1) * M]);
+        }
+        if (r < H) cmac_conj(V, pa[r * M], pb[r * M]);
+      }
+      V.x += V2.x;
+      V.y += V2.y;
+      float2 *op = OT + offs[c] + lane;
+      const float2 *pain = pa + H * M, *pbin = pb + H * M, *kp = keep;
+      for (int s = 0; s < I; ++s) {
+        const float2 o = lane_window_sum(V, Wd);
+        if (lane < J) *op = o;
+        op += J;
+        if (s < I - 1 && mok) {  // row s leaves the box, row s + H enters
+          const float2 xin = prod_conj(*pain, *pbin);
+          const float2 xout = *kp;
+          V.x += xin.x - xout.x;
+          V.y += xin.y - xout.y;
+        }
+        pain += M;
+        pbin += M;
+        kp += 32;
+      }
+    }
+    __syncthreads();
+    // ---- R, row by row (both triangles) ------------------------------------
+    const long long K = (long long)H * Wd;
+    const float rK = mean ? 1.0f / (float)K : 1.0f;
+    int ib[4], jb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int b = lane + 32 * q;
+      ib[q] = b % P;
+      jb[q] = b / P;
+    }
+    for (int a = warp; a < DD; a += kXWarps) {
+      const int ia = a % P, ja = a / P;
+      float2 *Ra = d.R + (long long)a * DD;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = lane + 32 * q;
+        if (b < DD) {
+          const bool mir = b < a;
+          const int dr = mir ? ia - ib[q] : ib[q] - ia, dc = mir ? ja - jb[q] : jb[q] - ja;
+          const int s = (mir ? ib[q] : ia) - (dr < 0 ? -dr : 0), j = mir ? jb[q] : ja;
+          float2 v = OT[offs[combo_index(P, dr, dc)] + s * (Q - dc) + j];
+          v.x *= rK;
+          v.y *= rK;
+          if (mir) v.y = -v.y;
+          if (a == b) v.y = 0.f;
+          Ra[b] = v;
+        }
+      }
+    }
+  }
+}
+
 }  // namespace cov
 
 // ---------------------------------------------------------------------------
@@ -603,7 +788,9 @@ struct cov_batched_plan {
   int grid;
   int sms;
   int narrow_ok;               // every member fits k_batched_warp
-  int warp_kernel;             // tuned: 1 = one warp per member
+  int box_ok;                  // every member fits k_batched_box
+  size_t box_smem;             // k_batched_box's shared memory for the largest member
+  int form;                    // tuned: 0 = CTA form, 1 = one warp per member, 2 = box form
   int L;                       // tuned: re-seed interval of the CTA form's walk (0: none)
   int rs_max;                  // tuned: row ranges per column block (1, 2, 4)
   int mean;
@@ -728,21 +915,26 @@ void build_schedule(cov_batched_plan *pl) {
   std::vector<long long> cost(count);
   for (int i = 0; i < count; ++i) {
     const cov::BDesc &d = pl->descs[i];
-    if (pl->warp_kernel) {
-      // the warp form: distinct products plus the per-output scan and write
-      // steps
+    if (pl->form == 1 || pl->form == 2) {
+      // the warp and box forms: distinct products plus the per-output-row
+      // window sums and, for the box form, the R elements written
       long long steps = 0;  // outputs i of every combination
       for (int dc = 0; dc < d.Q; ++dc)
         for (int dr = dc ? -(d.P - 1) : 0; dr < d.P; ++dr) steps += d.P - (dr < 0 ? -dr : dr);
-      cost[i] = cov::distinct_products(d.N, d.M, d.P, d.Q) / 8 + 40 * steps + 200;
+      const long long DD = (long long)d.P * d.Q;
+      cost[i] = pl->form == 1 ? cov::distinct_products(d.N, d.M, d.P, d.Q) / 8 + 40 * steps + 200
+                              : cov::distinct_products(d.N, d.M, d.P, d.Q) / 8 + 24 * steps +
+                                    DD * DD / 8 + 200;
     } else {
       cost[i] = (long long)batched_member_cost(d.N, d.M, d.P, d.Q);
     }
   }
-  // (the warp kernel fits two CTAs an SM: twice the warps to hide latency)
-  const int grid = pl->warp_kernel ? std::min(2 * pl->sms, (count + cov::kWWarps - 1) / cov::kWWarps)
+  // (the warp kernel fits two CTAs an SM: twice the warps to hide latency;
+  // the box kernel three CTAs an SM, one member each)
+  const int grid = pl->form == 1 ? std::min(2 * pl->sms, (count + cov::kWWarps - 1) / cov::kWWarps)
+                   : pl->form == 2 ? std::min(3 * pl->sms, count)
                                    : std::min(pl->sms, count);
-  const int slots = pl->warp_kernel ? grid * cov::kWWarps : grid;
+  const int slots = pl->form == 1 ? grid * cov::kWWarps : grid;
   std::vector<int> bin(count);
   cov::lpt_assign(cost.data(), count, slots, bin.data(), nullptr);
   std::vector<int> order(count);
@@ -780,23 +972,31 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   pl->sms = sms;
   pl->descs.resize(count);
   bool narrow = true;  // every member small enough for one warp
+  bool box = true;     // every member small enough for the box form
+  size_t box_smem = 0;
   for (int i = 0; i < count; ++i) {
     const cov_desc &d = descs[i];
     pl->descs[i] = {(const float2 *)d.A, (float2 *)d.R, d.lda, d.N, d.M, d.P, d.Q};
     narrow = narrow && d.M <= cov::kWMaxM && d.P <= cov::kWMaxPQ && d.Q <= cov::kWMaxPQ &&
              d.N * d.M <= cov::kWMaxElems;
+    box = box && d.M <= cov::kXMaxM && d.P <= cov::kXMaxPQ && d.Q <= cov::kXMaxPQ &&
+          d.P * d.Q <= cov::kXMaxD && d.N * d.M <= cov::kXMaxElems;
+    if (box) box_smem = std::max(box_smem, cov::box_smem_bytes(d.N * d.M, d.P, d.Q));
   }
   pl->narrow_ok = narrow ? 1 : 0;
+  pl->box_ok = box ? 1 : 0;
+  pl->box_smem = box ? box_smem : 0;
   // defaults (cov_batched_autotune times the alternatives)
-  pl->warp_kernel = pl->narrow_ok;
+  pl->form = pl->box_ok ? 2 : pl->narrow_ok ? 1 : 0;
   pl->L = 0;
   pl->rs_max = cov::kBMaxRS;
   build_schedule(pl);
   // the tables are laid out for the larger of the two forms' slot counts
-  const int max_slots = std::max(std::min(sms, count),
-                                 narrow ? std::min(2 * sms, (count + cov::kWWarps - 1) / cov::kWWarps) *
-                                              cov::kWWarps
-                                        : 0);
+  const int max_slots = std::max({std::min(sms, count),
+                                  narrow ? std::min(2 * sms, (count + cov::kWWarps - 1) / cov::kWWarps) *
+                                               cov::kWWarps
+                                         : 0,
+                                  box ? std::min(3 * sms, count) : 0});
   size_t off = cov::kWsHeader;
   pl->off_desc = off;
   off = al256(off + sizeof(cov::BDesc) * count);
@@ -859,7 +1059,15 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, s
   if (cov::ensure_dyn_smem((const void *)cov::k_batched, smem, false) != cudaSuccess)
     return COV_ECUDA;
   if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
-  if (plan->warp_kernel) {
+  if (plan->form == 2) {
+    if (cov::ensure_dyn_smem((const void *)cov::k_batched_box, plan->box_smem, false) != cudaSuccess)
+      return COV_ECUDA;
+    cov::k_batched_box<<<plan->grid, cov::kXWarps * 32, plan->box_smem, s>>>(
+        (const cov::BDesc *)(w + plan->off_desc), (const int *)(w + plan->off_order),
+        (const int *)(w + plan->off_begin), plan->mean);
+    return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
+  }
+  if (plan->form == 1) {
     const size_t wsmem = cov::kWWarps * cov::kWWarpBytes;
     if (cov::ensure_dyn_smem((const void *)cov::k_batched_warp, wsmem, false) != cudaSuccess)
       return COV_ECUDA;
@@ -878,7 +1086,7 @@ void cov_batched_plan_destroy(cov_batched_plan *plan) { delete plan; }
 
 cov_status cov_batched_get_tuning(const cov_batched_plan *plan, cov_batched_tuning_t *t) {
   if (!plan || !t) return COV_EINVAL;
-  t->form = plan->warp_kernel;
+  t->form = plan->form;
   t->reseed_interval = plan->L;
   t->row_ranges = plan->rs_max;
   return COV_OK;
@@ -886,11 +1094,13 @@ cov_status cov_batched_get_tuning(const cov_batched_plan *plan, cov_batched_tuni
 
 cov_status cov_batched_set_tuning(cov_batched_plan *plan, const cov_batched_tuning_t *t) {
   if (!plan || !t) return COV_EINVAL;
-  if (t->form < 0 || t->form > 1 || (t->form == 1 && !plan->narrow_ok)) return COV_EINVAL;
+  if (t->form < 0 || t->form > 2 || (t->form == 1 && !plan->narrow_ok) ||
+      (t->form == 2 && !plan->box_ok))
+    return COV_EINVAL;
   if (t->reseed_interval < 0 || t->reseed_interval > cov::kBMaxPQ) return COV_EINVAL;
   if (t->row_ranges != 1 && t->row_ranges != 2 && t->row_ranges != 4) return COV_EINVAL;
-  const bool rebuild = t->form != plan->warp_kernel;
-  plan->warp_kernel = t->form;
+  const bool rebuild = t->form != plan->form;
+  plan->form = t->form;
   plan->L = t->reseed_interval;
   plan->rs_max = t->row_ranges;
   if (rebuild) build_schedule(plan);
@@ -904,10 +1114,11 @@ cov_status cov_batched_autotune(cov_batched_plan *plan, void *workspace, size_t 
   const cov_status dst = plan_matches_device(plan);
   if (dst != COV_OK) return dst;
   cudaStream_t s = (cudaStream_t)stream;
-  // candidates: the warp form where every member fits it; the CTA form with
-  // segments of the whole diagonal or of 2 or 4 outputs, and 2 or 4 row
-  // ranges
+  // candidates: the box and warp forms where every member fits them; the CTA
+  // form with segments of the whole diagonal or of 2 or 4 outputs, and 2 or
+  // 4 row ranges
   std::vector<cov_batched_tuning_t> cand;
+  if (plan->box_ok) cand.push_back({2, 0, cov::kBMaxRS});
   if (plan->narrow_ok) cand.push_back({1, 0, cov::kBMaxRS});
   for (int L : {0, 2, 4})
     for (int rs : {2, 4}) cand.push_back({0, L, rs});

@@ -164,7 +164,7 @@ def test_batched_narrow_both_forms_and_autotune(oracle_mod):
         for (At, Rt, P, Q), A in zip(items, host):
             assert rel_fro(Rt.cpu().numpy(), oracle_R(oracle_mod, A, P, Q)) < F32_TOL, (form, L)
     best = plan.autotune(ws, reps=2)
-    assert best["form"] in (0, 1) and best["row_ranges"] in (2, 4)
+    assert best["form"] in (0, 1, 2) and best["row_ranges"] in (2, 4)
     for _, Rt, _, _ in items:
         Rt.fill_(complex(np.nan, np.nan))
     plan.run(ws)
@@ -172,3 +172,52 @@ def test_batched_narrow_both_forms_and_autotune(oracle_mod):
     cov.check_device_status(ws)
     for (At, Rt, P, Q), A in zip(items, host):
         assert rel_fro(Rt.cpu().numpy(), oracle_R(oracle_mod, A, P, Q)) < F32_TOL
+
+
+def box_shapes(count, seed):
+    """Members the box form takes (M <= 32, N M <= 1024, P, Q <= 16,
+    PQ <= 100), including the smallest and the widest windows."""
+    rng = np.random.default_rng(seed)
+    out = [(25, 25, 10, 10), (19, 32, 10, 10), (31, 32, 16, 6), (33, 31, 6, 16), (9, 1, 5, 1),
+           (1, 1, 1, 1), (64, 2, 7, 1), (21, 17, 11, 9), (8, 32, 1, 16), (40, 25, 20, 5)]
+    out = [s for s in out if s[2] <= 16 and s[3] <= 16]
+    while len(out) < count:
+        N, M = int(rng.integers(1, 81)), int(rng.integers(1, 33))
+        if N * M > 1024:
+            continue
+        P = int(rng.integers(1, min(16, (N + 1) // 2) + 1))
+        Q = int(rng.integers(1, min(16, (M + 1) // 2) + 1))
+        if P * Q <= 100:
+            out.append((N, M, P, Q))
+    return out
+
+
+@pytest.mark.parametrize("form", [2, 1, 0])
+def test_batched_box_form_members(oracle_mod, form):
+    shapes = box_shapes(48, 51)
+    items, host = make_batch(shapes, "cn", 1500)
+    plan = cov.BatchedPlan(items)
+    assert plan.tuning["form"] == 2  # the default where every member fits it
+    plan.set_tuning(form, 0, 4)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    plan.run(ws)
+    torch.cuda.synchronize()
+    cov.check_device_status(ws)
+    for (At, Rt, P, Q), A in zip(items, host):
+        got = Rt.cpu().numpy()
+        assert rel_fro(got, oracle_R(oracle_mod, A, P, Q)) < F32_TOL, (A.shape, P, Q, form)
+        assert np.array_equal(got, got.conj().T)
+        assert np.all(got.diagonal().imag == 0)
+
+
+def test_batched_box_form_integer_exact(oracle_mod):
+    # small integers: products, column sums, walks and lane-window sums are
+    # exact integers in FP32, so the SUM result is exact
+    shapes = box_shapes(30, 52)
+    items, host = make_batch(shapes, "int", 1700)
+    plan, _ = run_plan(items, norm="sum")
+    assert plan.tuning["form"] == 2
+    for (At, Rt, P, Q), A in zip(items, host):
+        S = oracle_R(oracle_mod, A, P, Q, mean=False)
+        assert np.array_equal(Rt.cpu().numpy(), S.astype(np.complex64)), (A.shape, P, Q)
