@@ -20,6 +20,23 @@ def test_small_members_default_to_the_warp_form():
     assert plan.tuning == {"form": 1, "reseed_interval": 0, "row_ranges": 4}
 
 
+def test_aperture_sized_members_default_to_the_box_form():
+    plan = make_plan([(25, 25, 10, 10), (20, 17, 4, 3), (9, 1, 5, 1)])
+    assert plan.tuning == {"form": 2, "reseed_interval": 0, "row_ranges": 4}
+    for form in (1, 0, 2):
+        plan.set_tuning(form, 0, 4)
+        assert plan.tuning["form"] == form
+
+
+def test_box_form_refused_beyond_its_limits():
+    plan = make_plan([(25, 25, 10, 10), (31, 32, 16, 16)])  # PQ = 256 > 100
+    with pytest.raises(cov.CovError):
+        plan.set_tuning(2)
+    plan2 = make_plan([(25, 25, 10, 10), (64, 64, 8, 8)])  # M = 64 > 32
+    with pytest.raises(cov.CovError):
+        plan2.set_tuning(2)
+
+
 def test_wide_members_default_to_the_cta_form_and_refuse_the_warp_form():
     plan = make_plan([(25, 25, 10, 10), (64, 64, 8, 8)])  # M = 64 does not fit one warp
     assert plan.tuning == {"form": 0, "reseed_interval": 0, "row_ranges": 4}
@@ -36,7 +53,7 @@ def test_set_and_get_round_trip():
         assert plan.tuning == {"form": form, "reseed_interval": L, "row_ranges": rs}
 
 
-@pytest.mark.parametrize("form,L,rs", [(2, 0, 4), (-1, 0, 4), (0, -1, 4), (0, 17, 4), (0, 0, 3),
+@pytest.mark.parametrize("form,L,rs", [(3, 0, 4), (-1, 0, 4), (0, -1, 4), (0, 17, 4), (0, 0, 3),
                                        (0, 0, 0)])
 def test_bad_values_are_refused(form, L, rs):
     plan = make_plan([(25, 25, 10, 10)])
