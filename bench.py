@@ -63,6 +63,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def parse_knobs(text: str) -> dict:
+    """"G,TRB,L,K[,TC]" -> the combination path's tuning knobs."""
+    v = [int(x) for x in text.split(",")]
+    if len(v) not in (4, 5):
+        raise ValueError("--knobs wants G,TRB,L,K or G,TRB,L,K,TC")
+    names = ("lag_group", "rows_per_task", "reseed_interval", "kernels", "tile_cols")
+    return dict(zip(names, v + [0] * (5 - len(v))))
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -302,6 +311,109 @@ def _config(w):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def bench_sharded(args, rank, world, local):
+    """One matrix split across the ranks by column lag (Section 4.2: the
+    combinations of a lag range own whole blocks of R, so no reduction is
+    needed). A step: every rank computes its lags' blocks
+    (cov_estimate_shard), packs them (cov_shard_pack), one NCCL all-gather of
+    the packed blocks, and every rank unpacks the others' (cov_shard_unpack),
+    so that each ends with all of R. Strong scaling: the total work is one
+    matrix whatever the rank count; value = its distinct products / max over
+    ranks of the step time."""
+    import datetime
+    import socket
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import cov_workloads as wl
+    import paper_1303_2285_gb300 as cov
+    from paper_1303_2285_gb300 import shard
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:  # the same NCCL collective with a one-rank group
+        with socket.socket() as so:
+            so.bind(("127.0.0.1", 0))
+            port = so.getsockname()[1]
+        store = dist.TCPStore("127.0.0.1", port, 1, True, timeout=datetime.timedelta(seconds=60))
+        dist.init_process_group("nccl", store=store, rank=0, world_size=1,
+                                device_id=torch.device("cuda", local))
+    w = wl.WORKLOADS[args.workload]
+    dt = torch.complex64 if w.dtype == "c64" else torch.complex128
+    A_np = wl.workload_input(w)  # every rank holds all of A (the same input)
+    A = torch.from_numpy(A_np).cuda()
+    D = w.P * w.Q
+    R = torch.empty((D, D), dtype=dt, device="cuda")
+    um = cov.plan_info(w.N, w.M, w.P, w.Q)["distinct_products"]
+    if args.knobs:
+        cov.tuning_set(w.dtype, w.N, w.M, w.P, w.Q, parse_knobs(args.knobs))
+    elif args.autotune:
+        cov.autotune(A, w.P, w.Q, reps=5)
+    knobs, _ = cov.tuning_get(w.dtype, w.N, w.M, w.P, w.Q)
+    ranges, costs = shard.partition_lags(w.N, w.M, w.P, w.Q, world)
+    lo, hi = ranges[rank]
+    ws = torch.empty(max(256, cov.workspace_size(w.dtype, w.N, w.M, w.P, w.Q, "recurrence")),
+                     dtype=torch.uint8, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    scratch = None
+
+    def step():
+        nonlocal scratch
+        shard.estimate_shard_into(A, R, w.P, w.Q, lo, hi, workspace=ws)
+        scratch = shard.allgather_blocks(R, w.P, w.Q, ranges, rank, scratch=scratch)
+
+    for k in range(args.warmup):
+        flush.fill_(k & 0xFF)
+        step()
+    torch.cuda.synchronize()
+    cov.check_device_status(ws)
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(K):
+        flush.fill_((k + 1) & 0xFF)
+        ev[2 * k].record(stream)
+        step()
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    cov.check_device_status(ws)
+    total_s = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)) / 1e3
+    t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_s = float(t.item())
+    # the assembled R against the unsharded estimate on the same input
+    full = cov.estimate(A, w.P, w.Q, algo="recurrence")
+    torch.cuda.synchronize()
+    same = bool(torch.equal(torch.view_as_real(full), torch.view_as_real(R)))
+    ok = torch.tensor([1 if same else 0], dtype=torch.int32, device="cuda")
+    dist.all_reduce(ok, op=dist.ReduceOp.MIN)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": um * K / total_s, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / K, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64" if w.dtype == "c128" else "f32",
+            "data": "synthetic",
+            "config": dict(_config(w), tuning=knobs, sharding="column lags per rank",
+                           lag_ranges=ranges, rank_costs=costs,
+                           collective="NCCL all_gather of the packed blocks (padded to the largest share)"),
+            "assembled_R_equals_unsharded": bool(ok.item() == 1),
+            "nccl_version": ".".join(str(x) for x in torch.cuda.nccl.version()),
+            "process_group_size": dist.get_world_size(),
+            # per step: the shard's kernels, one pack, one unpack per other rank
+            "gpu_launches": K * ((4 if knobs["kernels"] == 4 else 1) + 1 + (world - 1)),
+        }
+        print(json.dumps(line))
+    dist.barrier()
+    dist.destroy_process_group()
+    return 0
+
+
 def bench_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -330,9 +442,7 @@ def bench_ours(args, rank, world, local):
     um = info["distinct_products"]
     tune_ms, source = None, "defaults"
     if args.knobs:
-        g_, trb_, l_, k_ = (int(x) for x in args.knobs.split(","))
-        cov.tuning_set(w.dtype, w.N, w.M, w.P, w.Q, {"lag_group": g_, "rows_per_task": trb_,
-                                                     "reseed_interval": l_, "kernels": k_})
+        cov.tuning_set(w.dtype, w.N, w.M, w.P, w.Q, parse_knobs(args.knobs))
         source = "given"
     elif args.tuning_file and os.path.exists(args.tuning_file):
         cov.tuning_load(args.tuning_file)
@@ -862,9 +972,7 @@ def profile_case(case: str, knobs=None) -> int:
         # 2048 x 512 input (32 x 32 window) or the 1024 x 1024 one (16 x 16)
         w = wl.WORKLOADS["sar_2048x512_w32_f32" if case == "sar" else "cn_1024x1024_w16_f32"]
         if knobs:
-            g_, trb_, l_, k_ = (int(x) for x in knobs.split(","))
-            cov.tuning_set(w.dtype, w.N, w.M, w.P, w.Q, {"lag_group": g_, "rows_per_task": trb_,
-                                                         "reseed_interval": l_, "kernels": k_})
+            cov.tuning_set(w.dtype, w.N, w.M, w.P, w.Q, parse_knobs(knobs))
         A = torch.from_numpy(wl.workload_input(w)).cuda()
         R = torch.empty((w.P * w.Q, w.P * w.Q), dtype=torch.complex64, device="cuda")
         ws = torch.empty(cov.workspace_size(w.dtype, w.N, w.M, w.P, w.Q, "recurrence"),
@@ -912,6 +1020,9 @@ def profile_case(case: str, knobs=None) -> int:
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--sharded", action="store_true",
+                    help="split one matrix across the ranks by column lag and gather R with NCCL "
+                         "(strong scaling) instead of one matrix per rank")
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
@@ -924,8 +1035,8 @@ def main():
     ap.add_argument("--tuning-file", default=None,
                     help="load the knobs from this file if it exists, else autotune and save them")
     ap.add_argument("--knobs", default=None,
-                    help="G,TRB,L,K: use these knobs (lag group, rows per task, re-seed interval, "
-                         "kernels 1|4) instead of autotuning")
+                    help="G,TRB,L,K[,TC]: use these knobs (lag group, rows per task, re-seed interval, "
+                         "kernels 1|4, tile columns 32|64) instead of autotuning")
     ap.add_argument("--profile-case", choices=("sar", "cn", "batched", "gemm", "adjoint", "apertures"),
                     default=None,
                     help="run a few launches of one secondary kernel on a small case (for ncu) "
@@ -938,6 +1049,8 @@ def main():
     rank, world, local = dist_setup()
     if args.impl == "reference":
         return bench_reference(args, rank, world)
+    if args.sharded:
+        return bench_sharded(args, rank, world, local)
     return bench_ours(args, rank, world, local)
 
 

@@ -482,6 +482,22 @@ cov_status cov_partition_lags(int64_t N, int64_t M, int P, int Q, int n_ranks, i
 cov_status cov_estimate_shard(const void *A, cov_dtype dtype, int64_t N, int64_t M, int64_t lda,
                               int P, int Q, int dc_lo, int dc_hi, void *R, cov_norm norm,
                               void *workspace, size_t ws_bytes, cov_stream_t stream);
+/* The exchange of a sharded estimate: the blocks of R a column-lag range
+ * [dc_lo, dc_hi) owns (above), packed contiguously so that ranks can gather
+ * them with one collective (no reduction: Section 4.2 gives each block one
+ * owner). Layout: lag by lag; within lag dc, for a = 0 .. Q-dc-1, block
+ * (a, a + dc) and then, for dc > 0, block (a + dc, a); each block P x P
+ * row-major. cov_shard_packed_size (host) gives its bytes; cov_shard_pack
+ * copies those blocks of R (device, PQ x PQ) into `packed` (device) and
+ * cov_shard_unpack writes them back into R, leaving every other element of R
+ * untouched. Stream-ordered kernels; an empty range queues nothing.
+ * COV_EINVAL for a bad dtype, shape or range, or a null pointer. */
+cov_status cov_shard_packed_size(cov_dtype dtype, int P, int Q, int dc_lo, int dc_hi,
+                                 size_t *bytes);
+cov_status cov_shard_pack(const void *R, cov_dtype dtype, int P, int Q, int dc_lo, int dc_hi,
+                          void *packed, cov_stream_t stream);
+cov_status cov_shard_unpack(const void *packed, cov_dtype dtype, int P, int Q, int dc_lo,
+                            int dc_hi, void *R, cov_stream_t stream);
 /* Batched workload (Section 5.1, several matrices at once): assigns each of
  * `count` matrices (HOST descriptors; only the sizes are read) to one of
  * n_ranks ranks, longest processing time first by the same cost the batched

@@ -117,6 +117,9 @@ SIGNATURES = [
                                 ctypes.POINTER(ctypes.c_int64)]),
     ("cov_estimate_shard", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _I, _I, _VP, _I, _VP, _SZ,
                                 _VP]),
+    ("cov_shard_packed_size", _I, [_I, _I, _I, _I, _I, ctypes.POINTER(_SZ)]),
+    ("cov_shard_pack", _I, [_VP, _I, _I, _I, _I, _I, _VP, _VP]),
+    ("cov_shard_unpack", _I, [_VP, _I, _I, _I, _I, _I, _VP, _VP]),
     ("cov_partition_matrices", _I, [ctypes.POINTER(CovDesc), _I, _I,
                                     ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int64)]),

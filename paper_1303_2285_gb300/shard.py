@@ -155,6 +155,72 @@ def assemble(P: int, Q: int, ranges: Sequence[Tuple[int, int]], shards: Sequence
 
 
 # ---------------------------------------------------------------------------
+# gather through one collective (NCCL for device tensors, gloo on the host)
+# ---------------------------------------------------------------------------
+def packed_elements(P: int, Q: int, dc_lo: int, dc_hi: int) -> int:
+    """Complex elements of a lag range's packed blocks (len(owned_blocks) P^2)."""
+    return len(owned_blocks(Q, dc_lo, dc_hi)) * P * P
+
+
+def device_pack(R, P: int, Q: int, dc_lo: int, dc_hi: int, out, stream=None) -> None:
+    """The library's pack kernel: R's blocks of [dc_lo, dc_hi) into `out`
+    (device tensors of R's dtype, `out` with packed_elements(...) entries)."""
+    if not (R.is_cuda and out.is_cuda):
+        raise ValueError("device tensors expected (no CPU fallback)")
+    _check(load().cov_shard_pack(R.data_ptr(), DTYPES[_dtype_of(R)], P, Q, dc_lo, dc_hi,
+                                 out.data_ptr(), _stream_ptr(stream)), "cov_shard_pack")
+
+
+def device_unpack(packed, R, P: int, Q: int, dc_lo: int, dc_hi: int, stream=None) -> None:
+    if not (R.is_cuda and packed.is_cuda):
+        raise ValueError("device tensors expected (no CPU fallback)")
+    _check(load().cov_shard_unpack(packed.data_ptr(), DTYPES[_dtype_of(R)], P, Q, dc_lo, dc_hi,
+                                   R.data_ptr(), _stream_ptr(stream)), "cov_shard_unpack")
+
+
+def host_pack(R, P: int, Q: int, dc_lo: int, dc_hi: int, out) -> None:
+    """The same layout on host tensors (for CPU process groups)."""
+    import torch
+    out.copy_(torch.from_numpy(pack_blocks(R.numpy(), P, Q, dc_lo, dc_hi).reshape(-1)))
+
+
+def host_unpack(packed, R, P: int, Q: int, dc_lo: int, dc_hi: int) -> None:
+    Rn = R.numpy()
+    unpack_blocks(Rn, packed.numpy().reshape(-1, P, P), P, Q, dc_lo, dc_hi)
+
+
+def allgather_blocks(R, P: int, Q: int, ranges: Sequence[Tuple[int, int]], rank: int,
+                     group=None, pack=None, unpack=None, scratch=None):
+    """Every rank holds its own blocks of R (the lag range ranges[rank]); after
+    this call every rank holds all of R. One all-gather of equal-size packed
+    buffers (each rank's blocks, zero-padded to the largest share); `pack`
+    and `unpack` default to the library's kernels (device tensors); pass
+    host_pack / host_unpack for host tensors on a CPU process group.
+    `scratch` may hold (send, recv) buffers from an earlier call."""
+    import torch
+    import torch.distributed as dist
+    pack = pack or device_pack
+    unpack = unpack or device_unpack
+    world = len(ranges)
+    sizes = [packed_elements(P, Q, lo, hi) for lo, hi in ranges]
+    mx = max(sizes)
+    if scratch is None:
+        send = torch.zeros(mx, dtype=R.dtype, device=R.device)
+        recv = [torch.empty(mx, dtype=R.dtype, device=R.device) for _ in range(world)]
+    else:
+        send, recv = scratch
+    lo, hi = ranges[rank]
+    if sizes[rank]:
+        pack(R, P, Q, lo, hi, send[:sizes[rank]])
+    # collectives carry the real and imaginary parts as a real tensor
+    dist.all_gather([torch.view_as_real(x) for x in recv], torch.view_as_real(send), group=group)
+    for r, (lo_r, hi_r) in enumerate(ranges):
+        if r != rank and sizes[r]:
+            unpack(recv[r][:sizes[r]], R, P, Q, lo_r, hi_r)
+    return send, recv
+
+
+# ---------------------------------------------------------------------------
 # the device side of one rank
 # ---------------------------------------------------------------------------
 def estimate_shard_into(A, R, P: int, Q: int, dc_lo: int, dc_hi: int, norm: str = "mean",

@@ -78,3 +78,56 @@ def test_adjoint_row_bands(N, M, P, Q, ranks, norm):
         got[lo:hi] = dA[lo - hl:hi - hl]
     assert not np.isnan(got).any()
     assert rel_fro(got, full) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("P,Q,ranks", [(7, 5, 2), (16, 16, 3), (32, 32, 8), (4, 1, 2)])
+def test_device_pack_unpack_assembles_R(dtype, P, Q, ranks):
+    # the library's pack kernel must give the host layout (shard.pack_blocks)
+    # bit for bit, and unpacking every rank's packed blocks into a NaN-filled
+    # R must rebuild the unsharded estimate
+    N, M = 2 * P + 40, 2 * Q + 33
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    A = to_dev(wl.complex_normal((N, M), 11 + P * Q, dtype=dtype), tdt)
+    full = cov.estimate(A, P, Q, algo="recurrence")
+    ranges, _ = shard.partition_lags(N, M, P, Q, ranks)
+    D = P * Q
+    out = torch.full((D, D), complex(np.nan, np.nan), dtype=tdt, device="cuda")
+    for lo, hi in ranges:
+        buf = torch.full((shard.packed_elements(P, Q, lo, hi),), complex(np.nan, np.nan),
+                         dtype=tdt, device="cuda")
+        shard.device_pack(full, P, Q, lo, hi, buf)
+        torch.cuda.synchronize()
+        want = shard.pack_blocks(full.cpu().numpy(), P, Q, lo, hi).reshape(-1)
+        assert np.array_equal(buf.cpu().numpy(), want)
+        shard.device_unpack(buf, out, P, Q, lo, hi)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), full.cpu().numpy())
+
+
+def test_nccl_allgather_of_one_rank_round_trips():
+    # the collective path of the sharded bench (NCCL, complex viewed as real)
+    # with a one-rank group: the rank's own blocks come back untouched
+    import datetime
+    import socket
+    import torch.distributed as dist
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    store = dist.TCPStore("127.0.0.1", port, 1, True, timeout=datetime.timedelta(seconds=30))
+    pg_was = dist.is_initialized()
+    if not pg_was:
+        dist.init_process_group("nccl", store=store, rank=0, world_size=1)
+    try:
+        N, M, P, Q = 120, 90, 8, 6
+        A = to_dev(wl.complex_normal((N, M), 5, dtype="c64"), torch.complex64)
+        want = cov.estimate(A, P, Q, algo="recurrence")
+        ranges, _ = shard.partition_lags(N, M, P, Q, 1)
+        R = torch.full_like(want, complex(np.nan, np.nan))
+        shard.estimate_shard_into(A, R, P, Q, *ranges[0])
+        shard.allgather_blocks(R, P, Q, ranges, 0)
+        torch.cuda.synchronize()
+        assert np.array_equal(R.cpu().numpy(), want.cpu().numpy())
+    finally:
+        if not pg_was:
+            dist.destroy_process_group()

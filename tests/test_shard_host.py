@@ -223,3 +223,69 @@ def test_two_ranks_assemble_oracle():
 def test_two_ranks_fault_detected(fault, kind):
     res = _run_world(fault)
     assert res.get(0) == f"ShardError:{kind}:1"
+
+
+# ---------------------------------------------------------------------------
+# the collective exchange (one all-gather of padded packed blocks), on gloo
+# ---------------------------------------------------------------------------
+def _rank_allgather(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    try:
+        dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                                world_size=world)
+        N, M, P, Q = SHAPE
+        ranges, _ = shard.partition_lags(N, M, P, Q, world)
+        A = wl.complex_normal((N, M), 99, dtype="c128")
+        D = P * Q
+        R = np.full((D, D), np.nan + 0j, np.complex128)
+        lo, hi = ranges[rank]
+        shard.unpack_blocks(R, _oracle_blocks(A, P, Q, lo, hi), P, Q, lo, hi)
+        Rt = torch.from_numpy(R)
+        shard.allgather_blocks(Rt, P, Q, ranges, rank, pack=shard.host_pack,
+                               unpack=shard.host_unpack)
+        import oracle
+        q.put((rank, "equal" if np.array_equal(Rt.numpy(), oracle.cov_window(A, P, Q))
+               else "differs"))
+        dist.barrier()
+        dist.destroy_process_group()
+    except Exception as e:  # noqa: BLE001 - reported to the parent
+        q.put((rank, f"error:{type(e).__name__}:{e}"))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_allgather_of_packed_blocks_assembles_R_on_every_rank(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_allgather, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    deadline = time.monotonic() + 120
+    while len(res) < world and time.monotonic() < deadline:
+        try:
+            r, msg = q.get(timeout=1.0)
+            res[r] = msg
+        except Exception:  # noqa: BLE001 - queue.Empty
+            pass
+    for p in procs:
+        p.join(timeout=30)
+        if p.is_alive():
+            p.kill()
+            p.join()
+    assert res == {r: "equal" for r in range(world)}
+
+
+def test_packed_sizes_match_the_layout():
+    lib = __import__("paper_1303_2285_gb300").load()
+    import ctypes
+    for P, Q in ((4, 5), (16, 16), (1, 7), (9, 1)):
+        for lo in range(Q + 1):
+            for hi in range(lo, Q + 1):
+                n = ctypes.c_size_t(0)
+                assert lib.cov_shard_packed_size(0, P, Q, lo, hi, ctypes.byref(n)) == 0
+                assert n.value == 8 * shard.packed_elements(P, Q, lo, hi)
+    n = ctypes.c_size_t(0)
+    assert lib.cov_shard_packed_size(0, 4, 5, 3, 2, ctypes.byref(n)) == 1  # empty-reversed range
+    assert lib.cov_shard_packed_size(0, 4, 5, 0, 6, ctypes.byref(n)) == 1  # past Q
