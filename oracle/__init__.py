@@ -14,6 +14,8 @@ Contents
 * ``combinations``  -- the counting and indexing of Section 3 and 4.
 * ``algorithm1``    -- Algorithm 1 in the paper's own steps (pure Python).
 * ``exact``         -- exact Gaussian-integer evaluation of Eq. 2.2.
+* ``capon``         -- the minimum-variance (Capon) spectrum of an estimate
+                       (the downstream use Section 2.3 cites), FP64.
 * ``gram``          -- Eq. 2.2 as the Gram product X X^H of the window vectors
                        (BLAS zherk, FP64): the full-size reference where the
                        window loop would take minutes.

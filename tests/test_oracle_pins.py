@@ -503,3 +503,51 @@ def test_gram_form_closed_forms():
     P, Q = 5, 4
     v = np.array([np.exp(1j * (om * (a % P) + nu * (a // P))) for a in range(P * Q)])
     assert rel_err(cov_gram(A, P, Q), abs(c) ** 2 * np.outer(v, v.conj())) < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# The Capon spectrum (oracle/capon.py), the downstream use of R (Section 2.3).
+# ----------------------------------------------------------------------------
+def test_capon_closed_forms():
+    from oracle.capon import capon_spectrum, steering_vectors
+    P, Q = 4, 3
+    D = P * Q
+    rng = np.random.default_rng(5)
+    A = steering_vectors(P, Q, rng.uniform(-np.pi, np.pi, 9), rng.uniform(-np.pi, np.pi, 9))
+    assert np.allclose(np.abs(A) ** 2, 1.0)
+    # white noise: P = (s2 + d) / ||a||^2 with d = loading * trace / D = loading * s2
+    s2 = 2.5
+    for loading in (0.0, 0.1):
+        got = capon_spectrum(s2 * np.eye(D), A, loading)
+        assert np.allclose(got, (s2 * (1 + loading)) / D, rtol=1e-13)
+    # one source plus noise, Sherman-Morrison:
+    # a^H (v v^H + s2 I)^{-1} a = (||a||^2 - |v^H a|^2 / (s2 + ||v||^2)) / s2
+    v = steering_vectors(P, Q, [0.7], [-1.3])[0] * (1.5 - 0.5j)
+    R = np.outer(v, v.conj()) + s2 * np.eye(D)
+    got = capon_spectrum(R, A)
+    na = np.sum(np.abs(A) ** 2, axis=1)
+    va = A @ v.conj()                       # v^H a_f, conjugated: |.| is the same
+    want = s2 / (na - np.abs(va) ** 2 / (s2 + np.vdot(v, v).real))
+    assert np.allclose(got, want, rtol=1e-12)
+    # the peak is at the source's own steering vector
+    grid = steering_vectors(P, Q, np.linspace(-np.pi, np.pi, 41)[:-1].repeat(40),
+                            np.tile(np.linspace(-np.pi, np.pi, 41)[:-1], 40))
+    spec = capon_spectrum(R, np.vstack([grid, v / np.linalg.norm(v) * np.sqrt(D)]))
+    assert np.argmax(spec) == len(spec) - 1
+
+
+def test_capon_scaling_and_batch():
+    from oracle.capon import capon_spectrum, steering_vectors
+    P, Q = 3, 5
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((P * Q, 40)) + 1j * rng.standard_normal((P * Q, 40))
+    R = X @ X.conj().T / 40
+    A = steering_vectors(P, Q, rng.uniform(-3, 3, 6), rng.uniform(-3, 3, 6))
+    p1 = capon_spectrum(R, A, 0.05)
+    assert np.all(p1 > 0)
+    assert np.allclose(capon_spectrum(3.0 * R, A, 0.05), 3.0 * p1, rtol=1e-12)
+    both = capon_spectrum(np.stack([R, 2 * R]), A, 0.05)
+    assert np.allclose(both[0], p1, rtol=1e-14) and np.allclose(both[1], 2 * p1, rtol=1e-12)
+    # a planted mistake (a^H R a instead of a^H R^{-1} a) fails the closed form
+    bad = 1.0 / np.einsum("fd,de,fe->f", A.conj(), 2.5 * np.eye(P * Q), A).real
+    assert not np.allclose(bad, 2.5 / (P * Q))
