@@ -667,6 +667,8 @@ def bench_ours(args, rank, world, local):
                                                                 fp32_peak)
         line["rows"]["apertures_100x100_of_25x25_w10_f32"] = bench_apertures(
             cov, torch, np, wl, mk_events, stream, fp32_peak, hbm)
+        line["rows"]["capon_spectra_of_10000_apertures"] = bench_capon(cov, torch, np, wl, mk_events,
+                                                                      stream, fp32_peak)
         line["rows"]["diff_b64_256x256_w12_f32"] = bench_adjoint(cov, torch, np, wl, mk_events, stream,
                                                                  fp32_peak)
         line["rows"]["gemm_tf32x3_" + GEMM_WORKLOAD] = bench_gemm(cov, torch, np, wl, mk_events, stream)
@@ -769,6 +771,42 @@ def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak, hbm) -> di
             "distinct_products_per_s": um / (ms * 1e-3), "fp32_fma_frac": 8.0 * um / (ms * 1e-3) / fp32_peak,
             "r_bytes": R.numel() * 8, "r_write_hbm_frac": R.numel() * 8 / (ms * 1e-3) / hbm,
             "graph_captured": True, "tuning": tuning}
+
+
+def bench_capon(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
+    """Minimum-variance (Capon) spectra of the 10,000 aperture estimates (the
+    downstream use of R named in Section 2.3): an 8 x 8 grid of 2-D steering
+    vectors, diagonal loading 0.01 trace(R) / D."""
+    H = W = 1015
+    img = torch.from_numpy(wl.complex_normal((H, W), 77, "c64")).cuda()
+    plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+    plan.upload(ws)
+    plan.run(ws)
+    g = np.linspace(-np.pi, np.pi, 9)[:-1]
+    om, nu = np.repeat(g, 8), np.tile(g, 8)
+    i = np.arange(10)
+    steer_np = np.array([np.exp(1j * (w * i[:, None] + v * i[None, :])).T.reshape(-1)
+                         for w, v in zip(om, nu)]).astype(np.complex64)
+    steer = torch.from_numpy(steer_np).cuda()
+    out = torch.empty((R.shape[0], steer.shape[0]), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        cov.capon_spectrum(R, steer, 0.01, out=out)
+    torch.cuda.synchronize()
+    n = 5
+    ev = mk_events(2 * n)
+    for k in range(n):
+        ev[2 * k].record(stream)
+        cov.capon_spectrum(R, steer, 0.01, out=out)
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n))[n // 2]
+    D, F, cnt = 100, steer.shape[0], R.shape[0]
+    flops = 8.0 * cnt * (D ** 3 / 6 + F * D * D / 2)  # complex MACs of the factorisation and solves
+    return {"matrices": cnt, "D": D, "steering_vectors": F, "ms_per_launch": ms,
+            "spectra_values_per_s": cnt * F / (ms * 1e-3),
+            "fp32_fma_frac": flops / (ms * 1e-3) / fp32_peak,
+            "all_finite": bool(torch.isfinite(out).all())}
 
 
 def bench_adjoint(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:

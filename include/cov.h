@@ -404,6 +404,23 @@ cov_status cov_batched_autotune(cov_batched_plan *plan, void *workspace, size_t 
                                 cov_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Downstream use of the estimates: minimum-variance (Capon) spectra. Section
+ * 2.3 cites the covariance method as the input of the Minimum Variance
+ * Method in SAR imaging (one estimate per aperture of an image) and of the
+ * Capon estimator. For each of `count` matrices R_k (device, COV_C64, D x D,
+ * contiguous, R_k at R + k D^2 complex elements) and each of F steering
+ * vectors a_f (device, F x D complex64, row f = a_f):
+ *     P_k(f) = 1 / (a_f^H (R_k + d_k I)^{-1} a_f),  d_k = loading trace(R_k) / D,
+ * computed by an FP32 Cholesky factorisation of R_k + d_k I in shared memory
+ * (one CTA per matrix) and forward substitution, P = 1 / ||L^{-1} a||^2.
+ * out: device, count x F floats. A matrix whose factorisation meets a
+ * non-positive pivot (R_k + d_k I not positive definite) gets NaN outputs.
+ * 1 <= D <= 128, loading >= 0; COV_EINVAL otherwise. Stream-ordered.
+ * ------------------------------------------------------------------------- */
+cov_status cov_capon_spectrum(const void *R, int count, int D, const void *steer, int F,
+                              float loading, float *out, cov_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Adjoint (not in the paper; the derivative of Eq. 2.2).
  * Given G = dL/dR (PQ x PQ, device, convention dL/dRe + i dL/dIm), writes
  * dA = dL/dA (N x M, device, leading dimension M, same convention):

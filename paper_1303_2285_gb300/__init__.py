@@ -24,7 +24,7 @@ __all__ = ["load", "estimate", "estimate_into", "workspace_size", "plan_info",
            "tuning_get", "tuning_set", "tuning_clear", "tuning_save", "tuning_load",
            "covariance", "estimate_backward", "estimate_backward_batch",
            "backward_workspace_size", "BatchedPlan", "aperture_descs", "aperture_batch",
-           "selftest_timeout", "set_stage_events", "SIGNATURES"]
+           "selftest_timeout", "set_stage_events", "capon_spectrum", "SIGNATURES"]
 
 ALGOS = {"auto": 0, "recurrence": 1, "gemm_tf32x3": 2, "gemm_bf16x3": 3, "direct": 4}
 NORMS = {"mean": 0, "sum": 1}
@@ -113,6 +113,7 @@ SIGNATURES = [
     ("cov_estimate_backward_ex", _I, [_VP, _VP, _I, _I64, _I64, _I, _I, _I, _I, _VP, _VP, _SZ,
                                       _VP]),
     ("cov_selftest_timeout", _I, [_VP, _SZ, ctypes.c_uint32, _VP]),
+    ("cov_capon_spectrum", _I, [_VP, _I, _I, _VP, _I, ctypes.c_float, _VP, _VP]),
     ("cov_partition_lags", _I, [_I64, _I64, _I, _I, _I, ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_int64)]),
     ("cov_estimate_shard", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _I, _I, _VP, _I, _VP, _SZ,
@@ -505,3 +506,26 @@ def check_device_status(workspace, stream=None) -> None:
     """Raises CovError if a kernel recorded a device-side failure in workspace."""
     _check(load().cov_check_device_status(workspace.data_ptr(), _stream_ptr(stream)),
            "device status")
+
+
+def capon_spectrum(R, steer, loading: float = 0.0, out=None, stream=None):
+    """Minimum-variance (Capon) spectra P_k(f) = 1 / (a_f^H (R_k + d_k I)^{-1} a_f)
+    of a batch of estimates R (CUDA complex64, (count, D, D) or (D, D)) for
+    the steering vectors ``steer`` (CUDA complex64, (F, D)); d_k = loading
+    trace(R_k) / D. Returns a (count, F) float32 CUDA tensor."""
+    torch = _torch()
+    if not (R.is_cuda and steer.is_cuda) or R.dtype != torch.complex64 or steer.dtype != torch.complex64:
+        raise ValueError("R and steer must be complex64 CUDA tensors (no CPU fallback)")
+    Rb = R if R.dim() == 3 else R.unsqueeze(0)
+    if not Rb.is_contiguous() or Rb.shape[1] != Rb.shape[2]:
+        raise ValueError("R must be contiguous (count, D, D)")
+    st = steer.contiguous()
+    count, D = Rb.shape[0], Rb.shape[1]
+    if st.dim() != 2 or st.shape[1] != D:
+        raise ValueError("steer must be (F, D)")
+    F = st.shape[0]
+    if out is None:
+        out = torch.empty((count, F), dtype=torch.float32, device=R.device)
+    _check(load().cov_capon_spectrum(Rb.data_ptr(), count, D, st.data_ptr(), F, float(loading),
+                                     out.data_ptr(), _stream_ptr(stream)), "cov_capon_spectrum")
+    return out if R.dim() == 3 else out[0]
