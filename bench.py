@@ -45,9 +45,10 @@ FALLBACK_HBM_GBS = 6800.0
 # the production kernel from one ncu capture (profiles/), keyed by (workload,
 # kernel, hash of the combination path's kernel sources at capture time):
 # null once those sources have changed.
-NCU_TRAFFIC = {  # bytes per launch; profiles/k_fused_*.md, profiles/k_products_inner_*.md
+NCU_TRAFFIC = {  # bytes per launch; profiles/launches_*.md, profiles/k_products_inner_*.md
     ("cn_1024x1024_w16_f32", "k_fused", "96da72e2c97e5ecd"): 8561408,
     ("cn_1024x1024_w16_f32", "k_products_inner", "96da72e2c97e5ecd"): 8438016,
+    ("sar_2048x512_w32_f32", "k_products_inner", "d9ac602c9f27cc69"): 8580000,
 }
 KERNEL_SOURCES = ("cov_device.cuh", "cov_internal.h", "rec_common.cuh", "rec_products.cuh",
                   "rec_products.cu", "rec_fringe.cuh", "rec_fringe.cu", "rec_reduce.cuh",
@@ -994,13 +995,16 @@ def extras(args, cov, torch, np, wl, mk_events, stream) -> dict:
     return out
 
 
-def profile_case(case: str, knobs=None) -> int:
-    """Small cases of the secondary kernels for ncu captures: 600 uneven
-    matrices through the batched launch (seed 3), the dense TF32x3 form on the
-    bench workload, the stencil adjoint of a batch of eight 256 x 256 inputs
-    with a 12 x 12 window, the 30 x 30 apertures of 25 x 25 (stride 10,
-    10 x 10 window) of a 315 x 315 image through the one-warp-per-member
-    kernel."""
+def profile_case(case: str, knobs=None) -> int:  # noqa: C901 - one branch per case
+    """A few launches of one kernel family on a small case, for ncu captures:
+    the single-matrix combination path on the SAR-like 2048 x 512 input (32 x
+    32 window) or on the 1024 x 1024 one (16 x 16), 600 uneven matrices
+    through the batched launch (seed 3), the dense TF32x3 form on the
+    1024 x 1024 workload, the stencil adjoint of a batch of eight 256 x 256
+    inputs with a 12 x 12 window, the 30 x 30 apertures of 25 x 25 (stride
+    10, 10 x 10 window) of a 315 x 315 image through the batched launch's
+    default form, and the Capon spectra of those 900 estimates."""
+    import numpy as np
     import torch
 
     import cov_workloads as wl
@@ -1032,10 +1036,25 @@ def profile_case(case: str, knobs=None) -> int:
     elif case == "apertures":
         img = torch.from_numpy(wl.complex_normal((315, 315), 77, "c64")).cuda()
         plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
+        if knobs:  # the batched plan's form (0, 1 or 2); default: the plan's own
+            plan.set_tuning(int(knobs), 0, 4)
         ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
         plan.upload(ws)
         for _ in range(3):
             plan.run(ws)
+    elif case == "capon":
+        img = torch.from_numpy(wl.complex_normal((315, 315), 77, "c64")).cuda()
+        plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
+        ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+        plan.upload(ws)
+        plan.run(ws)
+        g = np.linspace(-np.pi, np.pi, 9)[:-1]
+        i = np.arange(10)
+        steer = torch.from_numpy(np.array(
+            [np.exp(1j * (w_ * i[:, None] + v_ * i[None, :])).T.reshape(-1)
+             for w_, v_ in zip(np.repeat(g, 8), np.tile(g, 8))]).astype(np.complex64)).cuda()
+        for _ in range(3):
+            cov.capon_spectrum(R, steer, 0.01)
     elif case == "gemm":
         w = wl.WORKLOADS[GEMM_WORKLOAD]
         A = torch.from_numpy(wl.workload_input(w)).cuda()
@@ -1075,7 +1094,8 @@ def main():
     ap.add_argument("--knobs", default=None,
                     help="G,TRB,L,K[,TC]: use these knobs (lag group, rows per task, re-seed interval, "
                          "kernels 1|4, tile columns 32|64) instead of autotuning")
-    ap.add_argument("--profile-case", choices=("sar", "cn", "batched", "gemm", "adjoint", "apertures"),
+    ap.add_argument("--profile-case",
+                    choices=("sar", "cn", "batched", "gemm", "adjoint", "apertures", "capon"),
                     default=None,
                     help="run a few launches of one secondary kernel on a small case (for ncu) "
                          "and exit")
