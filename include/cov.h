@@ -69,8 +69,9 @@ typedef enum {
    * segments are seeded with a direct box sum and walked along the diagonal
    * by adding the entering row of products and subtracting the leaving one;
    * exactly one thread block writes each element of R. FP32 with compensated
-   * running sums for COV_C64, FP64 for COV_C128. Needs N >= 2P-1,
-   * M >= 2Q-1 and P, Q <= 32 (COV_EUNSUPPORTED otherwise). */
+   * running sums for COV_C64, FP64 for COV_C128. Needs P, Q <= 32
+   * (COV_EUNSUPPORTED otherwise); every N >= P, M >= Q is taken, also
+   * where no row (N < 2P-1) or no column (M < 2Q-1) lies in every box. */
   COV_RECURRENCE = 1,
   /* Dense form R = X X^H on the block-Hankel data matrix X (PQ x K, Eq. 2.2)
    * on tcgen05 tensor cores, with split operands and FP32 accumulation.

@@ -110,15 +110,18 @@ cov_status cov_plan_info(int64_t N, int64_t M, int P, int Q, cov_plan_info_t *ou
       const int lo = dc == 0 ? 0 : -(P - 1);
       for (int dr = lo; dr <= P - 1; ++dr) {
         const long long cols_all = M - dc;                  // columns with a valid partner
-        const long long cols_inner = (M - 2LL * Q + 2);     // inner columns
+        const long long cols_inner = p.n_innerc;            // inner columns
         inner += (long long)p.n_inner * cols_all;
         long long rows_f = 0;                               // fringe rows with a valid partner
         for (int k = 0; k < p.NFR; ++k) {
-          const long long n = k < P - 1 ? k : (N - P + 1) + (k - (P - 1));
+          const long long n = fringe_row(P, p.n_inner, k);
           if (n + dr >= 0 && n + dr < N) ++rows_f;
         }
+        long long cols_f = 0;                               // fringe columns with a valid partner
+        for (int k = 0; k < p.NFC; ++k)
+          if (fringe_col(Q, p.n_innerc, k) + dc < M) ++cols_f;
         fringe += rows_f * cols_inner;                       // lane-strided inner columns
-        fringe += rows_f * (2LL * (Q - 1) - dc);             // its own fringe-column products
+        fringe += rows_f * cols_f;                           // its own fringe-column products
       }
     }
     out->products_inner = inner;

@@ -11,9 +11,19 @@
 //   box sum of Pi_D over rows [i, i+N-P] and columns [j, j+M-Q].
 //
 // Work split used by the kernels (rows; columns are analogous):
-//   inner rows  [P-1, N-P]: inside the box of every output of every Delta;
-//   fringe rows [0, P-2] and [N-P+1, N-1] (2(P-1) rows, index fr).
-//   inner cols  [Q-1, M-Q]; fringe cols [0, Q-2] and [M-Q+1, M-1] (index fc).
+//   inner rows  [P-1, N-P]: inside the box of every output of every Delta
+//     (n_inner = max(0, N-2P+2) of them);
+//   fringe rows: every other row, NFR = N - n_inner of them, in row order
+//     (index fr; row n = fr for fr < P-1, else fr + n_inner). A box holds
+//     the inner rows and H = N-P+1 - n_inner consecutive fringe rows: the
+//     fringe rows fr in [i, i+H) for the box starting at row i. With
+//     N >= 2P-1 these are the top rows [i, P-2] and the bottom rows
+//     [N-P+1, N-P+i] (H = P-1); with N < 2P-1 there are no inner rows and
+//     every row is a fringe row (H = N-P+1).
+//   inner cols  [Q-1, M-Q] (n_innerc = max(0, M-2Q+2)); fringe cols fc in
+//     [0, NFC), NFC = M - n_innerc, column m = fc for fc < Q-1 else
+//     fc + n_innerc; the box of column offset j holds the fringe columns
+//     fc in [j, j+HC), HC = M-Q+1 - n_innerc.
 //   Kernel 1 (products_inner): inner rows x all columns. For each Delta the
 //     sum over (inner rows x inner cols) -> core partials; per fringe column
 //     the sum over inner rows -> colsum partials.
@@ -24,10 +34,14 @@
 //     RV[Delta][j][fr] = sum_{m in [j, j+M-Q]} Pi_D[n][m] of each fringe row
 //     (S_in plus the row's own fringe-column products).
 //   Kernel 4 (walk_write): per output block, seed each diagonal segment with
-//     the direct sum CV + sum of RV over the fringe rows inside the box, walk
-//     down the diagonal by subtracting the leaving top row and adding the
-//     entering bottom row (re-seeding every L steps), divide by K and write
-//     the block and its conjugate mirror with coalesced stores.
+//     the direct sum CV + sum of RV over the H fringe rows inside the box,
+//     walk down the diagonal by subtracting the leaving row fr = i and adding
+//     the entering row fr = i + H (re-seeding every L steps), divide by K and
+//     write the block and its conjugate mirror with coalesced stores.
+//   Without inner rows the product kernel has no work (CV = 0); without
+//   inner columns the fringe-row kernel has none (S_in = 0) and the box sums
+//   over the fringe columns are direct window sums instead of the suffix /
+//   prefix scans used when the box holds Q-1 of them.
 #pragma once
 
 #include <stdint.h>
@@ -41,6 +55,7 @@
 namespace cov {
 
 constexpr int kMaxPQ = 32;       // recurrence path: P, Q <= 32 (smem tile fits)
+
 constexpr int kWsHeader = 256;   // status word + padding at the workspace head
 
 // Status codes written by kernels into the workspace status word.
@@ -64,6 +79,10 @@ COV_HD void combo_of(int P, int idx, int &dr, int &dc) {
     dr = k % (2 * P - 1) - (P - 1);
   }
 }
+
+// Fringe row fr -> row of A, fringe column fc -> column of A.
+COV_HD int fringe_row(int P, int n_inner, int fr) { return fr < P - 1 ? fr : fr + n_inner; }
+COV_HD int fringe_col(int Q, int n_innerc, int fc) { return fc < Q - 1 ? fc : fc + n_innerc; }
 
 // Lag groups: consecutive dr values of one dc, G per group. Group g gives
 // (dc, d0, cnt): lags dr = d0 .. d0+cnt-1 (cnt <= G). The G - cnt unused
@@ -119,7 +138,9 @@ struct RecParams {
   int G;                // lags per group
   int ngroups;
   int inner_lo;         // P-1
-  int n_inner;          // N-2P+2
+  int n_inner;          // max(0, N-2P+2) inner rows
+  int n_innerc;         // max(0, M-2Q+2) inner columns
+  int H, HC;            // fringe rows / fringe columns inside one box
   int TRB;              // rows per warp task (one partial row block)
   int TPT;              // row blocks per smem tile
   int TR, TC, CBT;      // tile rows (TRB*TPT), tile cols (64), 32-col blocks per tile
@@ -130,7 +151,7 @@ struct RecParams {
   int use_tma;          // stage tiles with TMA (set at launch)
   long long tasks_per_tile, n_tasks;
   // fringe-row kernel
-  int NFR, NFC;         // 2(P-1), 2(Q-1)
+  int NFR, NFC;         // N - n_inner, M - n_innerc (2(P-1), 2(Q-1) when both >= 0)
   int GF, ngroups_f, RB, nrb;
   int CWF, NCH;         // inner-column chunk width and count of the fringe-row kernel
   int FPB;              // its (fringe row, row lag) pairs per CTA (= threads)

@@ -33,8 +33,8 @@ long long distinct_products(long long N, long long M, int P, int Q) {
 }
 
 bool recurrence_ok(long long N, long long M, int P, int Q) {
-  return P >= 1 && Q >= 1 && P <= kMaxPQ && Q <= kMaxPQ && N >= 2LL * P - 1 &&
-         M >= 2LL * Q - 1 && N < (1LL << 30) && M < (1LL << 30);
+  return P >= 1 && Q >= 1 && P <= kMaxPQ && Q <= kMaxPQ && N >= P && M >= Q &&
+         N < (1LL << 30) && M < (1LL << 30);
 }
 
 int choose_group(int P, int Q, int elem) {
@@ -68,7 +68,14 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   if (t.G == 4 || t.G == 8 || (t.G == 16 && elem == 8)) p.G = t.G;
   p.ngroups = n_groups(P, Q, p.G);
   p.inner_lo = P - 1;
-  p.n_inner = (int)(N - 2LL * P + 2);
+  // inner rows / columns (none where N < 2P-1 / M < 2Q-1), the fringe rows
+  // and columns, and how many of them one box holds
+  p.n_inner = N >= 2LL * P - 1 ? (int)(N - 2LL * P + 2) : 0;
+  p.n_innerc = M >= 2LL * Q - 1 ? (int)(M - 2LL * Q + 2) : 0;
+  p.NFR = (int)(N - p.n_inner);
+  p.NFC = (int)(M - p.n_innerc);
+  p.H = (int)(N - P + 1 - p.n_inner);
+  p.HC = (int)(M - Q + 1 - p.n_innerc);
   p.d_lo = group_lag_lo(P, Q);
   p.d_hi = group_lag_hi(P, Q, p.G);
   const int span = p.d_hi - p.d_lo;
@@ -110,26 +117,24 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   if (TRB < 8) TRB = 8;
   int TPT = (int)(tr_max / TRB);
   if (TPT > 4) TPT = 4;
-  if (TPT < 1) TPT = 1;
   p.TRB = TRB;
-  p.n_rb = (p.n_inner + TRB - 1) / TRB;
+  p.n_rb = (p.n_inner + TRB - 1) / TRB;  // 0 without inner rows: no product tasks
   if (TPT > p.n_rb) TPT = p.n_rb;
+  if (TPT < 1) TPT = 1;
   p.TPT = TPT;
   p.TR = TRB * TPT;
   p.n_rt = (p.n_rb + TPT - 1) / TPT;
   p.STR = p.TR + span;
   p.tasks_per_tile = (long long)p.ngroups * p.CBT * p.TPT;
   p.n_tasks = (long long)p.n_rt * p.n_ct * p.tasks_per_tile;
-  // fringe rows
-  p.NFR = 2 * (P - 1);
-  p.NFC = 2 * (Q - 1);
+  // fringe rows (NFR, NFC set above)
   p.GF = 8;
   p.RB = 4;
   p.ngroups_f = n_groups(P, Q, p.GF);
   p.nrb = (P - 1 + p.RB - 1) / p.RB;
   p.CWF = elem == 16 ? 8 : 32;
   p.FPB = elem == 16 ? 32 : 256;
-  p.NCH = (int)((M - 2LL * Q + 2 + p.CWF - 1) / p.CWF);
+  p.NCH = (p.n_innerc + p.CWF - 1) / p.CWF;  // 0 without inner columns
   p.QMAXF = Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
   p.FPITCH = ((p.CWF + p.QMAXF - 1 + 14) / 16) * 16 + 1;  // >= CWF+QMAXF-1, = 1 mod 16
   p.L = (t.L >= 1 && t.L <= kMaxPQ) ? t.L : 8;

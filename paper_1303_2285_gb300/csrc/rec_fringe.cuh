@@ -23,8 +23,10 @@ namespace cov {
 
 // Stages the strip of A that chunk cc of side `side` reads (rows
 // [row0, row0 + 2P - 2), FPITCH columns from the chunk's first column; zero
-// outside A) with cp.async by all threads of the CTA, and waits for the
-// calling thread's copies. The caller synchronises the CTA before reading.
+// outside A, including the rows above A that the bottom side's strip starts
+// with where N < 2P-2) with cp.async by all threads of the CTA, and waits for
+// the calling thread's copies. The caller synchronises the CTA before
+// reading.
 template <typename T>
 __device__ __forceinline__ void fringe_stage(const RecParams &p, typename C2t<T>::type *S, int side,
                                              int cc) {
@@ -61,8 +63,9 @@ __device__ __forceinline__ void fringe_pair(const RecParams &p, const typename C
   const int row0 = side == 0 ? 0 : N - 2 * P + 2;
   const int SP = p.FPITCH;
   const int r = t % (P - 1), dr = t / (P - 1) - (P - 1);
-  const int n = side == 0 ? r : (N - P + 1) + r;
   const int fr = side * (P - 1) + r;
+  if (fr >= p.NFR) return;  // N < 2P-1: the bottom side has N-P+1 rows
+  const int n = fringe_row(P, p.n_inner, fr);
   const int nb = n + dr;
   C2 acc[QMAX];
 #pragma unroll

@@ -164,7 +164,7 @@ __device__ __forceinline__ void product_task(const RecParams &p, long long tile,
   const bool in_range = m < p.M;
   const bool inner = (m >= p.Q - 1) && (m <= p.M - p.Q);
   if (in_range && !inner) {
-    const int fc = (m < p.Q - 1) ? m : m - (p.M - 2 * p.Q + 2);
+    const int fc = (m < p.Q - 1) ? m : m - p.n_innerc;
     C2 *cs = (C2 *)p.colsum_part;
 #pragma unroll
     for (int k = 0; k < G; ++k)

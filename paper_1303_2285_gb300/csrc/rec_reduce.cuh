@@ -138,7 +138,7 @@ __device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int 
   const C2 *sin_d = (const C2 *)p.sin_part + (long long)D * NCH * NFR;
   C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR;
   for (int fr = lane; fr < NFR; fr += 32) {
-    const int n = fr < P - 1 ? fr : (p.N - P + 1) + (fr - (P - 1));
+    const int n = fringe_row(P, p.n_inner, fr);
     const bool rowok = n + dr >= 0 && n + dr < p.N;
     // S_in: four interleaved partial sums over the chunks, 16 loads in
     // flight per round
@@ -250,10 +250,12 @@ template <typename T>
 __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *sm) {
   using C2 = typename C2t<T>::type;
   const int P = p.P, Q = p.Q, NFR = p.NFR, NFC = p.NFC, NCH = p.NCH, n_rb = p.n_rb;
-  const int W = p.M - p.Q + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int S = red_cs_slices(NFC, n_rb), S2 = red_sin_slices(NFR, NCH);
   const RedSmem<T> L(NFR, NFC, S, S2);
+  // the box of a column offset holds Q - 1 fringe columns (M >= 2Q - 2):
+  // suffix / prefix scans; else (M < 2Q - 2) direct window sums of HC
+  const bool scan_form = NFC == 2 * (Q - 1);
   int dr, dc;
   combo_of(P, D, dr, dc);
   const int J = Q - dc;
@@ -327,36 +329,35 @@ __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *s
     o.y = si;
     ((C2 *)(sm + L.sin_part))[s0 * NFR + fr] = o;
   }
-  // the fringe-row x fringe-column products, each formed once: warp w takes
-  // the fringe rows w, w + 8, ...; lane k the left column k and the right
-  // column W + k (the lanes' loads of a row are contiguous)
+  // the fringe-row x fringe-column products, each formed once (zero where
+  // the partner falls outside A): warp w takes the fringe rows w, w + 8, ...;
+  // lane k the fringe columns k and k + 32 (NFC <= 62)
   {
     const C2 *A = (const C2 *)p.A;
     C2 *prod = (C2 *)(sm + L.prod);
     const int PS = red_prod_stride(NFC);
-    if (lane < Q - 1) {
+    const int m0 = fringe_col(Q, p.n_innerc, lane), m1 = fringe_col(Q, p.n_innerc, lane + 32);
+    const bool c0 = lane < NFC && m0 + dc < p.M, c1 = lane + 32 < NFC && m1 + dc < p.M;
 #pragma unroll 2
-      for (int fr = warp; fr < NFR; fr += kRedThreads / 32) {
-        const int n = fr < P - 1 ? fr : (p.N - P + 1) + (fr - (P - 1));
-        const bool rowok = n + dr >= 0 && n + dr < p.N;
-        const C2 *An = A + (long long)n * p.lda;
-        const C2 *Ab = A + (long long)(n + dr) * p.lda + dc;
-        const bool rok = rowok && W + lane + dc < p.M;
-        C2 a0 = czero<C2>(), b0 = czero<C2>(), a1 = czero<C2>(), b1 = czero<C2>();
-        if (rowok) {
-          a0 = __ldg(An + lane);
-          b0 = __ldg(Ab + lane);
-        }
-        if (rok) {
-          a1 = __ldg(An + W + lane);
-          b1 = __ldg(Ab + W + lane);
-        }
-        C2 vl = czero<C2>(), vr = czero<C2>();
-        cmac_conj(vl, a0, b0);
-        cmac_conj(vr, a1, b1);
-        prod[fr * PS + lane] = vl;
-        prod[fr * PS + Q - 1 + lane] = vr;
+    for (int fr = warp; fr < NFR; fr += kRedThreads / 32) {
+      const int n = fringe_row(P, p.n_inner, fr);
+      const bool rowok = n + dr >= 0 && n + dr < p.N;
+      const C2 *An = A + (long long)n * p.lda;
+      const C2 *Ab = A + (long long)(n + dr) * p.lda + dc;
+      C2 a0 = czero<C2>(), b0 = czero<C2>(), a1 = czero<C2>(), b1 = czero<C2>();
+      if (rowok && c0) {
+        a0 = __ldg(An + m0);
+        b0 = __ldg(Ab + m0);
       }
+      if (rowok && c1) {
+        a1 = __ldg(An + m1);
+        b1 = __ldg(Ab + m1);
+      }
+      C2 v0 = czero<C2>(), v1 = czero<C2>();
+      cmac_conj(v0, a0, b0);
+      cmac_conj(v1, a1, b1);
+      if (lane < NFC) prod[fr * PS + lane] = v0;
+      if (lane + 32 < NFC) prod[fr * PS + lane + 32] = v1;
     }
   }
   __syncthreads();
@@ -410,76 +411,113 @@ __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *s
   const int NL = Q - 1;                              // fringe columns per side
   const int SEG = (NL + kRedSeg - 1) / kRedSeg;      // columns per segment
   const int q = tid / 64, fr = tid % 64;
-  const int k0 = q * SEG, k1 = (k0 + SEG < NL) ? k0 + SEG : NL;
-  const C2 *row = (const C2 *)(sm + L.prod) + fr * red_prod_stride(NFC);
-  C2 *tot = (C2 *)(sm + L.tot);
-  if (fr < NFR) {
-    C2 sl = czero<C2>(), sr = czero<C2>();
-    for (int k = k0; k < k1; ++k) {
-      sl.x += row[k].x;
-      sl.y += row[k].y;
-      sr.x += row[NL + k].x;
-      sr.y += row[NL + k].y;
-    }
-    tot[2 * (q * NFR + fr)] = sl;
-    tot[2 * (q * NFR + fr) + 1] = sr;
-  }
-  __syncthreads();
-  if (fr < NFR) {
-    // carries: the left sums of the later segments (suffix) and the right
-    // sums of the earlier ones (prefix)
-    C2 cl = czero<C2>(), cr = czero<C2>();
-    for (int qq = kRedSeg - 1; qq > q; --qq) {
-      cl.x += tot[2 * (qq * NFR + fr)].x;
-      cl.y += tot[2 * (qq * NFR + fr)].y;
-    }
-    for (int qq = 0; qq < q; ++qq) {
-      cr.x += tot[2 * (qq * NFR + fr) + 1].x;
-      cr.y += tot[2 * (qq * NFR + fr) + 1].y;
-    }
-    const C2 s_in = ((const C2 *)(sm + L.sin))[fr];
-    C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR + fr;
-    // prefix of the right products at j = k0 is cr; the suffix of the left
-    // ones at j = k is cl + the segment's left values from k on
-    C2 suf[8];
-    {
-      C2 acc = cl;
-#pragma unroll
-      for (int u = 7; u >= 0; --u) {
-        if (k0 + u < k1) {
-          acc.x += row[k0 + u].x;
-          acc.y += row[k0 + u].y;
+  if (!scan_form) {
+    // window form: thread (q, fr) takes the column offsets j = q, q + 4, ...
+    if (fr < NFR) {
+      const C2 *row = (const C2 *)(sm + L.prod) + fr * red_prod_stride(NFC);
+      const C2 s_in = ((const C2 *)(sm + L.sin))[fr];
+      C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR + fr;
+      for (int j = q; j < J; j += kRedSeg) {
+        C2 w = czero<C2>();
+        for (int k = j; k < j + p.HC; ++k) {
+          w.x += row[k].x;
+          w.y += row[k].y;
         }
-        suf[u] = acc;
+        C2 o;
+        o.x = s_in.x + w.x;
+        o.y = s_in.y + w.y;
+        rv[(long long)j * NFR] = o;
       }
     }
-    C2 pre = cr;
+  } else {
+    const int k0 = q * SEG, k1 = (k0 + SEG < NL) ? k0 + SEG : NL;
+    const C2 *row = (const C2 *)(sm + L.prod) + fr * red_prod_stride(NFC);
+    C2 *tot = (C2 *)(sm + L.tot);
+    if (fr < NFR) {
+      C2 sl = czero<C2>(), sr = czero<C2>();
+      for (int k = k0; k < k1; ++k) {
+        sl.x += row[k].x;
+        sl.y += row[k].y;
+        sr.x += row[NL + k].x;
+        sr.y += row[NL + k].y;
+      }
+      tot[2 * (q * NFR + fr)] = sl;
+      tot[2 * (q * NFR + fr) + 1] = sr;
+    }
+    __syncthreads();
+    if (fr < NFR) {
+      // carries: the left sums of the later segments (suffix) and the right
+      // sums of the earlier ones (prefix)
+      C2 cl = czero<C2>(), cr = czero<C2>();
+      for (int qq = kRedSeg - 1; qq > q; --qq) {
+        cl.x += tot[2 * (qq * NFR + fr)].x;
+        cl.y += tot[2 * (qq * NFR + fr)].y;
+      }
+      for (int qq = 0; qq < q; ++qq) {
+        cr.x += tot[2 * (qq * NFR + fr) + 1].x;
+        cr.y += tot[2 * (qq * NFR + fr) + 1].y;
+      }
+      const C2 s_in = ((const C2 *)(sm + L.sin))[fr];
+      C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR + fr;
+      // prefix of the right products at j = k0 is cr; the suffix of the left
+      // ones at j = k is cl + the segment's left values from k on
+      C2 suf[8];
+      {
+        C2 acc = cl;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int j = k0 + u;
-      if (j < k1) {
-        if (j < J) {
-          C2 o;
-          o.x = s_in.x + suf[u].x + pre.x;
-          o.y = s_in.y + suf[u].y + pre.y;
-          rv[(long long)j * NFR] = o;
+        for (int u = 7; u >= 0; --u) {
+          if (k0 + u < k1) {
+            acc.x += row[k0 + u].x;
+            acc.y += row[k0 + u].y;
+          }
+          suf[u] = acc;
         }
-        pre.x += row[NL + j].x;
-        pre.y += row[NL + j].y;
+      }
+      C2 pre = cr;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = k0 + u;
+        if (j < k1) {
+          if (j < J) {
+            C2 o;
+            o.x = s_in.x + suf[u].x + pre.x;
+            o.y = s_in.y + suf[u].y + pre.y;
+            rv[(long long)j * NFR] = o;
+          }
+          pre.x += row[NL + j].x;
+          pre.y += row[NL + j].y;
+        }
+      }
+      // the last column offset j = Q - 1 (only dc = 0 has it): no left fringe
+      // column in its box, every right one
+      if (q == kRedSeg - 1 && J == Q) {
+        C2 o;
+        o.x = s_in.x + T(0) + pre.x;
+        o.y = s_in.y + T(0) + pre.y;
+        rv[(long long)(Q - 1) * NFR] = o;
       }
     }
-    // the last column offset j = Q - 1 (only dc = 0 has it): no left fringe
-    // column in its box, every right one
-    if (q == kRedSeg - 1 && J == Q) {
-      C2 o;
-      o.x = s_in.x + T(0) + pre.x;
-      o.y = s_in.y + T(0) + pre.y;
-      rv[(long long)(Q - 1) * NFR] = o;
-    }
-  }
+  }  // scan form
 
   // ---- 4. CV (warp 0) ----------------------------------------------------
-  if (warp == 0) {
+  if (warp == 0 && !scan_form) {
+    // window form: lane j sums the HC fringe-column sums of its box
+    if (lane < J) {
+      Neu<T> vr, vi;
+      const T *o = sm + L.core_tot;
+      vr.merge(o[0], o[1]);
+      vi.merge(o[2], o[3]);
+      const C2 *CS = (const C2 *)(sm + L.cs);
+      for (int k = lane; k < lane + p.HC; ++k) {
+        vr.add(CS[k].x);
+        vi.add(CS[k].y);
+      }
+      C2 v;
+      v.x = vr.value();
+      v.y = vi.value();
+      ((C2 *)p.colval)[(long long)D * Q + lane] = v;
+    }
+  } else if (warp == 0) {
     Neu<T> vr, vi;
     {
       const T *o = sm + L.core_tot;
@@ -584,15 +622,16 @@ __device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, u
     const int ie = (i0 + I) < (is + p.L) ? (i0 + I) : (is + p.L);
     const C2 *RV = RVs + (dr + P - 1) * NFR;
     const C2 cv = CVs[dr + P - 1];
-    // seed: the direct sum over the box of output (is, bj): the top fringe
-    // rows n in [is, P-2] and the bottom fringe rows N-P+1+k, k < is, i.e.
-    // the staged entries RV[is .. is+P-2], one contiguous range; two
-    // interleaved compensated sums (independent chains), merged
+    // seed: the direct sum over the box of output (is, bj): its H fringe
+    // rows fr in [is, is + H) (with inner rows, the top rows n in [is, P-2]
+    // and the bottom rows N-P+1+k, k < is), one contiguous range of the
+    // staged entries; two interleaved compensated sums (independent
+    // chains), merged
     Neu<T> orr, oii, o2r, o2i;
     orr.add(cv.x);
     oii.add(cv.y);
     {
-      const int ue = is + P - 1;
+      const int ue = is + p.H;
       int u = is;
       for (; u + 2 <= ue; u += 2) {
         const C2 a = RV[u], b = RV[u + 1];
@@ -624,11 +663,11 @@ __device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, u
       o.x = re;
       o.y = im;
       B[i * PP + i + dr] = o;
-      if (i + 1 < ie) {  // walk: row i leaves the box, row i+N-P+1 enters
+      if (i + 1 < ie) {  // walk: fringe row i leaves the box, fringe row i + H enters
         orr.add(-RV[i].x);
         oii.add(-RV[i].y);
-        orr.add(RV[P - 1 + i].x);
-        oii.add(RV[P - 1 + i].y);
+        orr.add(RV[p.H + i].x);
+        oii.add(RV[p.H + i].y);
       }
     }
   }

@@ -136,10 +136,13 @@ cudaError_t launch_recurrence(const RecParams &p, bool fp64, int num_sms, cudaSt
     cudaGetLastError();  // not co-resident here: the four kernels below
   }
   if ((e = mark(0)) != cudaSuccess) return e;
-  if (q.n_inner > 0 && q.n_tasks > 0 && (e = launch_products_any(q, tmap, fp64, num_sms, s)) != cudaSuccess)
-    return e;
+  // Without inner rows there is no product kernel; the fringe-row kernel,
+  // which reads A before its dependency wait, is then launched without PDL
+  // so that it cannot overlap the stream's earlier work.
+  const bool products = q.n_inner > 0 && q.n_tasks > 0;
+  if (products && (e = launch_products_any(q, tmap, fp64, num_sms, s)) != cudaSuccess) return e;
   if ((e = mark(1)) != cudaSuccess) return e;
-  if ((e = launch_fringe(q, fp64, s, pdl)) != cudaSuccess) return e;
+  if ((e = launch_fringe(q, fp64, s, pdl && products)) != cudaSuccess) return e;
   if ((e = mark(2)) != cudaSuccess) return e;
   if ((e = launch_reduce(q, fp64, s, pdl)) != cudaSuccess) return e;
   if ((e = mark(3)) != cudaSuccess) return e;

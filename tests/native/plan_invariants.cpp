@@ -1,5 +1,6 @@
 // Host-only invariants of the combination path's plan (plan.cpp), over a
-// sweep of shapes, element sizes and tuned knobs: tiles cover the inner rows
+// sweep of shapes (with and without inner rows and columns), element sizes
+// and tuned knobs: tiles cover the inner rows
 // and all columns; the staged tile holds every partner row and column of its
 // tasks and its two buffers fit the shared memory the kernels request; the
 // workspace regions are 256-byte aligned, disjoint and large enough for the
@@ -35,7 +36,15 @@ static void check_plan(long long N, long long M, int P, int Q, int elem, const T
   CHECK(p.d_lo == (Q > 1 ? -(P - 1) : 0), "d_lo %d", p.d_lo);
   CHECK(p.d_hi >= P - 1, "d_hi %d", p.d_hi);
   // row tiling of the inner rows [P-1, N-P]
-  CHECK(p.n_inner == N - 2 * P + 2, "n_inner %d", p.n_inner);
+  CHECK(p.n_inner == (N >= 2 * P - 1 ? N - 2 * P + 2 : 0), "n_inner %d", p.n_inner);
+  CHECK(p.n_innerc == (M >= 2 * Q - 1 ? M - 2 * Q + 2 : 0), "n_innerc %d", p.n_innerc);
+  // fringe rows / columns and the share of them inside one box
+  CHECK(p.NFR == N - p.n_inner && p.NFC == M - p.n_innerc, "NFR/NFC");
+  CHECK(p.NFR <= 2 * (P - 1) && p.NFC <= 2 * (Q - 1), "NFR %d NFC %d above the fringe", p.NFR, p.NFC);
+  CHECK(p.H == N - P + 1 - p.n_inner && p.HC == M - Q + 1 - p.n_innerc, "H/HC");
+  CHECK(p.H >= 0 && p.H <= P - 1 && p.HC >= 0 && p.HC <= Q - 1, "H %d HC %d", p.H, p.HC);
+  // the last walk step of the longest segment reads fringe row (P - 2) + H
+  CHECK(P == 1 || P - 2 + p.H < p.NFR || p.NFR == 0, "walk reads past the fringe rows");
   CHECK(p.TRB >= 8 && p.TRB % 8 == 0, "TRB %d", p.TRB);
   CHECK((long long)p.n_rb * p.TRB >= p.n_inner && (long long)(p.n_rb - 1) * p.TRB < p.n_inner,
         "n_rb %d", p.n_rb);
@@ -57,9 +66,8 @@ static void check_plan(long long N, long long M, int P, int Q, int elem, const T
   CHECK(p.n_tasks == (long long)p.n_rt * p.n_ct * p.tasks_per_tile, "n_tasks");
   CHECK(p.ngroups == n_groups(P, Q, p.G), "ngroups");
   // fringe-row stage
-  CHECK(p.NFR == 2 * (P - 1) && p.NFC == 2 * (Q - 1), "NFR/NFC");
   CHECK(p.QMAXF >= Q, "QMAXF %d", p.QMAXF);
-  CHECK((long long)p.NCH * p.CWF >= M - 2 * Q + 2, "NCH %d", p.NCH);
+  CHECK((long long)p.NCH * p.CWF >= p.n_innerc && (p.NCH == 0) == (p.n_innerc == 0), "NCH %d", p.NCH);
   CHECK(p.FPITCH >= p.CWF + p.QMAXF - 1 && p.FPITCH % 16 == 1, "FPITCH %d", p.FPITCH);
   CHECK(p.L >= 1 && p.L <= kMaxPQ, "L %d", p.L);
   CHECK(p.div_double == (elem == 8 && p.K > (1LL << 24) ? 1 : 0), "div_double");
@@ -98,11 +106,12 @@ int main() {
   for (P = 1; P <= 32; P += (P < 8 ? 1 : 3))
     for (Q = 1; Q <= 32; Q += (Q < 8 ? 1 : 5))
       for (elem = 8; elem <= 16; elem += 8) {
-        const long long sizes[4] = {2LL * P - 1, 2LL * P + 37, 300, 1024};
+        // shapes with and without inner rows / columns (N < 2P - 1, M < 2Q - 1)
+        const long long sizes[6] = {P, 2LL * P - 2, 2LL * P - 1, 2LL * P + 37, 300, 1024};
         for (long long n : sizes)
-          for (long long m : {2LL * Q - 1, 2LL * Q + 70, 1000LL}) {
-            N = n < 2LL * P - 1 ? 2LL * P - 1 : n;
-            M = m < 2LL * Q - 1 ? 2LL * Q - 1 : m;
+          for (long long m : {(long long)Q, 2LL * Q - 2, 2LL * Q - 1, 2LL * Q + 70, 1000LL}) {
+            N = n < P ? P : n;
+            M = m < Q ? Q : m;
             check_plan(N, M, P, Q, elem, nullptr);
             for (const Tuning &t : knobs) check_plan(N, M, P, Q, elem, &t);
           }

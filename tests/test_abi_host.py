@@ -55,11 +55,15 @@ def test_plan_counts_match_oracle(N, M, P, Q):
     assert info["r_elements"] == (P * Q) ** 2
     D = P * Q
     assert info["naive_macs"] == info["K"] * D * (D + 1) // 2
-    assert info["recurrence_ok"] == int(N >= 2 * P - 1 and M >= 2 * Q - 1 and P <= 32 and Q <= 32)
+    # the combination path takes every shape with P, Q <= 32, including those
+    # without inner rows (N < 2P - 1) or inner columns (M < 2Q - 1)
+    assert info["recurrence_ok"] == int(P <= 32 and Q <= 32)
 
 
 @pytest.mark.parametrize("N,M,P,Q", [(64, 64, 8, 8), (1024, 1024, 16, 16), (2048, 512, 32, 32),
-                                     (33, 70, 3, 11), (15, 31, 8, 16)])
+                                     (33, 70, 3, 11), (15, 31, 8, 16), (9, 9, 9, 9), (7, 30, 5, 3),
+                                     (30, 7, 2, 6), (12, 12, 7, 7), (5, 5, 1, 5), (62, 900, 32, 4),
+                                     (40, 40, 32, 32)])
 def test_plan_products_cover_um(N, M, P, Q):
     # Every distinct product is formed by exactly one of the two product
     # kernels; the rest of UM is the fringe-row x fringe-column corner
@@ -72,9 +76,10 @@ def test_workspace_sizes():
     n1 = cov.workspace_size("c64", 1024, 1024, 16, 16, "recurrence")
     n2 = cov.workspace_size("c128", 1024, 1024, 16, 16, "recurrence")
     assert n1 > 256 and n1 % 256 == 0 and n2 > n1
-    assert cov.workspace_size("c64", 9, 9, 9, 9, "auto") == 256  # direct path
+    assert cov.workspace_size("c64", 40, 40, 33, 1, "auto") == 256  # direct path (P > 32)
+    assert cov.workspace_size("c64", 9, 9, 9, 9, "auto") > 256  # no inner rows or columns
     with pytest.raises(cov.CovError) as e:
-        cov.workspace_size("c64", 9, 9, 9, 9, "recurrence")
+        cov.workspace_size("c64", 40, 40, 33, 1, "recurrence")
     assert e.value.code == 5
 
 
@@ -96,7 +101,7 @@ def test_argument_checks_fail_before_cuda():
     assert lib.cov_estimate_ex(fake, 0, 64, 64, 64, 8, 8, fake, 1, 0,
                                ctypes.c_void_p(0x1008), 1 << 30, None) == 3
     # recurrence on a shape it does not take
-    assert lib.cov_estimate_ex(fake, 0, 9, 9, 9, 9, 9, fake, 1, 0, None, 0, None) == 5
+    assert lib.cov_estimate_ex(fake, 0, 40, 40, 40, 33, 1, fake, 1, 0, None, 0, None) == 5
     info = cov.PlanInfo()
     assert lib.cov_plan_info(0, 5, 1, 1, ctypes.byref(info)) == 1
     assert lib.cov_plan_info(5, 5, 1, 1, None) == 1

@@ -61,5 +61,5 @@ def test_quarter_million_apertures_plan():
     assert arr[n - 1].R == R + (n - 1) * 100 * 100 * 8
     assert arr[n - 1].A == img + (498 * 16 * 8000 + 498 * 16) * 8
     plan = cov.BatchedPlan(None, descs=arr)
-    assert plan.tuning["form"] == 1
+    assert plan.tuning["form"] == 2  # the box form: 25 x 25 apertures, 10 x 10 windows
     assert plan.workspace_bytes >= n * ctypes.sizeof(cov.CovDesc)

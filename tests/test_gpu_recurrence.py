@@ -29,6 +29,17 @@ SHAPES = [
     (300, 101, 2, 2), (95, 95, 32, 32), (63, 70, 32, 3),
 ]
 
+# shapes without inner rows (N < 2P-1) or inner columns (M < 2Q-1), or both:
+# every row / column is a fringe one. N = 2P-2 and M = 2Q-2 keep the scan
+# form of the column sums with no inner column; below that the window form;
+# a single window (N = P, M = Q); wide and tall ones put every product in the
+# fringe-row kernel or the product kernel's column sums.
+SHORT_SHAPES = [
+    (9, 9, 9, 9), (7, 30, 5, 3), (30, 7, 2, 6), (12, 12, 7, 7), (5, 5, 1, 5), (14, 16, 8, 9),
+    (40, 40, 32, 32), (32, 32, 32, 32), (40, 3000, 32, 4), (3000, 40, 4, 32), (62, 600, 32, 20),
+    (5, 200, 3, 2), (200, 5, 2, 3), (1, 40, 1, 32),
+]
+
 
 def run(A_np, P, Q, dtype, algo="recurrence", norm="mean"):
     A = to_dev(A_np, dtype)
@@ -43,7 +54,7 @@ def run(A_np, P, Q, dtype, algo="recurrence", norm="mean"):
     return R.cpu().numpy()
 
 
-@pytest.mark.parametrize("N,M,P,Q", SHAPES)
+@pytest.mark.parametrize("N,M,P,Q", SHAPES + SHORT_SHAPES)
 def test_f64_integer_bit_exact(oracle_mod, N, M, P, Q):
     A = wl.integer_valued((N, M), 2285 + N + 7 * M)
     for norm in ("mean", "sum"):
@@ -52,7 +63,7 @@ def test_f64_integer_bit_exact(oracle_mod, N, M, P, Q):
         assert np.array_equal(got, want), f"max diff {np.abs(got - want).max()}"
 
 
-@pytest.mark.parametrize("N,M,P,Q", SHAPES)
+@pytest.mark.parametrize("N,M,P,Q", SHAPES + SHORT_SHAPES)
 def test_f64_gaussian(oracle_mod, N, M, P, Q):
     A = wl.complex_normal((N, M), 1303 + N + M)
     got = run(A, P, Q, torch.complex128)
@@ -62,7 +73,7 @@ def test_f64_gaussian(oracle_mod, N, M, P, Q):
     assert np.all(got.diagonal().imag == 0)
 
 
-@pytest.mark.parametrize("N,M,P,Q", SHAPES)
+@pytest.mark.parametrize("N,M,P,Q", SHAPES + SHORT_SHAPES)
 def test_f32_gaussian(oracle_mod, N, M, P, Q):
     A = wl.complex_normal((N, M), 1 + N * M, dtype="c64")
     got = run(A, P, Q, torch.complex64)
@@ -84,14 +95,36 @@ def test_f32_integer_exact(oracle_mod, N, M, P, Q):
     assert np.array_equal(run(A, P, Q, torch.complex64, norm="mean"), want.astype(np.complex64))
 
 
-@pytest.mark.parametrize("N,M,P,Q", [(9, 9, 9, 9), (7, 30, 5, 3), (30, 7, 2, 6), (12, 12, 7, 7), (5, 5, 1, 5)])
-def test_auto_on_shapes_the_recurrence_does_not_take(oracle_mod, N, M, P, Q):
+@pytest.mark.parametrize("N,M,P,Q", [(9, 9, 9, 9), (7, 30, 5, 3), (30, 7, 2, 6), (12, 12, 7, 7),
+                                     (5, 5, 1, 5)])
+def test_auto_takes_the_combination_path_without_inner_rows_or_columns(oracle_mod, N, M, P, Q):
+    assert cov.plan_info(N, M, P, Q)["recurrence_ok"] == 1
     A = wl.integer_valued((N, M), 5 + N)
     got = run(A, P, Q, torch.complex128, algo="auto")
+    assert np.array_equal(got, run(A, P, Q, torch.complex128, algo="recurrence"))
     assert np.array_equal(got, oracle_R(oracle_mod, A, P, Q))
     A32 = wl.complex_normal((N, M), 6 + N, dtype="c64")
     got = run(A32, P, Q, torch.complex64, algo="auto")
     assert rel_fro(got, oracle_R(oracle_mod, A32.astype(np.complex128), P, Q)) < 1e-6
+
+
+@pytest.mark.parametrize("N,M,P,Q", [(12, 40, 7, 5), (20, 20, 16, 6), (62, 600, 32, 20)])
+@pytest.mark.parametrize("kernels", [1, 4])
+def test_short_rows_fused_and_four_kernels(oracle_mod, N, M, P, Q, kernels):
+    # N < 2P - 1 with inner columns: the fused kernel takes it (no product
+    # tasks), as do the four kernels; both exact on integers
+    key = ("c64", N, M, P, Q)
+    cov.tuning_set(*key, {"lag_group": 8, "rows_per_task": 16, "reseed_interval": 4,
+                          "kernels": kernels})
+    try:
+        A = wl.integer_valued((N, M), 41 + M)
+        K = (N - P + 1) * (M - Q + 1)
+        assert K * 256 < 2 ** 24
+        S = oracle_R(oracle_mod, A, P, Q, mean=False)
+        assert np.array_equal(run(A.astype(np.complex64), P, Q, torch.complex64, norm="sum"),
+                              S.astype(np.complex64))
+    finally:
+        cov.tuning_set(*key, None)
 
 
 @pytest.mark.parametrize("N,M,P,Q", [(64, 64, 8, 8), (31, 17, 4, 6)])

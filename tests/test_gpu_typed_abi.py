@@ -4,7 +4,8 @@ instrumentation the roofline figures use.
 
 Bars as in test_gpu_recurrence.py: complex128 bit-identical to the oracle on
 small-integer inputs; complex64 within 1e-5 relative Frobenius of the FP64
-oracle. Shapes the combination path does not take go through COV_DIRECT
+oracle. Shapes without inner rows or columns run the combination path as
+well; shapes it does not take (P or Q above 32) go through COV_DIRECT
 (COV_AUTO), which is held to the same bars.
 """
 import ctypes
@@ -28,7 +29,7 @@ def _stream():
 
 
 @pytest.mark.parametrize("N,M,P,Q", [(64, 64, 8, 8), (100, 70, 8, 3), (40, 17, 7, 1),
-                                     (9, 30, 6, 4), (1, 1, 1, 1)])
+                                     (9, 30, 6, 4), (1, 1, 1, 1), (40, 36, 33, 1)])
 def test_typed_c128_integer_bit_exact(oracle_mod, N, M, P, Q):
     lib = cov.load()
     A_np = wl.integer_valued((N, M), 91 + N * M)

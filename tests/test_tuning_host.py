@@ -71,10 +71,15 @@ def test_fp64_lag_group_16_rejected():
 
 
 def test_unsupported_shape():
+    # P above 32: the combination path does not take it
     with pytest.raises(cov.CovError) as e:
-        cov.tuning_set("c64", 10, 10, 8, 8,
+        cov.tuning_set("c64", 40, 40, 33, 2,
                        {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4})
     assert e.value.code == 5
+    # no inner rows or columns: taken
+    cov.tuning_set("c64", 10, 10, 8, 8,
+                   {"lag_group": 8, "rows_per_task": 24, "reseed_interval": 4, "kernels": 4})
+    cov.tuning_clear()
 
 
 def test_planner_honours_rows_per_task():
