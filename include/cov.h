@@ -339,8 +339,10 @@ cov_status cov_aperture_descs(const void *image, cov_dtype dtype, int64_t H, int
                               cov_desc *descs, int max_count, int *count);
 
 /* Validates `count` descriptors (HOST array, copied) and builds the task
- * schedule. Only COV_C64 with COV_RECURRENCE (or COV_AUTO) is supported; every
- * member must satisfy the COV_RECURRENCE shape rule. On success *plan owns
+ * schedule. COV_RECURRENCE (or COV_AUTO) only; every member must satisfy the
+ * COV_RECURRENCE shape rule (P, Q <= 32), A and R 8-byte aligned. COV_C64
+ * plans offer every form whose limits the members meet (below); COV_C128
+ * plans the stage form only. On success *plan owns
  * host memory until cov_batched_plan_destroy. The schedule is balanced for
  * the SM count of the device current at creation (152, GB300's, when no
  * device is visible); cov_batched_upload, cov_estimate_batched and
@@ -352,8 +354,8 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
                                    cov_algo algo, cov_norm norm, cov_batched_plan **plan);
 cov_status cov_batched_workspace_size(const cov_batched_plan *plan, size_t *bytes);
 /* Copies the plan's tables into `workspace` (stream-ordered). Must precede the
- * first cov_estimate_batched on that workspace; not needed again while the
- * workspace is only used by this plan. */
+ * first cov_estimate_batched on that workspace (the tables hold addresses in
+ * it); not needed again while the workspace is only used by this plan. */
 cov_status cov_batched_upload(const cov_batched_plan *plan, void *workspace,
                               size_t ws_bytes, cov_stream_t stream);
 /* Launches the batched computation (kernel launches only; capturable). */
@@ -363,7 +365,16 @@ void cov_batched_plan_destroy(cov_batched_plan *plan);
 
 /* Tuned knobs of a batched plan (the segment length and task shape the
  * autotuner picks):
- *   form            0: one CTA per member in flight (any members);
+ *   form            0: one CTA per member in flight (COV_C64; members with
+ *                      P, Q <= 16, N >= 2P-1, M >= 2Q-1, M <= 512);
+ *                   3: the stages of the single-matrix combination path,
+ *                      each one launch over all members: products over the
+ *                      inner rows (persistent CTAs sharing the concatenated
+ *                      task list), fringe rows, then one CTA per member for
+ *                      the reductions and the seed-and-walk writer; the
+ *                      members' partial sums live in the workspace (offered
+ *                      while they fit in 4 GiB, and always where no other
+ *                      form takes the members);
  *                   1: one warp per member (only when every member has
  *                      M <= 32, N*M <= 1024 and P, Q <= 16);
  *                   2: one CTA per small member in flight, every output a
@@ -379,7 +390,7 @@ void cov_batched_plan_destroy(cov_batched_plan *plan);
  *                   additions in a chain); 0 = one seed per segment; <= 16;
  *   row_ranges      form 0: at most this many row ranges (1, 2 or 4) per
  *                   column block of the inner-row product tasks.
- * A new plan starts at form = 2 where allowed, else 1 where allowed, else 0,
+ * A new plan starts at form = 2 where offered, else 1, else 0, else 3,
  * reseed_interval 0, row_ranges 4. */
 typedef struct {
   int32_t form;
@@ -391,11 +402,10 @@ typedef struct {
 cov_status cov_batched_get_tuning(const cov_batched_plan *plan, cov_batched_tuning_t *t);
 /* Host only: sets the knobs and rebuilds the schedule when the form changes
  * (upload again before the next cov_estimate_batched). COV_EINVAL on a value
- * outside the ranges above, or form 1 for a plan whose members do not all
- * fit it. */
+ * outside the ranges above, or a form the plan does not offer. */
 cov_status cov_batched_set_tuning(cov_batched_plan *plan, const cov_batched_tuning_t *t);
-/* Times the candidate knob settings (forms 2 and 1 where allowed; form 0 with
- * reseed_interval 0, 2, 4 and row_ranges 2, 4) on the plan's own members,
+/* Times the candidate knob settings (forms 2, 1 and 3 where offered; form 0
+ * with reseed_interval 0, 2, 4 and row_ranges 2, 4) on the plan's own members,
  * `reps` launches each after one warm-up on `stream`, keeps the fastest and
  * uploads its tables into `workspace`. Writes every member's R (the last
  * setting's result, all settings compute the same R up to rounding);

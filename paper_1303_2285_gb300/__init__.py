@@ -61,9 +61,10 @@ class Tuning(ctypes.Structure):
 
 class BatchedTuning(ctypes.Structure):
     """Knobs of a batched plan: kernel form (0 CTA per member, 1 warp per
-    member, 2 box sums of small members in shared memory), walk re-seed
-    interval of form 0 (0: one seed per segment),
-    row ranges per column block of form 0 (cov_batched_tuning_t)."""
+    member, 2 box sums of small members in shared memory, 3 the single-matrix
+    stages over all members), walk re-seed interval of form 0 (0: one seed
+    per segment), row ranges per column block of form 0
+    (cov_batched_tuning_t)."""
     _fields_ = [("form", ctypes.c_int32), ("reseed_interval", ctypes.c_int32),
                 ("row_ranges", ctypes.c_int32)]
 
@@ -342,26 +343,36 @@ def covariance(A, P: int, Q: int, norm: str = "mean"):
 class BatchedPlan:
     """Many matrices of uneven shapes in one persistent launch (cov_batched_*).
 
-    ``items``: sequence of (A, R, P, Q) with A an N x M complex64 CUDA tensor
-    (unit column stride) and R a contiguous PQ x PQ complex64 CUDA tensor. The
-    plan keeps the device pointers: the tensors must outlive it.
+    ``items``: sequence of (A, R, P, Q) with A an N x M complex64 (or, all of
+    them, complex128) CUDA tensor (unit column stride) and R a contiguous
+    PQ x PQ CUDA tensor of the same dtype. The plan keeps the device pointers:
+    the tensors must outlive it. complex128 batches run the stage form only.
     """
 
-    def __init__(self, items, norm: str = "mean", descs=None):
+    def __init__(self, items, norm: str = "mean", descs=None, dtype: Optional[str] = None):
         lib = load()
         if descs is not None:  # prepared descriptors (e.g. aperture_batch)
             arr, n = descs, len(descs)
+            dtype = dtype or "c64"
         else:
             n = len(items)
             arr = (CovDesc * n)()
+            kinds = set()
             for k, (A, R, P, Q) in enumerate(items):
                 if not (A.is_cuda and R.is_cuda) or A.stride(1) != 1 or not R.is_contiguous():
                     raise ValueError("A and R must be CUDA tensors (A unit column stride, "
                                      "R contiguous)")
+                kinds.add((str(A.dtype), str(R.dtype)))
                 arr[k] = CovDesc(A.data_ptr(), R.data_ptr(), A.stride(0), A.shape[0], A.shape[1],
                                  P, Q)
+            if kinds == {("torch.complex128", "torch.complex128")}:
+                dtype = "c128"
+            elif kinds == {("torch.complex64", "torch.complex64")}:
+                dtype = "c64"
+            else:
+                raise ValueError("A and R must all be complex64, or all complex128")
         ptr = ctypes.c_void_p()
-        _check(lib.cov_batched_plan_create(arr, n, DTYPES["c64"], ALGOS["auto"], NORMS[norm],
+        _check(lib.cov_batched_plan_create(arr, n, DTYPES[dtype], ALGOS["auto"], NORMS[norm],
                                            ctypes.byref(ptr)), "cov_batched_plan_create")
         self._lib = lib
         self.ptr = ptr

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "../../include/cov.h"
+#include "batched_pipe.h"
 #include "cov_device.cuh"
 #include "cov_internal.h"
 #include "smem_attr.h"
@@ -787,10 +788,14 @@ struct cov_batched_plan {
   std::vector<int> cta_begin;  // slots + 1 offsets into order
   int grid;
   int sms;
+  int cta_ok;                  // every member fits k_batched
   int narrow_ok;               // every member fits k_batched_warp
   int box_ok;                  // every member fits k_batched_box
+  int pipe_ok;                 // every member fits the stage form (batched_pipe.cu)
   size_t box_smem;             // k_batched_box's shared memory for the largest member
-  int form;                    // tuned: 0 = CTA form, 1 = one warp per member, 2 = box form
+  cov::PipePlan pipe;          // the stage form's member plans and tables
+  int form;                    // tuned: 0 = CTA form, 1 = one warp per member, 2 = box form,
+                               // 3 = stage form
   int L;                       // tuned: re-seed interval of the CTA form's walk (0: none)
   int rs_max;                  // tuned: row ranges per column block (1, 2, 4)
   int mean;
@@ -799,12 +804,19 @@ struct cov_batched_plan {
 
 namespace {
 
+// A member the CTA, warp and box forms can take (they also need the
+// per-form limits checked in cov_batched_plan_create).
 bool batched_shape_ok(const cov_desc &d) {
   return d.A && d.R && d.N >= 1 && d.M >= 1 && d.P >= 1 && d.Q >= 1 && d.P <= cov::kBMaxPQ &&
          d.Q <= cov::kBMaxPQ && d.N >= 2 * d.P - 1 && d.M >= 2 * d.Q - 1 && d.M <= cov::kBMaxM &&
          d.lda >= d.M && (long long)d.N * d.lda < (1LL << 31) && (((uintptr_t)d.A) & 7) == 0 &&
          (((uintptr_t)d.R) & 7) == 0;
 }
+
+// The stage form keeps every member's partial sums in the workspace: it is
+// offered only while they stay within this many bytes (always where no other
+// form takes the members).
+constexpr size_t kPipeMaxWorkspace = (size_t)4 << 30;
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -958,9 +970,12 @@ void build_schedule(cov_batched_plan *pl) {
 cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype dtype, cov_algo algo,
                                    cov_norm norm, cov_batched_plan **plan) {
   if (!descs || count < 1 || !plan || (norm != COV_MEAN && norm != COV_SUM)) return COV_EINVAL;
-  if (dtype != COV_C64 || (algo != COV_AUTO && algo != COV_RECURRENCE)) return COV_EUNSUPPORTED;
-  for (int i = 0; i < count; ++i)
-    if (!batched_shape_ok(descs[i])) return COV_EINVAL;
+  if ((dtype != COV_C64 && dtype != COV_C128) || (algo != COV_AUTO && algo != COV_RECURRENCE))
+    return COV_EUNSUPPORTED;
+  bool cta = dtype == COV_C64;  // every member fits the CTA form (and the warp / box forms' base rule)
+  for (int i = 0; i < count; ++i) cta = cta && batched_shape_ok(descs[i]);
+  const bool pipe_members = cov::pipe_members_ok(descs, count);
+  if (!cta && !pipe_members) return COV_EINVAL;
   int sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
@@ -974,6 +989,8 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   bool narrow = true;  // every member small enough for one warp
   bool box = true;     // every member small enough for the box form
   size_t box_smem = 0;
+  narrow = narrow && cta;
+  box = box && cta;
   for (int i = 0; i < count; ++i) {
     const cov_desc &d = descs[i];
     pl->descs[i] = {(const float2 *)d.A, (float2 *)d.R, d.lda, d.N, d.M, d.P, d.Q};
@@ -983,14 +1000,12 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
           d.P * d.Q <= cov::kXMaxD && d.N * d.M <= cov::kXMaxElems;
     if (box) box_smem = std::max(box_smem, cov::box_smem_bytes(d.N * d.M, d.P, d.Q));
   }
+  pl->cta_ok = cta ? 1 : 0;
   pl->narrow_ok = narrow ? 1 : 0;
   pl->box_ok = box ? 1 : 0;
   pl->box_smem = box ? box_smem : 0;
-  // defaults (cov_batched_autotune times the alternatives)
-  pl->form = pl->box_ok ? 2 : pl->narrow_ok ? 1 : 0;
   pl->L = 0;
   pl->rs_max = cov::kBMaxRS;
-  build_schedule(pl);
   // the tables are laid out for the larger of the two forms' slot counts
   const int max_slots = std::max({std::min(sms, count),
                                   narrow ? std::min(2 * sms, (count + cov::kWWarps - 1) / cov::kWWarps) *
@@ -1005,6 +1020,24 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   pl->off_begin = off;
   off = al256(off + sizeof(int) * (max_slots + 1));
   pl->total = off;
+  // the stage form's tables and member regions follow, where offered
+  pl->pipe_ok = 0;
+  if (pipe_members) {
+    cov::pipe_plan_build(pl->pipe, descs, count, dtype == COV_C128 ? 16 : 8, pl->mean, off);
+    if (pl->pipe.total <= kPipeMaxWorkspace || !cta) {
+      pl->pipe_ok = 1;
+      pl->total = pl->pipe.total;
+    } else {
+      pl->pipe = cov::PipePlan();
+    }
+  }
+  if (!cta && !pl->pipe_ok) {
+    delete pl;
+    return COV_EINVAL;
+  }
+  // defaults (cov_batched_autotune times the alternatives)
+  pl->form = pl->box_ok ? 2 : pl->narrow_ok ? 1 : pl->cta_ok ? 0 : 3;
+  build_schedule(pl);
   *plan = pl;
   return COV_OK;
 }
@@ -1042,6 +1075,7 @@ cov_status cov_batched_upload(const cov_batched_plan *plan, void *workspace, siz
       cudaMemcpyAsync(w + plan->off_begin, plan->cta_begin.data(), sizeof(int) * plan->cta_begin.size(),
                       cudaMemcpyHostToDevice, s) != cudaSuccess)
     return COV_ECUDA;
+  if (plan->pipe_ok && cov::pipe_upload(plan->pipe, w, s) != cudaSuccess) return COV_ECUDA;
   // pageable host memory: make sure the copies have read it before returning
   if (cudaStreamSynchronize(s) != cudaSuccess) return COV_ECUDA;
   return COV_OK;
@@ -1055,10 +1089,12 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, s
   if (dst != COV_OK) return dst;
   cudaStream_t s = (cudaStream_t)stream;
   char *w = (char *)workspace;
+  if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  if (plan->form == 3)
+    return cov::pipe_launch(plan->pipe, w, plan->sms, s) == cudaSuccess ? COV_OK : COV_ECUDA;
   const size_t smem = cov::kBSmemBytes;
   if (cov::ensure_dyn_smem((const void *)cov::k_batched, smem, false) != cudaSuccess)
     return COV_ECUDA;
-  if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
   if (plan->form == 2) {
     if (cov::ensure_dyn_smem((const void *)cov::k_batched_box, plan->box_smem, false) != cudaSuccess)
       return COV_ECUDA;
@@ -1094,8 +1130,9 @@ cov_status cov_batched_get_tuning(const cov_batched_plan *plan, cov_batched_tuni
 
 cov_status cov_batched_set_tuning(cov_batched_plan *plan, const cov_batched_tuning_t *t) {
   if (!plan || !t) return COV_EINVAL;
-  if (t->form < 0 || t->form > 2 || (t->form == 1 && !plan->narrow_ok) ||
-      (t->form == 2 && !plan->box_ok))
+  if (t->form < 0 || t->form > 3 || (t->form == 0 && !plan->cta_ok) ||
+      (t->form == 1 && !plan->narrow_ok) || (t->form == 2 && !plan->box_ok) ||
+      (t->form == 3 && !plan->pipe_ok))
     return COV_EINVAL;
   if (t->reseed_interval < 0 || t->reseed_interval > cov::kBMaxPQ) return COV_EINVAL;
   if (t->row_ranges != 1 && t->row_ranges != 2 && t->row_ranges != 4) return COV_EINVAL;
@@ -1120,8 +1157,10 @@ cov_status cov_batched_autotune(cov_batched_plan *plan, void *workspace, size_t 
   std::vector<cov_batched_tuning_t> cand;
   if (plan->box_ok) cand.push_back({2, 0, cov::kBMaxRS});
   if (plan->narrow_ok) cand.push_back({1, 0, cov::kBMaxRS});
-  for (int L : {0, 2, 4})
-    for (int rs : {2, 4}) cand.push_back({0, L, rs});
+  if (plan->pipe_ok) cand.push_back({3, 0, cov::kBMaxRS});
+  if (plan->cta_ok)
+    for (int L : {0, 2, 4})
+      for (int rs : {2, 4}) cand.push_back({0, L, rs});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);

@@ -107,17 +107,20 @@ __device__ __forceinline__ void warp_transpose_reduce(T (&v)[V], int lane) {
 }
 
 // cp.async copies with zero fill: src_size 0 writes zeros without reading.
+// No memory clobber: the copy lands asynchronously, and its completion is
+// ordered by the wait that follows it (cp.async.wait_group or an mbarrier
+// wait), which carries one; a clobber here would make the compiler reload
+// every value it keeps in memory (kernel parameters read through a pointer)
+// after each copy of a staging loop.
 __device__ __forceinline__ void cp_async_8(void *smem, const void *gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   const int sz = valid ? 8 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(sz)
-               : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(sz));
 }
 __device__ __forceinline__ void cp_async_16(void *smem, const void *gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   const int sz = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz)
-               : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz));
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");

@@ -53,7 +53,7 @@ int choose_group(int P, int Q, int elem) {
 
 void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int elem, int sms,
                      RecParams &p, WsLayout &ws, const Tuning *tune) {
-  Tuning t = {0, 0, 0, 0, 0};
+  Tuning t = {0, 0, 0, 0, 0, 0};
   if (tune) t = *tune;
   else lookup_tuning(elem, N, M, P, Q, sms, t);
   memset(&p, 0, sizeof(p));
@@ -113,6 +113,10 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
     const int floor_rows = elem == 8 ? 16 : 8;
     while (TRB > floor_rows && (long long)((p.n_inner + TRB - 1) / TRB) * per_rb < want) TRB -= 8;
   }
+  // no longer than the inner rows (rounded up to 8): a longer block only
+  // stages rows no task reads
+  const int inner8 = ((p.n_inner + 7) / 8) * 8;
+  if (inner8 >= 8 && TRB > inner8) TRB = inner8;
   if (t.TRB >= 8 && t.TRB % 8 == 0 && t.TRB <= tr_max) TRB = t.TRB;
   if (TRB < 8) TRB = 8;
   int TPT = (int)(tr_max / TRB);
@@ -133,6 +137,7 @@ void plan_recurrence(long long N, long long M, long long lda, int P, int Q, int 
   p.ngroups_f = n_groups(P, Q, p.GF);
   p.nrb = (P - 1 + p.RB - 1) / p.RB;
   p.CWF = elem == 16 ? 8 : 32;
+  if (t.CWF >= 8 && t.CWF <= 256 && t.CWF % 8 == 0) p.CWF = t.CWF;
   p.FPB = elem == 16 ? 32 : 256;
   p.NCH = (p.n_innerc + p.CWF - 1) / p.CWF;  // 0 without inner columns
   p.QMAXF = Q <= 4 ? 4 : Q <= 8 ? 8 : Q <= 16 ? 16 : 32;

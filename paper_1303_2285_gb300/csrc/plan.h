@@ -30,9 +30,11 @@ int choose_group(int P, int Q, int elem);
 // Tuned knobs of the combination path (0 = the plan's default): lags per
 // group G, rows per product task TRB, walk re-seed interval L, kernels per
 // call K (1 = the fused cooperative kernel, FP32 only; 4 = four kernels),
-// columns per shared-memory tile TC (32 or 64).
+// columns per shared-memory tile TC (32 or 64), inner columns per fringe-row
+// chunk CWF (a multiple of 8 up to 256; not a public knob: the batched stage
+// form widens it for small members).
 struct Tuning {
-  int G, TRB, L, K, TC;
+  int G, TRB, L, K, TC, CWF;
 };
 
 // Fills every field of p that depends on the shape only (not the pointers);

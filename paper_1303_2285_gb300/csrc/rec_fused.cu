@@ -196,11 +196,8 @@ static cudaError_t launch_fused_g(const RecParams &p, const CUtensorMap &tmap, i
 }
 
 bool fused_supported(const RecParams &p, bool fp64) {
-  // the warp-task reductions take the scan form of the fringe columns only
-  // (a box holds Q - 1 of them: M >= 2Q - 2)
   return !fp64 && (p.G == 4 || p.G == 8 || p.G == 16) &&
-         (p.PITCH == 48 || p.PITCH == 64 || p.PITCH == 80 || p.PITCH == 96) &&
-         p.NFC == 2 * (p.Q - 1);
+         (p.PITCH == 48 || p.PITCH == 64 || p.PITCH == 80 || p.PITCH == 96);
 }
 
 cudaError_t launch_fused(const RecParams &p, const CUtensorMap &tmap, int num_sms, cudaStream_t s) {

@@ -72,6 +72,45 @@ __device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int
     cr.merge(s1, c1);
     ci.merge(s2, c2);
   }
+  if (p.NFC != 2 * (Q - 1)) {
+    // window form (M < 2Q - 2): lane k holds the sums of fringe columns k and
+    // k + 32 over the row blocks; lane j < J adds the HC sums of its box,
+    // fetched from their lanes in order
+    T c0r = 0, c0i = 0, c1r = 0, c1i = 0;
+    {
+      const C2 *cs = (const C2 *)p.colsum_part + (long long)D * p.n_rb * p.NFC;
+      Neu<T> a, b, c, d;
+      for (int rb = 0; rb < p.n_rb; ++rb) {
+        const C2 x = lane < p.NFC ? cs[(long long)rb * p.NFC + lane] : czero<C2>();
+        const C2 y = lane + 32 < p.NFC ? cs[(long long)rb * p.NFC + lane + 32] : czero<C2>();
+        a.add(x.x);
+        b.add(x.y);
+        c.add(y.x);
+        d.add(y.y);
+      }
+      c0r = a.value();
+      c0i = b.value();
+      c1r = c.value();
+      c1i = d.value();
+    }
+    const int J = Q - dc;
+    Neu<T> vr = cr, vi = ci;
+    for (int k = 0; k < p.HC; ++k) {
+      const int src = (lane + k) & 31;
+      const T x0 = __shfl_sync(0xffffffffu, c0r, src), y0 = __shfl_sync(0xffffffffu, c0i, src);
+      const T x1 = __shfl_sync(0xffffffffu, c1r, src), y1 = __shfl_sync(0xffffffffu, c1i, src);
+      const bool hi = lane + k >= 32;
+      vr.add(hi ? x1 : x0);
+      vi.add(hi ? y1 : y0);
+    }
+    if (lane < J) {
+      C2 o;
+      o.x = vr.value();
+      o.y = vi.value();
+      ((C2 *)p.colval)[(long long)D * Q + lane] = o;
+    }
+    return;
+  }
   // lane k < Q-1: fringe columns m = k (left) and m = W + k (right), each
   // summed over the row blocks
   T lr = 0, li = 0, rr = 0, ri = 0;
@@ -130,7 +169,7 @@ __device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int
 template <typename T, int QMAX>
 __device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int lane) {
   using C2 = typename C2t<T>::type;
-  const int P = p.P, Q = p.Q, W = p.M - p.Q + 1, NFR = p.NFR, NCH = p.NCH;
+  const int P = p.P, Q = p.Q, W = p.M - p.Q + 1, NFR = p.NFR, NFC = p.NFC, NCH = p.NCH;
   int dr, dc;
   combo_of(P, D, dr, dc);
   const int J = Q - dc;
@@ -156,6 +195,31 @@ __device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int 
     }
     const T s_r = (sr[0] + sr[1]) + (sr[2] + sr[3]);
     const T s_i = (si[0] + si[1]) + (si[2] + si[3]);
+    if (NFC != 2 * (Q - 1)) {
+      // window form (M < 2Q - 2): the row's NFC fringe-column products, each
+      // formed once, then out[j] = S_in + the HC of them in the box of j
+      C2 pr[2 * kMaxPQ];
+      const C2 *An = A + (long long)n * p.lda;
+      const C2 *Ab = A + (long long)(n + dr) * p.lda + dc;
+      for (int k = 0; k < NFC; ++k) {
+        const int m = fringe_col(Q, p.n_innerc, k);
+        C2 v = czero<C2>();
+        if (rowok && m + dc < p.M) cmac_conj(v, __ldg(An + m), __ldg(Ab + m));
+        pr[k] = v;
+      }
+      for (int j = 0; j < J; ++j) {
+        C2 w = czero<C2>();
+        for (int k = j; k < j + p.HC; ++k) {
+          w.x += pr[k].x;
+          w.y += pr[k].y;
+        }
+        C2 o;
+        o.x = s_r + w.x;
+        o.y = s_i + w.y;
+        rv[(long long)j * NFR + fr] = o;
+      }
+      continue;
+    }
     // out[j] = suffix of the left fringe-column products (k >= j)
     T outr[QMAX], outi[QMAX];
     {
@@ -701,6 +765,92 @@ __device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, u
         R[(ra + i) * DD + ra + ii] = v;
       }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Thread task: the same seed, walk and division as walk_block for one
+// diagonal segment (combination D, column offset j, chunk c of L outputs),
+// reading RV and CV from global memory and writing each output and its
+// conjugate mirror to R directly (no block staging: for batches of small
+// matrices, where a P x P block is too small to keep a CTA busy). The RV and
+// R pointers are declared unaliased so that the walk's loads can be issued
+// ahead of its stores.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void walk_segment_rv(const RecParams &p,
+                                                const typename C2t<T>::type *__restrict__ RV,
+                                                typename C2t<T>::type cv,
+                                                typename C2t<T>::type *__restrict__ R, int dr,
+                                                int dc, int j, int is, int ie) {
+  using C2 = typename C2t<T>::type;
+  const int P = p.P;
+  Neu<T> orr, oii, o2r, o2i;
+  orr.add(cv.x);
+  oii.add(cv.y);
+  {
+    const int ue = is + p.H;
+    int u = is;
+    for (; u + 2 <= ue; u += 2) {
+      const C2 a = RV[u], b = RV[u + 1];
+      orr.add(a.x);
+      oii.add(a.y);
+      o2r.add(b.x);
+      o2i.add(b.y);
+    }
+    if (u < ue) {
+      orr.add(RV[u].x);
+      oii.add(RV[u].y);
+    }
+    orr.merge(o2r.s, o2r.c);
+    oii.merge(o2i.s, o2i.c);
+  }
+  const long long DD = (long long)P * p.Q;
+  for (int i = is; i < ie; ++i) {
+    T re = orr.value(), im = oii.value();
+    if (p.mean) {
+      if (p.div_double) {
+        re = (T)((double)re / (double)p.K);
+        im = (T)((double)im / (double)p.K);
+      } else {
+        re = re / (T)p.K;
+        im = im / (T)p.K;
+      }
+    }
+    if (dr == 0 && dc == 0) im = T(0);
+    const long long a = i + (long long)P * j, b = (i + dr) + (long long)P * (j + dc);
+    C2 o;
+    o.x = re;
+    o.y = im;
+    R[a * DD + b] = o;
+    if (a != b) {
+      o.y = -im;
+      R[b * DD + a] = o;
+    }
+    if (i + 1 < ie) {
+      orr.add(-RV[i].x);
+      oii.add(-RV[i].y);
+      orr.add(RV[p.H + i].x);
+      oii.add(RV[p.H + i].y);
+    }
+  }
+}
+
+// Returns without work for an empty segment.
+template <typename T>
+__device__ __forceinline__ void walk_segment(const RecParams &p, int D, int j, int c) {
+  using C2 = typename C2t<T>::type;
+  const int P = p.P;
+  int dr, dc;
+  combo_of(P, D, dr, dc);
+  if (j >= p.Q - dc) return;
+  const int adr = dr < 0 ? -dr : dr;
+  const int I = P - adr, i0 = dr < 0 ? -dr : 0;
+  const int is = i0 + c * p.L;
+  if (is >= i0 + I) return;
+  const int ie = (i0 + I) < (is + p.L) ? (i0 + I) : (is + p.L);
+  const C2 *RV = (const C2 *)p.rowval + ((long long)D * p.Q + j) * p.NFR;
+  const C2 cv = ((const C2 *)p.colval)[(long long)D * p.Q + j];
+  walk_segment_rv<T>(p, RV, cv, (C2 *)p.R, dr, dc, j, is, ie);
 }
 
 // Blocks (bj, bj + dc) of the shard's column lags, in launch order.

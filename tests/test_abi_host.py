@@ -119,16 +119,34 @@ def test_batched_plan_validation_host_only():
         code = lib.cov_batched_plan_create(arr, len(shapes), 0, 0, 0, ctypes.byref(ptr))
         return code, ptr
 
+    def form_after(shapes, form):
+        code, ptr = plan(shapes)
+        assert code == 0, shapes
+        t = cov.BatchedTuning(form, 0, 4)
+        ok = lib.cov_batched_set_tuning(ptr, ctypes.byref(t)) == 0
+        lib.cov_batched_plan_destroy(ptr)
+        return ok
+
     code, ptr = plan([(64, 64, 8, 8), (33, 40, 16, 2), (200, 512, 3, 16)])
     assert code == 0
     n = ctypes.c_size_t(0)
     assert lib.cov_batched_workspace_size(ptr, ctypes.byref(n)) == 0 and n.value > 256
     lib.cov_batched_plan_destroy(ptr)
-    for bad in ([(64, 64, 17, 8)], [(30, 64, 16, 2)], [(64, 513, 2, 2)], [(8, 8, 0, 1)]):
+    # beyond the CTA form's limits (P or Q above 16, no inner rows, M above
+    # 512): only the stage form takes the batch
+    for wide in ([(64, 64, 17, 8)], [(30, 64, 16, 2)], [(64, 513, 2, 2)], [(40, 40, 32, 32)]):
+        assert form_after(wide, 3) and not form_after(wide, 0), wide
+    assert form_after([(64, 64, 8, 8)], 0) and form_after([(64, 64, 8, 8)], 3)
+    for bad in ([(8, 8, 0, 1)], [(64, 64, 33, 2)], [(8, 8, 9, 2)]):
         assert plan(bad)[0] == 1, bad
     arr = (cov.CovDesc * 1)(cov.CovDesc(fake, fake, 8, 8, 8, 2, 2))
     ptr = ctypes.c_void_p()
-    assert lib.cov_batched_plan_create(arr, 1, 1, 0, 0, ctypes.byref(ptr)) == 5  # c128
+    assert lib.cov_batched_plan_create(arr, 1, 1, 0, 0, ctypes.byref(ptr)) == 0  # c128: stage form
+    t = cov.BatchedTuning()
+    assert lib.cov_batched_get_tuning(ptr, ctypes.byref(t)) == 0 and t.form == 3
+    t.form = 0
+    assert lib.cov_batched_set_tuning(ptr, ctypes.byref(t)) == 1
+    lib.cov_batched_plan_destroy(ptr)
     assert lib.cov_batched_plan_create(arr, 1, 0, 2, 0, ctypes.byref(ptr)) == 5  # gemm algo
 
 

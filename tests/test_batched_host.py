@@ -53,7 +53,7 @@ def test_set_and_get_round_trip():
         assert plan.tuning == {"form": form, "reseed_interval": L, "row_ranges": rs}
 
 
-@pytest.mark.parametrize("form,L,rs", [(3, 0, 4), (-1, 0, 4), (0, -1, 4), (0, 17, 4), (0, 0, 3),
+@pytest.mark.parametrize("form,L,rs", [(4, 0, 4), (-1, 0, 4), (0, -1, 4), (0, 17, 4), (0, 0, 3),
                                        (0, 0, 0)])
 def test_bad_values_are_refused(form, L, rs):
     plan = make_plan([(25, 25, 10, 10)])
@@ -61,6 +61,23 @@ def test_bad_values_are_refused(form, L, rs):
     with pytest.raises(cov.CovError):
         plan.set_tuning(form, L, rs)
     assert plan.tuning == before
+
+
+def test_stage_form_offered_with_every_other_form():
+    plan = make_plan([(25, 25, 10, 10), (64, 64, 8, 8)])
+    plan.set_tuning(3)
+    assert plan.tuning["form"] == 3
+    plan.set_tuning(0)
+    assert plan.tuning["form"] == 0
+
+
+def test_members_only_the_stage_form_takes():
+    # P = 20, N < 2P - 1 and M = 600 are beyond the CTA form's limits
+    plan = make_plan([(64, 64, 20, 4), (30, 40, 16, 3), (100, 600, 4, 4)])
+    assert plan.tuning["form"] == 3
+    for form in (0, 1, 2):
+        with pytest.raises(cov.CovError):
+            plan.set_tuning(form)
 
 
 def test_null_arguments():
