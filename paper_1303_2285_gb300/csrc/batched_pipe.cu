@@ -7,14 +7,16 @@
 //      equal share of the concatenated task list of all members, weighted
 //      by each task's rows and lags (a share may start and end inside a
 //      member), and runs the product pipeline of rec_products.cuh (tiles
-//      staged with cp.async, one producer warp, consumer warps taking tasks)
-//      member by member; each member's lag group (4, 8 or 16) is chosen by
-//      its own plan;
+//      staged with cp.async by four producer warps, consumer warps taking
+//      tasks) member by member; each member's lag group (4, 8 or 16) is
+//      chosen by its own plan;
 //   2. fringe rows x inner columns: the fringe-row CTAs of every member;
-//   3. per member one CTA: the reductions as thread tasks (CV of each
-//      combination, RV of each (combination, fringe row)), then one thread
-//      per diagonal segment seeds, walks, divides by K and writes the outputs
-//      and their mirrors.
+//   3. the reductions as thread tasks over all members (CV of each
+//      combination, RV of each (combination, fringe row));
+//   4. one thread per diagonal segment of every member seeds, walks, divides
+//      by K and writes the outputs and their mirrors.
+// Stages 3 and 4 number their tasks across the batch (a member's tasks are
+// consecutive), so that a large member is spread over many CTAs.
 // The stages exchange the single-matrix partial sums through each member's
 // region of the workspace. The member plans are read from global memory as
 // the kernels' read-only input, their workspace addresses resolved when the
@@ -50,18 +52,21 @@ __device__ __forceinline__ int find_member(const long long *first, int n, long l
 }
 
 // ---- 1. products ------------------------------------------------------------
+// Register block rows, consumer warps and producer warps (the tiles are
+// staged with cp.async: several producer warps keep ahead of the consumers;
+// 16 warps at 128 registers fill the register file)
 template <typename T> struct PipeProd;
-template <> struct PipeProd<float> { static constexpr int R = 16, NCW = 12; };
-template <> struct PipeProd<double> { static constexpr int R = 8, NCW = 16; };
+template <> struct PipeProd<float> { static constexpr int R = 16, NCW = 12, NPW = 4; };
+template <> struct PipeProd<double> { static constexpr int R = 8, NCW = 12, NPW = 4; };
 
 // A CTA's share is a range of the class's cost axis: member j spans
 // [first[j], first[j + 1]) with n_tasks tasks of equal cost; task t belongs
 // to the CTA whose range holds first[j] + t * cost.
 template <typename T, int PITCH>
-__global__ void __launch_bounds__((PipeProd<T>::NCW + 1) * 32, 1)
+__global__ void __launch_bounds__((PipeProd<T>::NCW + PipeProd<T>::NPW) * 32, 1)
     k_pipe_products(const RecParams *__restrict__ mp, const int *__restrict__ members,
                     const long long *__restrict__ first, int n, long long total) {
-  constexpr int R = PipeProd<T>::R, NCW = PipeProd<T>::NCW;
+  constexpr int R = PipeProd<T>::R, NCW = PipeProd<T>::NCW, NPW = PipeProd<T>::NPW;
   extern __shared__ __align__(1024) unsigned char smem_pp[];
   const long long cb = total * blockIdx.x / gridDim.x;
   const long long ce = total * (blockIdx.x + 1) / gridDim.x;
@@ -74,11 +79,11 @@ __global__ void __launch_bounds__((PipeProd<T>::NCW + 1) * 32, 1)
     if (a >= b) continue;
     bool ok = false;
     if (p.G == 4) {
-      ok = products_phase<T, 4, R, PITCH, NCW>(p, g_pipe_no_map, smem_pp, a, b);
+      ok = products_phase<T, 4, R, PITCH, NCW, NPW>(p, g_pipe_no_map, smem_pp, a, b);
     } else if (p.G == 8) {
-      ok = products_phase<T, 8, R, PITCH, NCW>(p, g_pipe_no_map, smem_pp, a, b);
+      ok = products_phase<T, 8, R, PITCH, NCW, NPW>(p, g_pipe_no_map, smem_pp, a, b);
     } else if constexpr (sizeof(T) == 4) {
-      ok = products_phase<T, 16, R, PITCH, NCW>(p, g_pipe_no_map, smem_pp, a, b);
+      ok = products_phase<T, 16, R, PITCH, NCW, NPW>(p, g_pipe_no_map, smem_pp, a, b);
     }
     // every warp is done with the tiles and the barriers: invalidate them
     // before the next member's pipeline initialises its own
@@ -281,26 +286,34 @@ __device__ __forceinline__ void rv_thread(const RecParams &p, int D, int fr) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_pipe_finish(const RecParams *__restrict__ mp,
-                                                      const int *__restrict__ members) {
-  const RecParams &p = mp[members[blockIdx.x]];
-  // CV of each combination, RV of each (combination, fringe row): thread tasks
-  const long long nred = (long long)p.n_uc * (1 + p.NFR);
-  for (long long t = threadIdx.x; t < nred; t += blockDim.x) {
-    if (t < p.n_uc)
-      cv_thread<T>(p, (int)t);
-    else
-      rv_thread<T>(p, (int)((t - p.n_uc) / p.NFR), (int)((t - p.n_uc) % p.NFR));
-  }
-  // CV and RV are read below by other threads of this CTA only
-  __syncthreads();
-  const int nchunk = (p.P + p.L - 1) / p.L;
-  const long long nseg = (long long)p.n_uc * p.Q * nchunk;
-  for (long long t = threadIdx.x; t < nseg; t += blockDim.x) {
-    const int D = (int)(t % p.n_uc);
-    const long long r = t / p.n_uc;
-    walk_segment<T>(p, D, (int)(r % p.Q), (int)(r / p.Q));
-  }
+__global__ void __launch_bounds__(256) k_pipe_reduce(const RecParams *__restrict__ mp,
+                                                      const int *__restrict__ members,
+                                                      const long long *__restrict__ first, int n,
+                                                      long long total) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int j = find_member(first, n, t);
+  const RecParams &p = mp[members[j]];
+  const long long u = t - first[j];  // [0, n_uc): CV tasks; then RV tasks, fringe row fastest
+  if (u < p.n_uc)
+    cv_thread<T>(p, (int)u);
+  else
+    rv_thread<T>(p, (int)((u - p.n_uc) / p.NFR), (int)((u - p.n_uc) % p.NFR));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pipe_walk(const RecParams *__restrict__ mp,
+                                                    const int *__restrict__ members,
+                                                    const long long *__restrict__ first, int n,
+                                                    long long total) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int j = find_member(first, n, t);
+  const RecParams &p = mp[members[j]];
+  const long long u = t - first[j];  // (combination fastest, column offset, chunk)
+  const int D = (int)(u % p.n_uc);
+  const long long r = u / p.n_uc;
+  walk_segment<T>(p, D, (int)(r % p.Q), (int)(r / p.Q));
 }
 
 // ---------------------------------------------------------------------------
@@ -327,7 +340,6 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
   pp.fringe.clear();
   pp.finish.clear();
   std::map<int, PipeClass> prod, fr, fin;
-  std::vector<long long> cost(count);
   std::vector<size_t> region(count);
   std::vector<WsLayout> lay(count);
   for (int k = 0; k < count; ++k) {
@@ -344,15 +356,11 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     p.use_tma = 0;
     p.fused = 0;
     region[k] = lay[k].total - lay[k].core_off;
-    cost[k] = distinct_products(d.N, d.M, d.P, d.Q) + 2000LL * p.n_uc;
     if (p.n_inner > 0 && p.n_tasks > 0) prod[p.PITCH].members.push_back(k);
     if (p.NFR > 0 && p.NCH > 0) fr[p.QMAXF].members.push_back(k);
-    fin[0].members.push_back(k);
+    fin[0].members.push_back(k);  // reductions
+    fin[1].members.push_back(k);  // walk
   }
-  // the last stage starts the costliest members first
-  for (auto &kv : fin)
-    std::stable_sort(kv.second.members.begin(), kv.second.members.end(),
-                     [&](int a, int b) { return cost[a] > cost[b]; });
   const int fpb = elem == 16 ? 32 : 256;
   for (auto &kv : prod) {
     PipeClass &c = kv.second;
@@ -386,10 +394,17 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     c.smem = smem;
     pp.fringe.push_back(c);
   }
-  for (auto &kv : fin) {
+  for (auto &kv : fin) {  // key 0: reduction tasks; key 1: walk segments
     PipeClass &c = kv.second;
     c.key = kv.first;
-    c.total = (long long)c.members.size();
+    c.first.assign(1, 0);
+    for (int k : c.members) {
+      const RecParams &p = pp.params[k];
+      const long long nt = c.key == 0 ? (long long)p.n_uc * (1 + p.NFR)
+                                      : (long long)p.n_uc * p.Q * ((p.P + p.L - 1) / p.L);
+      c.first.push_back(c.first.back() + nt);
+    }
+    c.total = c.first.back();
     pp.finish.push_back(c);
   }
   // layout: the member plans, the class arrays, then each member's region;
@@ -452,7 +467,7 @@ static cudaError_t launch_pipe_products(const PipeClass &c, char *ws, const RecP
   if (e != cudaSuccess) return e;
   long long grid = sms;
   if (grid > c.total) grid = c.total;
-  kern<<<(unsigned)grid, (PipeProd<T>::NCW + 1) * 32, c.smem, s>>>(
+  kern<<<(unsigned)grid, (PipeProd<T>::NCW + PipeProd<T>::NPW) * 32, c.smem, s>>>(
       mp, (const int *)(ws + c.off_members), (const long long *)(ws + c.off_first),
       (int)c.members.size(), c.total);
   return cudaGetLastError();
@@ -498,7 +513,13 @@ static cudaError_t pipe_launch_t(const PipePlan &pp, char *ws, int sms, cudaStre
   }
   for (const PipeClass &c : pp.finish) {
     if (c.total <= 0) continue;
-    k_pipe_finish<T><<<(unsigned)c.total, 256, 0, s>>>(mp, (const int *)(ws + c.off_members));
+    const unsigned grid = (unsigned)((c.total + 255) / 256);
+    const int *mem = (const int *)(ws + c.off_members);
+    const long long *first = (const long long *)(ws + c.off_first);
+    if (c.key == 0)
+      k_pipe_reduce<T><<<grid, 256, 0, s>>>(mp, mem, first, (int)c.members.size(), c.total);
+    else
+      k_pipe_walk<T><<<grid, 256, 0, s>>>(mp, mem, first, (int)c.members.size(), c.total);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -28,15 +28,17 @@ namespace cov {
 // over the warp (transpose reduction) into the core partial; lanes on fringe
 // columns keep their own column sums.
 // ---------------------------------------------------------------------------
+// Rows pw, pw + npw, ... of the tile, by producer warp pw of npw.
 template <typename T, int PITCH>
 __device__ void stage_tile_cpasync(const RecParams &p, long long tile,
-                                   typename C2t<T>::type *S, uint64_t *full, int lane) {
+                                   typename C2t<T>::type *S, uint64_t *full, int lane, int pw,
+                                   int npw) {
   using C2 = typename C2t<T>::type;
   const int rt = (int)(tile / p.n_ct), ct = (int)(tile % p.n_ct);
   const long long r0 = (long long)p.inner_lo + (long long)rt * p.TR + p.d_lo;
   const int c0 = ct * p.TC;
   const C2 *A = (const C2 *)p.A;
-  for (int sr = 0; sr < p.STR; ++sr) {
+  for (int sr = pw; sr < p.STR; sr += npw) {
     const long long gr = r0 + sr;
     const bool rok = gr >= 0 && gr < p.N;
     const C2 *row = A + (rok ? gr : 0) * p.lda;
@@ -197,13 +199,15 @@ __host__ __device__ constexpr size_t tile_buf_bytes(int STR) {
   return (((size_t)STR * PITCH * sizeof(typename C2t<T>::type)) + 1023) & ~(size_t)1023;
 }
 
-// Runs the tasks [tb, te) of the product kernel in the calling CTA (one
-// producer warp NCW plus NCW consumer warps; `smem` holds two tile buffers and
-// the barriers). Every thread of the CTA calls it with the same range. Returns
-// false if a bounded wait gave up (the status word is then set); on return
-// the producer's copies have landed, but consumer warps may still be reading
-// shared memory: synchronise the CTA before reusing it.
-template <typename T, int G, int R, int PITCH, int NCW>
+// Runs the tasks [tb, te) of the product kernel in the calling CTA (NCW
+// consumer warps, then NPW producer warps; `smem` holds two tile buffers and
+// the barriers). With TMA the first producer warp issues each tile; with
+// cp.async the NPW warps share its rows (one warp's copies queue behind the
+// consumers' shared-memory loads). Every thread of the CTA calls it with the
+// same range. Returns false if a bounded wait gave up (the status word is
+// then set); on return the producers' copies have landed, but consumer warps
+// may still be reading shared memory: synchronise the CTA before reusing it.
+template <typename T, int G, int R, int PITCH, int NCW, int NPW = 1>
 __device__ __forceinline__ bool products_phase(const RecParams &p, const CUtensorMap &tmap,
                                                unsigned char *smem, long long tb, long long te) {
   using C2 = typename C2t<T>::type;
@@ -219,8 +223,8 @@ __device__ __forceinline__ bool products_phase(const RecParams &p, const CUtenso
   const long long tf = tb / tpt, tl = (te - 1) / tpt;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    mbar_init(&full[0], p.use_tma ? 1 : 32);
-    mbar_init(&full[1], p.use_tma ? 1 : 32);
+    mbar_init(&full[0], p.use_tma ? 1 : 32 * NPW);
+    mbar_init(&full[1], p.use_tma ? 1 : 32 * NPW);
     mbar_init(&empty[0], NCW);
     mbar_init(&empty[1], NCW);
     ctr[0] = 0;
@@ -231,7 +235,9 @@ __device__ __forceinline__ bool products_phase(const RecParams &p, const CUtenso
 
   // Every warp goes through the CTA's tiles in order and waits on each tile's
   // barrier phase in turn, so a parity wait never spans more than one phase.
-  if (warp == NCW) {  // producer
+  if (warp >= NCW) {  // producers
+    const int pw = warp - NCW;
+    if (p.use_tma && pw > 0) return true;
     const unsigned bytes = (unsigned)((size_t)p.STR * PITCH * sizeof(C2));
     bool ok = true;
     long long issued = -1;  // index (from tf) of the last tile whose load was issued
@@ -243,7 +249,7 @@ __device__ __forceinline__ bool products_phase(const RecParams &p, const CUtenso
         ok = false;
         break;
       }
-      if (lane == 0) ctr[b] = 0;  // all warps are done with the buffer's previous tile
+      if (pw == 0 && lane == 0) ctr[b] = 0;  // all warps are done with the buffer's previous tile
       __syncwarp();
       if (p.use_tma) {
         if (lane == 0) {
@@ -254,7 +260,7 @@ __device__ __forceinline__ bool products_phase(const RecParams &p, const CUtenso
           tma_load_2d(dst, &tmap, x, y, &full[b]);
         }
       } else {
-        stage_tile_cpasync<T, PITCH>(p, tile, dst, &full[b], lane);
+        stage_tile_cpasync<T, PITCH>(p, tile, dst, &full[b], lane, pw, NPW);
       }
       issued = tile - tf;
     }
