@@ -47,8 +47,11 @@ template <typename T> __device__ __forceinline__ T scan_suffix(T x, int lane) {
 // inside the box of column offset j (suffix scan over the left fringe
 // columns, prefix scan over the right ones).
 template <typename T>
-__device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int lane) {
+__device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int lane,
+                                                  typename C2t<T>::type *cv_out = nullptr) {
   using C2 = typename C2t<T>::type;
+  // CV[D][j] goes to cv_out[j] when given, else to the workspace's colval
+  C2 *cvo = cv_out ? cv_out : (C2 *)p.colval + (long long)D * p.Q;
   const int P = p.P, Q = p.Q;
   int dr, dc;
   combo_of(P, D, dr, dc);
@@ -107,7 +110,7 @@ __device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int
       C2 o;
       o.x = vr.value();
       o.y = vi.value();
-      ((C2 *)p.colval)[(long long)D * Q + lane] = o;
+      cvo[lane] = o;
     }
     return;
   }
@@ -154,7 +157,7 @@ __device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int
     C2 o;
     o.x = vr.value();
     o.y = vi.value();
-    ((C2 *)p.colval)[(long long)D * Q + lane] = o;
+    cvo[lane] = o;
   }
 }
 
@@ -167,7 +170,8 @@ __device__ __forceinline__ void reduce_combo_warp(const RecParams &p, int D, int
 // sums in registers. The lane's J = Q - dc outputs are stored per j, lanes
 // again contiguous.
 template <typename T, int QMAX>
-__device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int lane) {
+__device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int lane,
+                                                 typename C2t<T>::type *rv_out = nullptr) {
   using C2 = typename C2t<T>::type;
   const int P = p.P, Q = p.Q, W = p.M - p.Q + 1, NFR = p.NFR, NFC = p.NFC, NCH = p.NCH;
   int dr, dc;
@@ -175,7 +179,9 @@ __device__ __forceinline__ void reduce_rows_warp(const RecParams &p, int D, int 
   const int J = Q - dc;
   const C2 *A = (const C2 *)p.A;
   const C2 *sin_d = (const C2 *)p.sin_part + (long long)D * NCH * NFR;
-  C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR;
+  // RV[D][j][fr] goes to rv_out[j * NFR + fr] when given, else to the
+  // workspace's rowval
+  C2 *rv = rv_out ? rv_out : (C2 *)p.rowval + (long long)D * Q * NFR;
   for (int fr = lane; fr < NFR; fr += 32) {
     const int n = fringe_row(P, p.n_inner, fr);
     const bool rowok = n + dr >= 0 && n + dr < p.N;
