@@ -11,12 +11,12 @@
 //      tasks) member by member; each member's lag group (4, 8 or 16) is
 //      chosen by its own plan;
 //   2. fringe rows x inner columns: the fringe-row CTAs of every member;
-//   3. one warp per (member, combination): the combination's reductions (CV
-//      and the box-row sums RV, rec_reduce.cuh's warp tasks) into shared
-//      memory, then its diagonal segments, one lane each: seed, walk,
-//      divide by K, write the outputs and their mirrors.
-// Stage 3 numbers the combinations across the batch, so that a large member
-// is spread over many CTAs.
+//   3. the reductions as thread tasks over all members (CV of each
+//      combination, RV of each (combination, fringe row));
+//   4. one thread per diagonal segment of every member seeds, walks, divides
+//      by K and writes the outputs and their mirrors.
+// Stages 3 and 4 number their tasks across the batch (a member's tasks are
+// consecutive), so that a large member is spread over many CTAs.
 // The stages exchange the single-matrix partial sums through each member's
 // region of the workspace. The member plans are read from global memory as
 // the kernels' read-only input, their workspace addresses resolved when the
@@ -119,41 +119,201 @@ __global__ void __launch_bounds__(256) k_pipe_fringe(const RecParams *__restrict
 }
 
 // ---- 3. reductions, seed, walk and write ----------------------------------------
-// One warp per (member, combination D): CV of D (lanes over the fringe
-// columns) and RV of D (lanes over the fringe rows) into the warp's region of
-// shared memory, then the lanes take D's diagonal segments (column offset j,
-// chunk of L outputs): seed, walk, divide by K, write each output and its
-// mirror. The row sums never leave the SM.
-template <typename T, int QMAX>
-__global__ void __launch_bounds__(256) k_pipe_combo(const RecParams *__restrict__ mp,
-                                                     const int *__restrict__ members,
-                                                     const long long *__restrict__ first, int n,
-                                                     long long total, int stride) {
+// Thread task: CV[D][j] of combination D for every column offset j (the
+// inner-row box sums: core partials plus the fringe-column sums in the box;
+// suffix and prefix running sums where a box holds Q - 1 fringe columns,
+// window sums otherwise).
+template <typename T>
+__device__ __forceinline__ void cv_thread(const RecParams &p, int D) {
   using C2 = typename C2t<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_pc[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long t = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (t >= total) return;  // the whole warp
-  const int j = find_member(first, n, t);
-  const RecParams &p = mp[members[j]];
-  const int D = (int)(t - first[j]);
-  C2 *cv = (C2 *)smem_pc + (size_t)warp * stride;  // [Q]
-  C2 *rv = cv + p.Q;                                // [Q][NFR]
-  reduce_combo_warp<T>(p, D, lane, cv);
-  reduce_rows_warp<T, QMAX>(p, D, lane, rv);
-  __syncwarp();
+  const int Q = p.Q, NFC = p.NFC, n_rb = p.n_rb;
   int dr, dc;
   combo_of(p.P, D, dr, dc);
-  const int adr = dr < 0 ? -dr : dr;
-  const int I = p.P - adr, i0 = dr < 0 ? -dr : 0;
-  const int nchunk = (p.P + p.L - 1) / p.L, J = p.Q - dc;
-  for (int u = lane; u < J * nchunk; u += 32) {
-    const int jj = u % J, c = u / J;
-    const int is = i0 + c * p.L;
-    if (is >= i0 + I) continue;
-    const int ie = (i0 + I) < (is + p.L) ? (i0 + I) : (is + p.L);
-    walk_segment_rv<T>(p, rv + jj * p.NFR, cv[jj], (C2 *)p.R, dr, dc, jj, is, ie);
+  const int J = Q - dc;
+  Neu<T> cr, ci;
+  {
+    const int np = n_rb * p.n_cb;
+    const C2 *cp = (const C2 *)p.core_part + (long long)D * np;
+    for (int k = 0; k < np; ++k) {
+      const C2 x = cp[k];
+      cr.add(x.x);
+      ci.add(x.y);
+    }
   }
+  const C2 *cs = (const C2 *)p.colsum_part + (long long)D * n_rb * NFC;
+  auto colsum = [&](int fc) {
+    Neu<T> a, b;
+    for (int rb = 0; rb < n_rb; ++rb) {
+      const C2 x = cs[(long long)rb * NFC + fc];
+      a.add(x.x);
+      b.add(x.y);
+    }
+    C2 v;
+    v.x = a.value();
+    v.y = b.value();
+    return v;
+  };
+  C2 *cv = (C2 *)p.colval + (long long)D * Q;
+  if (NFC == 2 * (Q - 1)) {
+    // suffix over the left fringe columns k >= j, kept in cv[j] ...
+    T sr = T(0), si = T(0);
+    for (int k = Q - 2; k >= 0; --k) {
+      const C2 x = colsum(k);
+      sr += x.x;
+      si += x.y;
+      if (k < J) {
+        C2 o;
+        o.x = sr;
+        o.y = si;
+        cv[k] = o;
+      }
+    }
+    // ... then the core and the prefix over the right ones k < j
+    T pr = T(0), pi = T(0);
+    for (int j = 0; j < J; ++j) {
+      Neu<T> vr = cr, vi = ci;
+      if (j < Q - 1) {
+        vr.add(cv[j].x);
+        vi.add(cv[j].y);
+      }
+      vr.add(pr);
+      vi.add(pi);
+      C2 o;
+      o.x = vr.value();
+      o.y = vi.value();
+      cv[j] = o;
+      if (j < Q - 1) {
+        const C2 x = colsum(Q - 1 + j);
+        pr += x.x;
+        pi += x.y;
+      }
+    }
+  } else {
+    for (int j = 0; j < J; ++j) {
+      Neu<T> vr = cr, vi = ci;
+      for (int k = j; k < j + p.HC; ++k) {
+        const C2 x = colsum(k);
+        vr.add(x.x);
+        vi.add(x.y);
+      }
+      C2 o;
+      o.x = vr.value();
+      o.y = vi.value();
+      cv[j] = o;
+    }
+  }
+}
+
+// Thread task: RV[D][j][fr] of fringe row fr of combination D for every
+// column offset j: the row's inner-column sum S_in (its chunk partials) plus
+// its own fringe-column products (each formed once) inside the box of j. The
+// pointers are declared unaliased so that the loads of the running sums can
+// be issued ahead of the stores of the outputs.
+template <typename C2>
+__device__ __forceinline__ void rv_scan(const C2 *__restrict__ An, const C2 *__restrict__ Ab,
+                                        C2 *__restrict__ rv, C2 s_in, bool rowok, int Q, int J,
+                                        int W, int dc, int M, int NFR) {
+  // suffix of the left fringe-column products (m = k >= j) ...
+  C2 acc = czero<C2>();
+#pragma unroll 4
+  for (int k = Q - 2; k >= 0; --k) {
+    if (rowok) cmac_conj(acc, An[k], Ab[k]);
+    if (k < J) {
+      C2 o;
+      o.x = s_in.x + acc.x;
+      o.y = s_in.y + acc.y;
+      rv[(long long)k * NFR] = o;
+    }
+  }
+  if (Q - 1 < J) rv[(long long)(Q - 1) * NFR] = s_in;
+  // ... plus the prefix of the right ones (m = W + k, k < j)
+  C2 pre = czero<C2>();
+#pragma unroll 4
+  for (int j = 1; j < J; ++j) {
+    const int k = j - 1;
+    if (rowok && W + k + dc < M) cmac_conj(pre, An[W + k], Ab[W + k]);
+    C2 o = rv[(long long)j * NFR];
+    o.x += pre.x;
+    o.y += pre.y;
+    rv[(long long)j * NFR] = o;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void rv_thread(const RecParams &p, int D, int fr) {
+  using C2 = typename C2t<T>::type;
+  const int P = p.P, Q = p.Q, NFR = p.NFR, NFC = p.NFC, NCH = p.NCH;
+  int dr, dc;
+  combo_of(P, D, dr, dc);
+  const int J = Q - dc;
+  const int n = fringe_row(P, p.n_inner, fr);
+  const bool rowok = n + dr >= 0 && n + dr < p.N;
+  C2 s_in = czero<C2>();
+  {
+    const C2 *sp = (const C2 *)p.sin_part + (long long)D * NCH * NFR + fr;
+    for (int cc = 0; cc < NCH; ++cc) {
+      const C2 x = sp[(long long)cc * NFR];
+      s_in.x += x.x;
+      s_in.y += x.y;
+    }
+  }
+  const C2 *A = (const C2 *)p.A;
+  const C2 *An = A + (long long)n * p.lda;
+  const C2 *Ab = A + (long long)(rowok ? n + dr : n) * p.lda + dc;
+  C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR + fr;
+  if (NFC == 2 * (Q - 1)) {
+    rv_scan<C2>(An, Ab, rv, s_in, rowok, Q, J, p.M - Q + 1, dc, p.M, NFR);
+  } else {
+    C2 pr[2 * kMaxPQ];
+    for (int k = 0; k < NFC; ++k) {
+      const int m = fringe_col(Q, p.n_innerc, k);
+      C2 v = czero<C2>();
+      if (rowok && m + dc < p.M) cmac_conj(v, __ldg(An + m), __ldg(Ab + m));
+      pr[k] = v;
+    }
+    for (int j = 0; j < J; ++j) {
+      C2 w = czero<C2>();
+      for (int k = j; k < j + p.HC; ++k) {
+        w.x += pr[k].x;
+        w.y += pr[k].y;
+      }
+      C2 o;
+      o.x = s_in.x + w.x;
+      o.y = s_in.y + w.y;
+      rv[(long long)j * NFR] = o;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pipe_reduce(const RecParams *__restrict__ mp,
+                                                      const int *__restrict__ members,
+                                                      const long long *__restrict__ first, int n,
+                                                      long long total) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int j = find_member(first, n, t);
+  const RecParams &p = mp[members[j]];
+  const long long u = t - first[j];  // [0, n_uc): CV tasks; then RV tasks, fringe row fastest
+  if (u < p.n_uc)
+    cv_thread<T>(p, (int)u);
+  else
+    rv_thread<T>(p, (int)((u - p.n_uc) / p.NFR), (int)((u - p.n_uc) % p.NFR));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pipe_walk(const RecParams *__restrict__ mp,
+                                                    const int *__restrict__ members,
+                                                    const long long *__restrict__ first, int n,
+                                                    long long total) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int j = find_member(first, n, t);
+  const RecParams &p = mp[members[j]];
+  const long long u = t - first[j];  // (combination fastest, column offset, chunk)
+  const int D = (int)(u % p.n_uc);
+  const long long r = u / p.n_uc;
+  walk_segment<T>(p, D, (int)(r % p.Q), (int)(r / p.Q));
 }
 
 // ---------------------------------------------------------------------------
@@ -198,7 +358,8 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     region[k] = lay[k].total - lay[k].core_off;
     if (p.n_inner > 0 && p.n_tasks > 0) prod[p.PITCH].members.push_back(k);
     if (p.NFR > 0 && p.NCH > 0) fr[p.QMAXF].members.push_back(k);
-    fin[p.QMAXF].members.push_back(k);
+    fin[0].members.push_back(k);  // reductions
+    fin[1].members.push_back(k);  // walk
   }
   const int fpb = elem == 16 ? 32 : 256;
   for (auto &kv : prod) {
@@ -233,21 +394,17 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     c.smem = smem;
     pp.fringe.push_back(c);
   }
-  for (auto &kv : fin) {
+  for (auto &kv : fin) {  // key 0: reduction tasks; key 1: walk segments
     PipeClass &c = kv.second;
     c.key = kv.first;
     c.first.assign(1, 0);
-    int stride = 0;
     for (int k : c.members) {
       const RecParams &p = pp.params[k];
-      c.first.push_back(c.first.back() + p.n_uc);
-      stride = std::max(stride, p.Q * (1 + p.NFR));
+      const long long nt = c.key == 0 ? (long long)p.n_uc * (1 + p.NFR)
+                                      : (long long)p.n_uc * p.Q * ((p.P + p.L - 1) / p.L);
+      c.first.push_back(c.first.back() + nt);
     }
     c.total = c.first.back();
-    // warps per CTA: up to 8, their regions within 64 KB
-    c.stride = (stride + 1) & ~1;
-    c.warps = (int)std::min<size_t>(8, std::max<size_t>(1, (64 << 10) / ((size_t)c.stride * elem)));
-    c.smem = (size_t)c.warps * c.stride * elem;
     pp.finish.push_back(c);
   }
   // layout: the member plans, the class arrays, then each member's region;
@@ -328,19 +485,6 @@ static cudaError_t launch_pipe_fringe(const PipeClass &c, char *ws, const RecPar
   return cudaGetLastError();
 }
 
-template <typename T, int QMAX>
-static cudaError_t launch_pipe_combo(const PipeClass &c, char *ws, const RecParams *mp,
-                                     cudaStream_t s) {
-  auto kern = k_pipe_combo<T, QMAX>;
-  cudaError_t e = ensure_dyn_smem((const void *)kern, c.smem, true);
-  if (e != cudaSuccess) return e;
-  const long long grid = (c.total + c.warps - 1) / c.warps;
-  kern<<<(unsigned)grid, 32 * c.warps, c.smem, s>>>(
-      mp, (const int *)(ws + c.off_members), (const long long *)(ws + c.off_first),
-      (int)c.members.size(), c.total, c.stride);
-  return cudaGetLastError();
-}
-
 template <typename T>
 static cudaError_t pipe_launch_t(const PipePlan &pp, char *ws, int sms, cudaStream_t s) {
   const RecParams *mp = (const RecParams *)(ws + pp.off_params);
@@ -369,14 +513,14 @@ static cudaError_t pipe_launch_t(const PipePlan &pp, char *ws, int sms, cudaStre
   }
   for (const PipeClass &c : pp.finish) {
     if (c.total <= 0) continue;
-    switch (c.key) {
-      case 4: e = launch_pipe_combo<T, 4>(c, ws, mp, s); break;
-      case 8: e = launch_pipe_combo<T, 8>(c, ws, mp, s); break;
-      case 16: e = launch_pipe_combo<T, 16>(c, ws, mp, s); break;
-      case 32: e = launch_pipe_combo<T, 32>(c, ws, mp, s); break;
-      default: e = cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((c.total + 255) / 256);
+    const int *mem = (const int *)(ws + c.off_members);
+    const long long *first = (const long long *)(ws + c.off_first);
+    if (c.key == 0)
+      k_pipe_reduce<T><<<grid, 256, 0, s>>>(mp, mem, first, (int)c.members.size(), c.total);
+    else
+      k_pipe_walk<T><<<grid, 256, 0, s>>>(mp, mem, first, (int)c.members.size(), c.total);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -15,15 +15,15 @@ namespace cov {
 
 // Members grouped by a template parameter of a stage's kernel: the shared-
 // memory pitch of the product tiles, or the column-lag register count of the
-// fringe-row and reduction tasks.
+// fringe-row tasks; the last two stages: every member (key 0 the reductions,
+// key 1 the walk).
 struct PipeClass {
-  int key;                       // PITCH (products), QMAXF (fringe rows, last stage)
+  int key;                       // PITCH (products), QMAXF (fringe rows), 0 / 1 (last stages)
   std::vector<int> members;      // member indices, in launch order
   std::vector<long long> first;  // prefix over the members (members + 1 entries): products
-                                 // cost, fringe-row CTAs or combinations
+                                 // cost, fringe-row CTAs, reduction tasks or walk segments
   long long total = 0;           // its last entry
   size_t smem = 0;               // dynamic shared memory of the launch
-  int stride = 0, warps = 0;     // last stage: complex elements per warp region, warps per CTA
   size_t off_members = 0, off_first = 0;  // workspace offsets of the two arrays
 };
 
@@ -52,7 +52,7 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
 // the copies have run). The tables are valid for this workspace only.
 cudaError_t pipe_upload(const PipePlan &pp, char *ws, cudaStream_t s);
 
-// The launches: products, fringe rows, then reductions with the walk.
+// The launches: products, fringe rows, reductions, walk.
 cudaError_t pipe_launch(const PipePlan &pp, char *ws, int sms, cudaStream_t s);
 
 }  // namespace cov
