@@ -153,7 +153,9 @@ __device__ __forceinline__ void cv_thread(const RecParams &p, int D) {
     v.y = b.value();
     return v;
   };
-  C2 *cv = (C2 *)p.colval + (long long)D * Q;
+  // CV of the stage form: [j][D] (combination fastest)
+  const long long cs_j = p.n_uc;
+  C2 *cv = (C2 *)p.colval + D;
   if (NFC == 2 * (Q - 1)) {
     // suffix over the left fringe columns k >= j, kept in cv[j] ...
     T sr = T(0), si = T(0);
@@ -165,7 +167,7 @@ __device__ __forceinline__ void cv_thread(const RecParams &p, int D) {
         C2 o;
         o.x = sr;
         o.y = si;
-        cv[k] = o;
+        cv[k * cs_j] = o;
       }
     }
     // ... then the core and the prefix over the right ones k < j
@@ -173,15 +175,15 @@ __device__ __forceinline__ void cv_thread(const RecParams &p, int D) {
     for (int j = 0; j < J; ++j) {
       Neu<T> vr = cr, vi = ci;
       if (j < Q - 1) {
-        vr.add(cv[j].x);
-        vi.add(cv[j].y);
+        vr.add(cv[j * cs_j].x);
+        vi.add(cv[j * cs_j].y);
       }
       vr.add(pr);
       vi.add(pi);
       C2 o;
       o.x = vr.value();
       o.y = vi.value();
-      cv[j] = o;
+      cv[j * cs_j] = o;
       if (j < Q - 1) {
         const C2 x = colsum(Q - 1 + j);
         pr += x.x;
@@ -199,20 +201,22 @@ __device__ __forceinline__ void cv_thread(const RecParams &p, int D) {
       C2 o;
       o.x = vr.value();
       o.y = vi.value();
-      cv[j] = o;
+      cv[j * cs_j] = o;
     }
   }
 }
 
-// Thread task: RV[D][j][fr] of fringe row fr of combination D for every
-// column offset j: the row's inner-column sum S_in (its chunk partials) plus
-// its own fringe-column products (each formed once) inside the box of j. The
-// pointers are declared unaliased so that the loads of the running sums can
-// be issued ahead of the stores of the outputs.
+// Thread task: RV of fringe row fr of combination D for every column offset
+// j: the row's inner-column sum S_in (its chunk partials) plus its own
+// fringe-column products (each formed once) inside the box of j. The stage
+// form lays RV out as [j][fr][D] (combination fastest: consecutive threads
+// store, and the walk's threads load, consecutive elements); js is the
+// stride of j. The pointers are declared unaliased so that the loads of the
+// running sums can be issued ahead of the stores of the outputs.
 template <typename C2>
 __device__ __forceinline__ void rv_scan(const C2 *__restrict__ An, const C2 *__restrict__ Ab,
                                         C2 *__restrict__ rv, C2 s_in, bool rowok, int Q, int J,
-                                        int W, int dc, int M, int NFR) {
+                                        int W, int dc, int M, long long js) {
   // suffix of the left fringe-column products (m = k >= j) ...
   C2 acc = czero<C2>();
 #pragma unroll 4
@@ -222,20 +226,20 @@ __device__ __forceinline__ void rv_scan(const C2 *__restrict__ An, const C2 *__r
       C2 o;
       o.x = s_in.x + acc.x;
       o.y = s_in.y + acc.y;
-      rv[(long long)k * NFR] = o;
+      rv[k * js] = o;
     }
   }
-  if (Q - 1 < J) rv[(long long)(Q - 1) * NFR] = s_in;
+  if (Q - 1 < J) rv[(Q - 1) * js] = s_in;
   // ... plus the prefix of the right ones (m = W + k, k < j)
   C2 pre = czero<C2>();
 #pragma unroll 4
   for (int j = 1; j < J; ++j) {
     const int k = j - 1;
     if (rowok && W + k + dc < M) cmac_conj(pre, An[W + k], Ab[W + k]);
-    C2 o = rv[(long long)j * NFR];
+    C2 o = rv[j * js];
     o.x += pre.x;
     o.y += pre.y;
-    rv[(long long)j * NFR] = o;
+    rv[j * js] = o;
   }
 }
 
@@ -260,9 +264,10 @@ __device__ __forceinline__ void rv_thread(const RecParams &p, int D, int fr) {
   const C2 *A = (const C2 *)p.A;
   const C2 *An = A + (long long)n * p.lda;
   const C2 *Ab = A + (long long)(rowok ? n + dr : n) * p.lda + dc;
-  C2 *rv = (C2 *)p.rowval + (long long)D * Q * NFR + fr;
+  const long long js = (long long)NFR * p.n_uc;
+  C2 *rv = (C2 *)p.rowval + (long long)fr * p.n_uc + D;
   if (NFC == 2 * (Q - 1)) {
-    rv_scan<C2>(An, Ab, rv, s_in, rowok, Q, J, p.M - Q + 1, dc, p.M, NFR);
+    rv_scan<C2>(An, Ab, rv, s_in, rowok, Q, J, p.M - Q + 1, dc, p.M, js);
   } else {
     C2 pr[2 * kMaxPQ];
     for (int k = 0; k < NFC; ++k) {
@@ -280,7 +285,7 @@ __device__ __forceinline__ void rv_thread(const RecParams &p, int D, int fr) {
       C2 o;
       o.x = s_in.x + w.x;
       o.y = s_in.y + w.y;
-      rv[(long long)j * NFR] = o;
+      rv[j * js] = o;
     }
   }
 }
@@ -294,11 +299,11 @@ __global__ void __launch_bounds__(256) k_pipe_reduce(const RecParams *__restrict
   if (t >= total) return;
   const int j = find_member(first, n, t);
   const RecParams &p = mp[members[j]];
-  const long long u = t - first[j];  // [0, n_uc): CV tasks; then RV tasks, fringe row fastest
+  const long long u = t - first[j];  // [0, n_uc): CV tasks; then RV tasks, combination fastest
   if (u < p.n_uc)
     cv_thread<T>(p, (int)u);
   else
-    rv_thread<T>(p, (int)((u - p.n_uc) / p.NFR), (int)((u - p.n_uc) % p.NFR));
+    rv_thread<T>(p, (int)((u - p.n_uc) % p.n_uc), (int)((u - p.n_uc) / p.n_uc));
 }
 
 template <typename T>
@@ -313,7 +318,20 @@ __global__ void __launch_bounds__(256) k_pipe_walk(const RecParams *__restrict__
   const long long u = t - first[j];  // (combination fastest, column offset, chunk)
   const int D = (int)(u % p.n_uc);
   const long long r = u / p.n_uc;
-  walk_segment<T>(p, D, (int)(r % p.Q), (int)(r / p.Q));
+  const int jj = (int)(r % p.Q), c = (int)(r / p.Q);
+  int dr, dc;
+  combo_of(p.P, D, dr, dc);
+  if (jj >= p.Q - dc) return;
+  const int adr = dr < 0 ? -dr : dr;
+  const int I = p.P - adr, i0 = dr < 0 ? -dr : 0;
+  const int is = i0 + c * p.L;
+  if (is >= i0 + I) return;
+  const int ie = (i0 + I) < (is + p.L) ? (i0 + I) : (is + p.L);
+  using C2 = typename C2t<T>::type;
+  const long long n_uc = p.n_uc;
+  const C2 *RV = (const C2 *)p.rowval + (long long)jj * p.NFR * n_uc + D;  // [j][fr][D]
+  const C2 cv = ((const C2 *)p.colval)[jj * n_uc + D];                      // [j][D]
+  walk_segment_rv<T>(p, RV, n_uc, cv, (C2 *)p.R, dr, dc, jj, is, ie);
 }
 
 // ---------------------------------------------------------------------------

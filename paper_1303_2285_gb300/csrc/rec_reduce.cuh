@@ -775,17 +775,17 @@ __device__ __forceinline__ void walk_block(const RecParams &p, int dc, int bj, u
 
 // ---------------------------------------------------------------------------
 // Thread task: the same seed, walk and division as walk_block for one
-// diagonal segment (combination D, column offset j, chunk c of L outputs),
-// reading RV and CV from global memory and writing each output and its
-// conjugate mirror to R directly (no block staging: for batches of small
-// matrices, where a P x P block is too small to keep a CTA busy). The RV and
-// R pointers are declared unaliased so that the walk's loads can be issued
-// ahead of its stores.
+// diagonal segment of combination (dr, dc) at column offset j, outputs
+// is .. ie-1, from its box-row sums RV(u) = RV[u * rs] (any layout) and its
+// CV, writing each output and its conjugate mirror to R directly (no block
+// staging: for batches of small matrices, where a P x P block is too small
+// to keep a CTA busy). The RV and R pointers are declared unaliased so that
+// the walk's loads can be issued ahead of its stores.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void walk_segment_rv(const RecParams &p,
                                                 const typename C2t<T>::type *__restrict__ RV,
-                                                typename C2t<T>::type cv,
+                                                long long rs, typename C2t<T>::type cv,
                                                 typename C2t<T>::type *__restrict__ R, int dr,
                                                 int dc, int j, int is, int ie) {
   using C2 = typename C2t<T>::type;
@@ -797,15 +797,15 @@ __device__ __forceinline__ void walk_segment_rv(const RecParams &p,
     const int ue = is + p.H;
     int u = is;
     for (; u + 2 <= ue; u += 2) {
-      const C2 a = RV[u], b = RV[u + 1];
+      const C2 a = RV[u * rs], b = RV[(u + 1) * rs];
       orr.add(a.x);
       oii.add(a.y);
       o2r.add(b.x);
       o2i.add(b.y);
     }
     if (u < ue) {
-      orr.add(RV[u].x);
-      oii.add(RV[u].y);
+      orr.add(RV[u * rs].x);
+      oii.add(RV[u * rs].y);
     }
     orr.merge(o2r.s, o2r.c);
     oii.merge(o2i.s, o2i.c);
@@ -833,30 +833,12 @@ __device__ __forceinline__ void walk_segment_rv(const RecParams &p,
       R[b * DD + a] = o;
     }
     if (i + 1 < ie) {
-      orr.add(-RV[i].x);
-      oii.add(-RV[i].y);
-      orr.add(RV[p.H + i].x);
-      oii.add(RV[p.H + i].y);
+      orr.add(-RV[i * rs].x);
+      oii.add(-RV[i * rs].y);
+      orr.add(RV[(p.H + i) * rs].x);
+      oii.add(RV[(p.H + i) * rs].y);
     }
   }
-}
-
-// Returns without work for an empty segment.
-template <typename T>
-__device__ __forceinline__ void walk_segment(const RecParams &p, int D, int j, int c) {
-  using C2 = typename C2t<T>::type;
-  const int P = p.P;
-  int dr, dc;
-  combo_of(P, D, dr, dc);
-  if (j >= p.Q - dc) return;
-  const int adr = dr < 0 ? -dr : dr;
-  const int I = P - adr, i0 = dr < 0 ? -dr : 0;
-  const int is = i0 + c * p.L;
-  if (is >= i0 + I) return;
-  const int ie = (i0 + I) < (is + p.L) ? (i0 + I) : (is + p.L);
-  const C2 *RV = (const C2 *)p.rowval + ((long long)D * p.Q + j) * p.NFR;
-  const C2 cv = ((const C2 *)p.colval)[(long long)D * p.Q + j];
-  walk_segment_rv<T>(p, RV, cv, (C2 *)p.R, dr, dc, j, is, ie);
 }
 
 // Blocks (bj, bj + dc) of the shard's column lags, in launch order.
