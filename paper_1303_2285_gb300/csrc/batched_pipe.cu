@@ -363,10 +363,11 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
   for (int k = 0; k < count; ++k) {
     const cov_desc &d = descs[k];
     RecParams &p = pp.params[k];
-    // the plan's defaults, four stages, no tuning cache; FP32 fringe-row
-    // chunks of 128 columns (a small member's inner columns in one or two
-    // chunks: fewer CTAs and partial sums)
-    const Tuning t = {0, 0, 0, 4, 0, elem == 8 ? 128 : 0};
+    // the plan's defaults, four stages, no tuning cache; one walk segment
+    // per diagonal (the walk's threads are many already; fewer seeds);
+    // FP32 fringe-row chunks of 128 columns (a small member's inner columns
+    // in one or two chunks: fewer CTAs and partial sums)
+    const Tuning t = {0, 0, kMaxPQ, 4, 0, elem == 8 ? 128 : 0};
     plan_recurrence(d.N, d.M, d.lda, d.P, d.Q, elem, 0, p, lay[k], &t);
     p.A = d.A;
     p.R = d.R;
