@@ -390,7 +390,7 @@ void cov_batched_plan_destroy(cov_batched_plan *plan);
  *                   additions in a chain); 0 = one seed per segment; <= 16;
  *   row_ranges      form 0: at most this many row ranges (1, 2 or 4) per
  *                   column block of the inner-row product tasks.
- * A new plan starts at form = 2 where offered, else 1, else 0, else 3,
+ * A new plan starts at form = 2 where offered, else 1, else 3, else 0,
  * reseed_interval 0, row_ranges 4. */
 typedef struct {
   int32_t form;

@@ -37,13 +37,15 @@ def test_box_form_refused_beyond_its_limits():
         plan2.set_tuning(2)
 
 
-def test_wide_members_default_to_the_cta_form_and_refuse_the_warp_form():
+def test_wide_members_default_to_the_stage_form_and_refuse_the_warp_form():
     plan = make_plan([(25, 25, 10, 10), (64, 64, 8, 8)])  # M = 64 does not fit one warp
-    assert plan.tuning == {"form": 0, "reseed_interval": 0, "row_ranges": 4}
+    assert plan.tuning == {"form": 3, "reseed_interval": 0, "row_ranges": 4}
     with pytest.raises(cov.CovError):
         plan.set_tuning(1)
+    plan.set_tuning(0)  # the CTA form takes them too
+    assert plan.tuning["form"] == 0
     plan2 = make_plan([(40, 30, 4, 4)])  # N * M = 1200 > 1024
-    assert plan2.tuning["form"] == 0
+    assert plan2.tuning["form"] == 3
 
 
 def test_set_and_get_round_trip():
