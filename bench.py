@@ -1029,6 +1029,8 @@ def profile_case(case: str, knobs=None) -> int:  # noqa: C901 - one branch per c
             A = torch.from_numpy(wl.complex_normal((N, M), wl.BATCHED_SEED * 100003 + k, "c64")).cuda()
             items.append((A, torch.empty((P * Q, P * Q), dtype=torch.complex64, device="cuda"), P, Q))
         plan = cov.BatchedPlan(items)
+        if knobs:  # the batched plan's form (0 or 3); default: the plan's own
+            plan.set_tuning(int(knobs), 0, 4)
         ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
         plan.upload(ws)
         for _ in range(3):
