@@ -32,8 +32,9 @@
 
 namespace cov {
 
-constexpr int kStTR = 32;  // output tile of the inner stencil: 32 rows x 32 columns,
-constexpr int kStTC = 32;  // four consecutive rows a thread
+constexpr int kStRPT = 8;             // consecutive output rows a thread of the inner stencil
+constexpr int kStTR = 8 * kStRPT;     // its output tile: 8 warps x kStRPT rows
+constexpr int kStTC = 32;             // x 32 columns
 
 struct StParams {
   const float2 *A;
@@ -209,31 +210,33 @@ __global__ void __launch_bounds__(256) k_adjs_inner(const StParams p0) {
   }
   __syncthreads();
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  unsigned long long acc[4];
+  constexpr int RPT = kStRPT;
+  unsigned long long acc[RPT];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) acc[k] = 0ull;
+  for (int k = 0; k < RPT; ++k) acc[k] = 0ull;
   for (int dc = 0; dc < 2 * Q - 1; ++dc) {
     const ulonglong2 *wv = Ws + dc * DR;
-    const int base = (4 * ty) * SW + tx + dc;  // row 4ty of the window at dr = 0
+    const int base = (RPT * ty) * SW + tx + dc;  // row RPT*ty of the window at dr = 0
     const unsigned long long *col = As + base;
-    unsigned long long x[4], xs[4];
+    unsigned long long x[RPT - 1], xs[RPT - 1];
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
+    for (int u = 0; u < RPT - 1; ++u) {
       x[u] = col[u * SW];
       xs[u] = swap2(x[u]);
     }
-    // rows used at lag dr: 4ty+dr .. 4ty+dr+3 (at most 4ty+2P+1 < SH); four
-    // lags per round, so that the window rotates by register renaming
+    // rows used at lag dr: RPT*ty+dr .. RPT*ty+dr+RPT-1 (at most
+    // 8*RPT+2P-3 < SH); four lags per round, so that the window rotates by
+    // register renaming
     int dr = 0;
     for (; dr + 4 <= DR; dr += 4) {
-      unsigned long long y[7], ys[7];
+      unsigned long long y[RPT + 3], ys[RPT + 3];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
+      for (int u = 0; u < RPT - 1; ++u) {
         y[u] = x[u];
         ys[u] = xs[u];
       }
 #pragma unroll
-      for (int u = 3; u < 7; ++u) {
+      for (int u = RPT - 1; u < RPT + 3; ++u) {
         y[u] = col[(dr + u) * SW];
         ys[u] = swap2(y[u]);
       }
@@ -241,34 +244,40 @@ __global__ void __launch_bounds__(256) k_adjs_inner(const StParams p0) {
       for (int u = 0; u < 4; ++u) {
         const ulonglong2 w = wv[dr + u];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < RPT; ++k) {
           ffma2(acc[k], w.x, y[u + k]);
           ffma2(acc[k], w.y, ys[u + k]);
         }
       }
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
+      for (int u = 0; u < RPT - 1; ++u) {
         x[u] = y[u + 4];
         xs[u] = ys[u + 4];
       }
     }
     for (; dr < DR; ++dr) {
-      x[3] = col[(dr + 3) * SW];
-      xs[3] = swap2(x[3]);
+      const unsigned long long xl = col[(dr + RPT - 1) * SW], xls = swap2(xl);
       const ulonglong2 w = wv[dr];
-      cmac4_f2(acc, w.x, w.y, x, xs);
-      x[0] = x[1];
-      x[1] = x[2];
-      x[2] = x[3];
-      xs[0] = xs[1];
-      xs[1] = xs[2];
-      xs[2] = xs[3];
+#pragma unroll
+      for (int k = 0; k < RPT - 1; ++k) {
+        ffma2(acc[k], w.x, x[k]);
+        ffma2(acc[k], w.y, xs[k]);
+      }
+      ffma2(acc[RPT - 1], w.x, xl);
+      ffma2(acc[RPT - 1], w.y, xls);
+#pragma unroll
+      for (int k = 0; k < RPT - 2; ++k) {
+        x[k] = x[k + 1];
+        xs[k] = xs[k + 1];
+      }
+      x[RPT - 2] = xl;
+      xs[RPT - 2] = xls;
     }
   }
   const int m = m0 + tx;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int n = n0 + 4 * ty + k;
+  for (int k = 0; k < RPT; ++k) {
+    const int n = n0 + RPT * ty + k;
     if (n - (P - 1) < n_in && m - (Q - 1) < m_in) p.dA[(long long)n * p.M + m] = upk2(acc[k]);
   }
 }
