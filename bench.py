@@ -1000,8 +1000,8 @@ def profile_case(case: str, knobs=None) -> int:  # noqa: C901 - one branch per c
     the single-matrix combination path on the SAR-like 2048 x 512 input (32 x
     32 window) or on the 1024 x 1024 one (16 x 16), 600 uneven matrices
     through the batched launch (seed 3), the dense TF32x3 form on the
-    1024 x 1024 workload, the stencil adjoint of a batch of eight 256 x 256
-    inputs with a 12 x 12 window, the 30 x 30 apertures of 25 x 25 (stride
+    1024 x 1024 workload, the stencil adjoint of a batch of eight (or, with
+    the knob, that many) 256 x 256 inputs with a 12 x 12 window, the 30 x 30 apertures of 25 x 25 (stride
     10, 10 x 10 window) of a 315 x 315 image through the batched launch's
     default form, and the Capon spectra of those 900 estimates."""
     import numpy as np
@@ -1065,10 +1065,11 @@ def profile_case(case: str, knobs=None) -> int:  # noqa: C901 - one branch per c
     else:
         N = M = 256
         P = Q = 12
+        B = int(knobs) if knobs else 8  # members (the bench row's batch: 64)
         A = torch.stack([torch.from_numpy(wl.complex_normal((N, M), 4 + k, "c64"))
-                         for k in range(8)]).cuda()
+                         for k in range(B)]).cuda()
         G = torch.stack([torch.from_numpy(wl.complex_normal((P * Q, P * Q), 5 + k, "c64"))
-                         for k in range(8)]).cuda()
+                         for k in range(B)]).cuda()
         for _ in range(3):
             cov.estimate_backward_batch(A, G, P, Q)
     torch.cuda.synchronize()
