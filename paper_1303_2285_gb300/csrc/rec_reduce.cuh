@@ -401,14 +401,15 @@ __device__ __forceinline__ void reduce_combo_cta(const RecParams &p, int D, T *s
   }
   // the fringe-row x fringe-column products, each formed once (zero where
   // the partner falls outside A): warp w takes the fringe rows w, w + 8, ...;
-  // lane k the fringe columns k and k + 32 (NFC <= 62)
+  // lane k the fringe columns k and k + 32 (NFC <= 62); the rows' loads are
+  // unrolled so that a warp's loads of all its rows are in flight together
   {
     const C2 *A = (const C2 *)p.A;
     C2 *prod = (C2 *)(sm + L.prod);
     const int PS = red_prod_stride(NFC);
     const int m0 = fringe_col(Q, p.n_innerc, lane), m1 = fringe_col(Q, p.n_innerc, lane + 32);
     const bool c0 = lane < NFC && m0 + dc < p.M, c1 = lane + 32 < NFC && m1 + dc < p.M;
-#pragma unroll 2
+#pragma unroll 8
     for (int fr = warp; fr < NFR; fr += kRedThreads / 32) {
       const int n = fringe_row(P, p.n_inner, fr);
       const bool rowok = n + dr >= 0 && n + dr < p.N;
