@@ -48,7 +48,7 @@ FALLBACK_HBM_GBS = 6800.0
 NCU_TRAFFIC = {  # bytes per launch; profiles/launches_*.md, profiles/k_products_inner_*.md
     ("cn_1024x1024_w16_f32", "k_fused", "96da72e2c97e5ecd"): 8561408,
     ("cn_1024x1024_w16_f32", "k_products_inner", "96da72e2c97e5ecd"): 8438016,
-    ("sar_2048x512_w32_f32", "k_products_inner", "36991523223af072"): 8582485,
+    ("sar_2048x512_w32_f32", "k_products_inner", "e46608b38ef1696e"): 8582400,
 }
 KERNEL_SOURCES = ("cov_device.cuh", "cov_internal.h", "rec_common.cuh", "rec_products.cuh",
                   "rec_products.cu", "rec_fringe.cuh", "rec_fringe.cu", "rec_reduce.cuh",
