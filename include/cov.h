@@ -438,7 +438,10 @@ cov_status cov_capon_spectrum(const void *R, int count, int D, const void *steer
  *     H = (G + G^H) / K  (G + G^H for COV_SUM),  Y = H X,
  *     dA[n][m] = sum over windows w containing (n, m) of Y[(n-p) + P(m-q), w],
  * with X recomputed from A (never stored) and a gather-form col2im (one
- * writer per element of dA, no atomics). COV_C64 only.
+ * writer per element of dA, no atomics). COV_C64 (FP32) and, in the dense
+ * form only, COV_C128 (FP64; COV_BWD_AUTO picks it, COV_BWD_STENCIL is
+ * COV_EUNSUPPORTED; shapes whose H rows and A patch exceed shared memory,
+ * about PQ > 280, are COV_EUNSUPPORTED).
  * ------------------------------------------------------------------------- */
 /* Two forms of the same dA (equal up to rounding):
  *   COV_BWD_DENSE    the formula above (H X, (PQ)^2 complex MACs per window);

@@ -248,9 +248,10 @@ def estimate(A, P: int, Q: int, algo: str = "auto", norm: str = "mean", workspac
 BWD_FORMS = {"auto": 0, "dense": 1, "stencil": 2}
 
 
-def backward_workspace_size(N: int, M: int, P: int, Q: int, form: str = "auto") -> int:
+def backward_workspace_size(N: int, M: int, P: int, Q: int, form: str = "auto",
+                            dtype: str = "c64") -> int:
     out = ctypes.c_size_t(0)
-    _check(load().cov_backward_workspace_size_ex(DTYPES["c64"], N, M, P, Q, BWD_FORMS[form],
+    _check(load().cov_backward_workspace_size_ex(DTYPES[dtype], N, M, P, Q, BWD_FORMS[form],
                                                  ctypes.byref(out)),
            "cov_backward_workspace_size")
     return int(out.value)
@@ -258,21 +259,24 @@ def backward_workspace_size(N: int, M: int, P: int, Q: int, form: str = "auto") 
 
 def estimate_backward(A, G, P: int, Q: int, norm: str = "mean", workspace=None, stream=None,
                       form: str = "auto"):
-    """dL/dA for G = dL/dR (complex64 CUDA tensors; dL/dRe + i dL/dIm convention).
-    ``form``: "auto" (stencil where it applies), "stencil" or "dense"."""
+    """dL/dA for G = dL/dR (CUDA tensors, both complex64 or both complex128;
+    dL/dRe + i dL/dIm convention). ``form``: "auto" (complex64: the stencil
+    where it applies; complex128: the dense form in FP64), "stencil" or
+    "dense"."""
     torch = _torch()
-    if not (A.is_cuda and G.is_cuda) or A.dtype != torch.complex64 or G.dtype != torch.complex64:
-        raise ValueError("A and G must be complex64 CUDA tensors")
+    if not (A.is_cuda and G.is_cuda) or A.dtype != G.dtype:
+        raise ValueError("A and G must be CUDA tensors of one dtype")
+    dt = _dtype_of(A)
     A = A.contiguous()
     G = G.contiguous()
     N, M = A.shape
     if tuple(G.shape) != (P * Q, P * Q):
         raise ValueError("G must be PQ x PQ")
-    need = backward_workspace_size(N, M, P, Q, form)
+    need = backward_workspace_size(N, M, P, Q, form, dt)
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=A.device)
     dA = torch.empty_like(A)
-    _check(load().cov_estimate_backward_ex(A.data_ptr(), G.data_ptr(), DTYPES["c64"], N, M, P, Q,
+    _check(load().cov_estimate_backward_ex(A.data_ptr(), G.data_ptr(), DTYPES[dt], N, M, P, Q,
                                            NORMS[norm], BWD_FORMS[form], dA.data_ptr(),
                                            workspace.data_ptr(), workspace.numel(),
                                            _stream_ptr(stream)),
@@ -333,7 +337,7 @@ _autograd_fn = None
 def covariance(A, P: int, Q: int, norm: str = "mean"):
     """Differentiable estimate: R = covariance(A, P, Q); backward runs the
     library's adjoint (the stencil form where it applies, else (G + G^H) X
-    with a gather col2im). complex64 CUDA tensors."""
+    with a gather col2im). complex64 or complex128 CUDA tensors."""
     global _autograd_fn
     if _autograd_fn is None:
         _autograd_fn = _make_autograd()

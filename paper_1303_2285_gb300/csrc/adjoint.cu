@@ -8,7 +8,9 @@
 // window's column stack) is never stored; each CTA gathers its windows' values
 // from a staged patch of A. Kernel 2 is the col2im in gather form: one thread
 // per element of dA sums the entries of Y that belong to it, so every element
-// of dA has one writer and no atomics are needed.
+// of dA has one writer and no atomics are needed. Both are templated on the
+// real type: FP32 for complex64, FP64 for complex128 (this dense form is the
+// adjoint of complex128 estimates).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,11 +33,12 @@ constexpr int kAdjTA = 48;   // rows a of Y per CTA
 constexpr int kAdjTW = 128;  // windows per CTA (one window row p, consecutive q)
 constexpr int kAdjPQMax = 1024;
 
-struct AdjParams {
-  const float2 *A;
-  const float2 *G;
-  float2 *Y;   // [PQ][KW], window index w = p * W + q
-  float2 *dA;  // N x M, leading dimension M
+template <typename T> struct AdjParams {
+  using C2 = typename C2t<T>::type;
+  const C2 *A;
+  const C2 *G;
+  C2 *Y;   // [PQ][KW], window index w = p * W + q
+  C2 *dA;  // N x M, leading dimension M
   long long lda;
   int N, M, P, Q, W, Hn;  // W = M-Q+1 window columns, Hn = N-P+1 window rows
   long long KW;           // number of windows
@@ -45,11 +48,13 @@ struct AdjParams {
 // Y[a][w] for a in [a0, a0+48), w = p*W + q, q in [q0, q0+128).
 // Thread (ta, tw) of a 16 x 16 grid: a = a0 + ta + 16k (k < 3),
 // q = q0 + tw + 16l (l < 8): 24 complex accumulators.
-__global__ void __launch_bounds__(256) k_adj_hx(const AdjParams p) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_hx(const AdjParams<T> p) {
+  using C2 = typename C2t<T>::type;
   extern __shared__ __align__(16) unsigned char smem_adj[];
   const int D = p.P * p.Q;
-  float2 *Hs = (float2 *)smem_adj;                // [48][D]
-  float2 *As = Hs + kAdjTA * D;                   // [P][128 + Q - 1]
+  C2 *Hs = (C2 *)smem_adj;                        // [48][D]
+  C2 *As = Hs + kAdjTA * D;                       // [P][128 + Q - 1]
   const int AP = kAdjTW + p.Q - 1;
   const int nqc = (p.W + kAdjTW - 1) / kAdjTW;
   int bid = blockIdx.x;
@@ -61,14 +66,14 @@ __global__ void __launch_bounds__(256) k_adj_hx(const AdjParams p) {
   // H rows a0..a0+47: H[a][b] = (G[a][b] + conj(G[b][a])) / K
   for (int e = threadIdx.x; e < kAdjTA * D; e += blockDim.x) {
     const int ar = e / D, b = e - ar * D, a = a0 + ar;
-    float2 h = make_float2(0.f, 0.f);
+    C2 h = czero<C2>();
     if (a < D) {
-      const float2 g1 = p.G[(long long)a * D + b], g2 = p.G[(long long)b * D + a];
+      const C2 g1 = p.G[(long long)a * D + b], g2 = p.G[(long long)b * D + a];
       h.x = g1.x + g2.x;
       h.y = g1.y - g2.y;
       if (p.mean) {
-        h.x = h.x / (float)p.KW;
-        h.y = h.y / (float)p.KW;
+        h.x = h.x / (T)p.KW;
+        h.y = h.y / (T)p.KW;
       }
     }
     Hs[e] = h;
@@ -77,18 +82,18 @@ __global__ void __launch_bounds__(256) k_adj_hx(const AdjParams p) {
   for (int e = threadIdx.x; e < p.P * AP; e += blockDim.x) {
     const int r = e / AP, c = e - r * AP;
     const int gc = q0 + c;
-    As[e] = gc < p.M ? p.A[(long long)(pw + r) * p.lda + gc] : make_float2(0.f, 0.f);
+    As[e] = gc < p.M ? p.A[(long long)(pw + r) * p.lda + gc] : czero<C2>();
   }
   __syncthreads();
   const int ta = threadIdx.x >> 4, tw = threadIdx.x & 15;
-  float2 acc[3][8];
+  C2 acc[3][8];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
 #pragma unroll
-    for (int l = 0; l < 8; ++l) acc[k][l] = make_float2(0.f, 0.f);
+    for (int l = 0; l < 8; ++l) acc[k][l] = czero<C2>();
   for (int jb = 0, b = 0; jb < p.Q; ++jb)
   for (int ib = 0; ib < p.P; ++ib, ++b) {
-    float2 h[3], x[8];
+    C2 h[3], x[8];
 #pragma unroll
     for (int k = 0; k < 3; ++k) h[k] = Hs[(ta + 16 * k) * D + b];
 #pragma unroll
@@ -116,23 +121,62 @@ __global__ void __launch_bounds__(256) k_adj_hx(const AdjParams p) {
 }
 
 // dA[n][m] = sum over (i, j) with window (n-i, m-j) valid of Y[i + P j][(n-i) W + (m-j)].
-__global__ void __launch_bounds__(256) k_adj_col2im(const AdjParams p) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_col2im(const AdjParams<T> p) {
+  using C2 = typename C2t<T>::type;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)p.N * p.M) return;
   const int n = (int)(idx / p.M), m = (int)(idx - (long long)n * p.M);
   const int i_lo = n - (p.Hn - 1) > 0 ? n - (p.Hn - 1) : 0, i_hi = n < p.P - 1 ? n : p.P - 1;
   const int j_lo = m - (p.W - 1) > 0 ? m - (p.W - 1) : 0, j_hi = m < p.Q - 1 ? m : p.Q - 1;
-  float sr = 0.f, si = 0.f;
+  T sr = T(0), si = T(0);
   for (int j = j_lo; j <= j_hi; ++j)
     for (int i = i_lo; i <= i_hi; ++i) {
-      const float2 y = p.Y[(long long)(i + p.P * j) * p.KW + (long long)(n - i) * p.W + (m - j)];
+      const C2 y = p.Y[(long long)(i + p.P * j) * p.KW + (long long)(n - i) * p.W + (m - j)];
       sr += y.x;
       si += y.y;
     }
-  p.dA[idx] = make_float2(sr, si);
+  C2 o;
+  o.x = sr;
+  o.y = si;
+  p.dA[idx] = o;
 }
 
 }  // namespace cov
+
+namespace {
+template <typename T>
+cov_status dense_adjoint(const void *A, const void *G, int64_t N, int64_t M, int P, int Q,
+                         cov_norm norm, void *dA, void *workspace, cudaStream_t s) {
+  using C2 = typename cov::C2t<T>::type;
+  cov::AdjParams<T> p;
+  p.A = (const C2 *)A;
+  p.G = (const C2 *)G;
+  p.Y = (C2 *)((char *)workspace + cov::kWsHeader);
+  p.dA = (C2 *)dA;
+  p.lda = M;
+  p.N = (int)N;
+  p.M = (int)M;
+  p.P = P;
+  p.Q = Q;
+  p.W = (int)(M - Q + 1);
+  p.Hn = (int)(N - P + 1);
+  p.KW = (long long)p.W * p.Hn;
+  p.mean = norm == COV_MEAN ? 1 : 0;
+  const int D = P * Q;
+  const size_t smem = ((size_t)cov::kAdjTA * D + (size_t)P * (cov::kAdjTW + Q - 1)) * sizeof(C2);
+  if (smem > 227 * 1024) return COV_EUNSUPPORTED;
+  if (cov::ensure_dyn_smem((const void *)cov::k_adj_hx<T>, smem, false) != cudaSuccess)
+    return COV_ECUDA;
+  const long long nqc = (p.W + cov::kAdjTW - 1) / cov::kAdjTW;
+  const long long grid1 = nqc * p.Hn * ((D + cov::kAdjTA - 1) / cov::kAdjTA);
+  cov::k_adj_hx<T><<<(unsigned)grid1, 256, smem, s>>>(p);
+  if (cudaGetLastError() != cudaSuccess) return COV_ECUDA;
+  const long long grid2 = (N * M + 255) / 256;
+  cov::k_adj_col2im<T><<<(unsigned)grid2, 256, 0, s>>>(p);
+  return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
+}
+}  // namespace
 
 extern "C" {
 
@@ -163,8 +207,10 @@ static cov_bwd_form resolve_bwd(cov_bwd_form f, int64_t N, int64_t M, int P, int
 cov_status cov_backward_workspace_size_ex(cov_dtype dtype, int64_t N, int64_t M, int P, int Q,
                                           cov_bwd_form form, size_t *bytes) {
   if (!bytes || !bwd_args_ok(N, M, P, Q)) return COV_EINVAL;
-  if (dtype != COV_C64) return COV_EUNSUPPORTED;
-  form = resolve_bwd(form, N, M, P, Q);
+  if (dtype != COV_C64 && dtype != COV_C128) return COV_EINVAL;
+  // complex128: the dense form (FP64) only
+  form = dtype == COV_C128 && form == COV_BWD_AUTO ? COV_BWD_DENSE : resolve_bwd(form, N, M, P, Q);
+  if (dtype == COV_C128 && form == COV_BWD_STENCIL) return COV_EUNSUPPORTED;
   if (form == COV_BWD_STENCIL) {
     if (!cov::stencil_adjoint_ok(N, M, P, Q)) return COV_EUNSUPPORTED;
     *bytes = cov::stencil_adjoint_workspace(P, Q, 1);
@@ -173,7 +219,8 @@ cov_status cov_backward_workspace_size_ex(cov_dtype dtype, int64_t N, int64_t M,
   if (form != COV_BWD_DENSE) return COV_EINVAL;
   if ((long long)P * Q > cov::kAdjPQMax) return COV_EUNSUPPORTED;
   const long long KW = (N - P + 1) * (M - Q + 1);
-  *bytes = cov::kWsHeader + (((size_t)P * Q * KW * 8 + 255) & ~(size_t)255);
+  const size_t elem = dtype == COV_C128 ? 16 : 8;
+  *bytes = cov::kWsHeader + (((size_t)P * Q * KW * elem + 255) & ~(size_t)255);
   return COV_OK;
 }
 
@@ -187,9 +234,10 @@ cov_status cov_estimate_backward_ex(const void *A, const void *G, cov_dtype dtyp
                                     void *dA, void *workspace, size_t ws_bytes, cov_stream_t stream) {
   if (!A || !G || !dA || !bwd_args_ok(N, M, P, Q) || (norm != COV_MEAN && norm != COV_SUM))
     return COV_EINVAL;
-  if (dtype != COV_C64) return COV_EUNSUPPORTED;
-  if ((((uintptr_t)A) & 7) || (((uintptr_t)G) & 7) || (((uintptr_t)dA) & 7)) return COV_EINVAL;
-  form = resolve_bwd(form, N, M, P, Q);
+  if (dtype != COV_C64 && dtype != COV_C128) return COV_EINVAL;
+  const uintptr_t al = dtype == COV_C128 ? 15 : 7;
+  if ((((uintptr_t)A) & al) || (((uintptr_t)G) & al) || (((uintptr_t)dA) & al)) return COV_EINVAL;
+  form = dtype == COV_C128 && form == COV_BWD_AUTO ? COV_BWD_DENSE : resolve_bwd(form, N, M, P, Q);
   size_t need = 0;
   const cov_status st = cov_backward_workspace_size_ex(dtype, N, M, P, Q, form, &need);
   if (st != COV_OK) return st;
@@ -201,32 +249,8 @@ cov_status cov_estimate_backward_ex(const void *A, const void *G, cov_dtype dtyp
                                        s, 1, 0, 0, 0) == cudaSuccess
                ? COV_OK
                : COV_ECUDA;
-  cov::AdjParams p;
-  p.A = (const float2 *)A;
-  p.G = (const float2 *)G;
-  p.Y = (float2 *)((char *)workspace + cov::kWsHeader);
-  p.dA = (float2 *)dA;
-  p.lda = M;
-  p.N = (int)N;
-  p.M = (int)M;
-  p.P = P;
-  p.Q = Q;
-  p.W = (int)(M - Q + 1);
-  p.Hn = (int)(N - P + 1);
-  p.KW = (long long)p.W * p.Hn;
-  p.mean = norm == COV_MEAN ? 1 : 0;
-  const int D = P * Q;
-  const size_t smem = ((size_t)cov::kAdjTA * D + (size_t)P * (cov::kAdjTW + Q - 1)) * sizeof(float2);
-  if (smem > 227 * 1024) return COV_EUNSUPPORTED;
-  if (cov::ensure_dyn_smem((const void *)cov::k_adj_hx, smem, false) != cudaSuccess)
-    return COV_ECUDA;
-  const long long nqc = (p.W + cov::kAdjTW - 1) / cov::kAdjTW;
-  const long long grid1 = nqc * p.Hn * ((D + cov::kAdjTA - 1) / cov::kAdjTA);
-  cov::k_adj_hx<<<(unsigned)grid1, 256, smem, s>>>(p);
-  if (cudaGetLastError() != cudaSuccess) return COV_ECUDA;
-  const long long grid2 = (N * M + 255) / 256;
-  cov::k_adj_col2im<<<(unsigned)grid2, 256, 0, s>>>(p);
-  return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
+  return dtype == COV_C128 ? dense_adjoint<double>(A, G, N, M, P, Q, norm, dA, workspace, s)
+                           : dense_adjoint<float>(A, G, N, M, P, Q, norm, dA, workspace, s);
 }
 
 cov_status cov_backward_strided_workspace_size(int batch, int64_t N, int64_t M, int P, int Q,

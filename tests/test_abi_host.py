@@ -158,5 +158,11 @@ def test_backward_workspace_by_form():
     assert st >= 23 ** 4 * 8 and de >= 144 * 245 * 245 * 8
     assert cov.backward_workspace_size(256, 256, 12, 12) == st  # auto picks the stencil
     assert cov.backward_workspace_size(9, 9, 9, 9) == cov.backward_workspace_size(9, 9, 9, 9, "dense")
+    # complex128: the dense form (FP64), Y twice the bytes; no stencil form
+    d128 = cov.backward_workspace_size(256, 256, 12, 12, "auto", "c128")
+    assert d128 == cov.backward_workspace_size(256, 256, 12, 12, "dense", "c128")
+    assert d128 - 256 >= 2 * (de - 256) - 256
+    with pytest.raises(cov.CovError):
+        cov.backward_workspace_size(256, 256, 12, 12, "stencil", "c128")
     with pytest.raises(cov.CovError):
         cov.backward_workspace_size(9, 9, 9, 9, "stencil")

@@ -102,3 +102,57 @@ def test_strided_batch_matches_oracle(oracle_mod, B, N, M, P, Q, norm):
         want = oracle_mod.cov_backward(A[k].astype(np.complex128), G[k].astype(np.complex128), P, Q,
                                        mean=(norm == "mean"))
         assert rel_fro(dA[k], want) < F32_TOL
+
+
+# complex128: the dense form in FP64
+@pytest.mark.parametrize("N,M,P,Q", [(20, 17, 4, 3), (9, 9, 9, 9), (37, 50, 7, 5), (30, 12, 1, 1),
+                                     (64, 70, 12, 12), (11, 13, 6, 7)])
+def test_backward_complex128_integer_exact_and_gaussian(oracle_mod, N, M, P, Q):
+    # small integers, plain sum: every partial sum is an exact integer in FP64
+    A = wl.integer_valued((N, M), 21 + N)
+    G = wl.integer_valued((P * Q, P * Q), 22 + M)
+    dA = cov.estimate_backward(torch.from_numpy(A).cuda(), torch.from_numpy(G).cuda(), P, Q,
+                               norm="sum")
+    assert dA.dtype == torch.complex128
+    want = oracle_mod.cov_backward(A, G, P, Q, mean=False)
+    assert np.array_equal(dA.cpu().numpy(), want)
+    A = wl.complex_normal((N, M), 23 + N)
+    G = wl.complex_normal((P * Q, P * Q), 24 + M)
+    dA = cov.estimate_backward(torch.from_numpy(A).cuda(), torch.from_numpy(G).cuda(), P, Q)
+    assert rel_fro(dA.cpu().numpy(), oracle_mod.cov_backward(A, G, P, Q)) < 1e-12
+
+
+def test_backward_complex128_refuses_the_stencil_form():
+    with pytest.raises(cov.CovError) as e:
+        cov.estimate_backward(torch.zeros((40, 40), dtype=torch.complex128, device="cuda"),
+                              torch.zeros((16, 16), dtype=torch.complex128, device="cuda"), 4, 4,
+                              form="stencil")
+    assert e.value.code == 5
+
+
+def test_autograd_complex128_against_fd(oracle_mod):
+    # the whole differentiable estimate in FP64: forward (combination path)
+    # and adjoint (dense form), against central differences of the oracle's loss
+    N = M = 12
+    P = Q = 3
+    A = wl.complex_normal((N, M), 31, dtype="c128")
+    T = oracle_mod.cov_window(wl.complex_normal((N, M), 5001, dtype="c128"), P, Q)
+    At = torch.tensor(A, device="cuda", requires_grad=True)
+    R = cov.covariance(At, P, Q)
+    loss = (R - torch.tensor(T, device="cuda")).abs().pow(2).sum()
+    loss.backward()
+    got = At.grad.cpu().numpy()
+
+    def L(X):
+        return float(np.sum(np.abs(oracle_mod.cov_window(X, P, Q) - T) ** 2))
+
+    h = 1e-6
+    fd = np.zeros((N, M), np.complex128)
+    for n in range(N):
+        for m in range(M):
+            for unit in (1.0, 1j):
+                E = np.zeros((N, M), np.complex128)
+                E[n, m] = unit * h
+                d = (L(A + E) - L(A - E)) / (2 * h)
+                fd[n, m] += d * (1.0 if unit == 1.0 else 1j)
+    assert rel_fro(got, fd) < 1e-7
