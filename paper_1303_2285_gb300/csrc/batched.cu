@@ -1091,7 +1091,8 @@ cov_status cov_estimate_batched(const cov_batched_plan *plan, void *workspace, s
   if (dst != COV_OK) return dst;
   cudaStream_t s = (cudaStream_t)stream;
   char *w = (char *)workspace;
-  if (cudaMemsetAsync(w, 0, 4, s) != cudaSuccess) return COV_ECUDA;
+  // the status word, and the stage form's chunk counters (header words 1..4)
+  if (cudaMemsetAsync(w, 0, plan->form == 3 ? 32 : 4, s) != cudaSuccess) return COV_ECUDA;
   if (plan->form == 3)
     return cov::pipe_launch(plan->pipe, w, plan->sms, s) == cudaSuccess ? COV_OK : COV_ECUDA;
   const size_t smem = cov::kBSmemBytes;

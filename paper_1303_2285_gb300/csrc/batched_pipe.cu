@@ -3,10 +3,10 @@
 // single-matrix combination path (Sections 3.1-3.4; see cov_internal.h),
 // each stage one launch over all members, so that a batch of small matrices
 // gets the single-matrix kernels' shared-memory tiles and register blocks:
-//   1. products over the inner rows: one persistent CTA per SM takes an
-//      equal share of the concatenated task list of all members, weighted
-//      by each task's rows and lags (a share may start and end inside a
-//      member), and runs the product pipeline of rec_products.cuh (tiles
+//   1. products over the inner rows: one persistent CTA per SM takes chunks
+//      of the members' product tasks (up to four tiles of one member,
+//      costliest first) from a counter until none is left, and runs the
+//      product pipeline of rec_products.cuh on each (tiles
 //      staged with cp.async by four producer warps, consumer warps taking
 //      tasks) member by member; each member's lag group (4, 8 or 16) is
 //      chosen by its own plan;
@@ -59,24 +59,25 @@ template <typename T> struct PipeProd;
 template <> struct PipeProd<float> { static constexpr int R = 16, NCW = 12, NPW = 4; };
 template <> struct PipeProd<double> { static constexpr int R = 8, NCW = 12, NPW = 4; };
 
-// A CTA's share is a range of the class's cost axis: member j spans
-// [first[j], first[j + 1]) with n_tasks tasks of equal cost; task t belongs
-// to the CTA whose range holds first[j] + t * cost.
+// Dynamic schedule: the class's product tasks are cut into chunks (a
+// member's tasks of up to four tiles), listed costliest first; each CTA takes
+// the next chunk from a counter in the workspace header until none is left,
+// and runs the product pipeline on it.
 template <typename T, int PITCH>
 __global__ void __launch_bounds__((PipeProd<T>::NCW + PipeProd<T>::NPW) * 32, 1)
-    k_pipe_products(const RecParams *__restrict__ mp, const int *__restrict__ members,
-                    const long long *__restrict__ first, int n, long long total) {
+    k_pipe_products(const RecParams *__restrict__ mp, const int *__restrict__ chunk_member,
+                    const long long *__restrict__ chunk_range, int n_chunks, unsigned *counter) {
   constexpr int R = PipeProd<T>::R, NCW = PipeProd<T>::NCW, NPW = PipeProd<T>::NPW;
   extern __shared__ __align__(1024) unsigned char smem_pp[];
-  const long long cb = total * blockIdx.x / gridDim.x;
-  const long long ce = total * (blockIdx.x + 1) / gridDim.x;
-  if (cb >= ce) return;
-  for (int j = find_member(first, n, cb); j < n && first[j] < ce; ++j) {
-    const RecParams &p = mp[members[j]];
-    const long long f0 = first[j], w = (first[j + 1] - f0) / p.n_tasks;
-    const long long lo = (cb > f0 ? cb : f0) - f0, hi = (ce < first[j + 1] ? ce : first[j + 1]) - f0;
-    const long long a = (lo + w - 1) / w, b = (hi + w - 1) / w;
-    if (a >= b) continue;
+  __shared__ int cur;
+  for (;;) {
+    if (threadIdx.x == 0) cur = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int c = cur;
+    __syncthreads();  // every thread has read cur before the next claim
+    if (c >= n_chunks) return;
+    const RecParams &p = mp[chunk_member[c]];
+    const long long a = chunk_range[2 * c], b = chunk_range[2 * c + 1];
     bool ok = false;
     if (p.G == 4) {
       ok = products_phase<T, 4, R, PITCH, NCW, NPW>(p, g_pipe_no_map, smem_pp, a, b);
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__((PipeProd<T>::NCW + PipeProd<T>::NPW) * 32, 1)
       ok = products_phase<T, 16, R, PITCH, NCW, NPW>(p, g_pipe_no_map, smem_pp, a, b);
     }
     // every warp is done with the tiles and the barriers: invalidate them
-    // before the next member's pipeline initialises its own
+    // before the next chunk's pipeline initialises its own
     ok = __syncthreads_and(ok) != 0;
     if (threadIdx.x == 0) {
       uint64_t *bars = (uint64_t *)(smem_pp + 2 * tile_buf_bytes<T, PITCH>(p.STR));
@@ -381,20 +382,39 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     fin[1].members.push_back(k);  // walk
   }
   const int fpb = elem == 16 ? 32 : 256;
+  int slot = 0;  // the counter word of each product launch in the workspace header
   for (auto &kv : prod) {
     PipeClass &c = kv.second;
     c.key = kv.first;
-    c.first.assign(1, 0);
     int str = 0;
+    // chunks of up to four tiles of one member; cost = tasks x (a task's rows,
+    // the member's mean over its row blocks, times its lags, plus its
+    // epilogue); costliest first
+    struct Chunk {
+      int k;
+      long long a, b, cost;
+    };
+    std::vector<Chunk> ch;
     for (int k : c.members) {
-      // the cost axis: a task's rows (the member's mean over its row blocks)
-      // times its lags, plus its epilogue
       const RecParams &p = pp.params[k];
       const long long w = (long long)((p.n_inner + p.n_rb - 1) / p.n_rb) * p.G + 48;
-      c.first.push_back(c.first.back() + p.n_tasks * w);
+      const long long step = 4 * p.tasks_per_tile;
+      for (long long a = 0; a < p.n_tasks; a += step) {
+        const long long b = std::min(p.n_tasks, a + step);
+        ch.push_back({k, a, b, (b - a) * w});
+      }
       str = std::max(str, p.STR);
     }
-    c.total = c.first.back();
+    std::stable_sort(ch.begin(), ch.end(), [](const Chunk &x, const Chunk &y) { return x.cost > y.cost; });
+    c.members.clear();
+    c.first.clear();
+    for (const Chunk &x : ch) {
+      c.members.push_back(x.k);
+      c.first.push_back(x.a);
+      c.first.push_back(x.b);
+    }
+    c.total = (long long)ch.size();
+    c.counter = 4 * (1 + slot++);
     c.smem = 2 * ((((size_t)str * c.key * elem) + 1023) & ~(size_t)1023) + 64;
     pp.products.push_back(c);
   }
@@ -487,8 +507,8 @@ static cudaError_t launch_pipe_products(const PipeClass &c, char *ws, const RecP
   long long grid = sms;
   if (grid > c.total) grid = c.total;
   kern<<<(unsigned)grid, (PipeProd<T>::NCW + PipeProd<T>::NPW) * 32, c.smem, s>>>(
-      mp, (const int *)(ws + c.off_members), (const long long *)(ws + c.off_first),
-      (int)c.members.size(), c.total);
+      mp, (const int *)(ws + c.off_members), (const long long *)(ws + c.off_first), (int)c.total,
+      (unsigned *)(ws + c.counter));
   return cudaGetLastError();
 }
 

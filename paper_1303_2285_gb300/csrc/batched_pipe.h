@@ -19,10 +19,12 @@ namespace cov {
 // key 1 the walk).
 struct PipeClass {
   int key;                       // PITCH (products), QMAXF (fringe rows), 0 / 1 (last stages)
-  std::vector<int> members;      // member indices, in launch order
-  std::vector<long long> first;  // prefix over the members (members + 1 entries): products
-                                 // cost, fringe-row CTAs, reduction tasks or walk segments
-  long long total = 0;           // its last entry
+  std::vector<int> members;      // member indices, in launch order (products: per chunk)
+  std::vector<long long> first;  // products: task range [a, b) of each chunk; otherwise a
+                                 // prefix over the members (members + 1 entries): fringe-row
+                                 // CTAs, reduction tasks or walk segments
+  long long total = 0;           // chunks, or the prefix's last entry
+  size_t counter = 0;            // products: workspace offset of the launch's chunk counter
   size_t smem = 0;               // dynamic shared memory of the launch
   size_t off_members = 0, off_first = 0;  // workspace offsets of the two arrays
 };
