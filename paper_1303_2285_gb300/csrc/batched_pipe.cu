@@ -4,7 +4,7 @@
 // each stage one launch over all members, so that a batch of small matrices
 // gets the single-matrix kernels' shared-memory tiles and register blocks:
 //   1. products over the inner rows: one persistent CTA per SM takes chunks
-//      of the members' product tasks (up to four tiles of one member,
+//      of the members' product tasks (up to eight tiles of one member,
 //      costliest first) from a counter until none is left, and runs the
 //      product pipeline of rec_products.cuh on each (tiles
 //      staged with cp.async by four producer warps, consumer warps taking
@@ -60,7 +60,7 @@ template <> struct PipeProd<float> { static constexpr int R = 16, NCW = 12, NPW 
 template <> struct PipeProd<double> { static constexpr int R = 8, NCW = 12, NPW = 4; };
 
 // Dynamic schedule: the class's product tasks are cut into chunks (a
-// member's tasks of up to four tiles), listed costliest first; each CTA takes
+// member's tasks of up to eight tiles), listed costliest first; each CTA takes
 // the next chunk from a counter in the workspace header until none is left,
 // and runs the product pipeline on it.
 template <typename T, int PITCH>
@@ -387,7 +387,7 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     PipeClass &c = kv.second;
     c.key = kv.first;
     int str = 0;
-    // chunks of up to four tiles of one member; cost = tasks x (a task's rows,
+    // chunks of up to eight tiles of one member; cost = tasks x (a task's rows,
     // the member's mean over its row blocks, times its lags, plus its
     // epilogue); costliest first
     struct Chunk {
@@ -398,7 +398,7 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     for (int k : c.members) {
       const RecParams &p = pp.params[k];
       const long long w = (long long)((p.n_inner + p.n_rb - 1) / p.n_rb) * p.G + 48;
-      const long long step = 4 * p.tasks_per_tile;
+      const long long step = 8 * p.tasks_per_tile;
       for (long long a = 0; a < p.n_tasks; a += step) {
         const long long b = std::min(p.n_tasks, a + step);
         ch.push_back({k, a, b, (b - a) * w});
