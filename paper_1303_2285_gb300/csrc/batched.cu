@@ -1023,7 +1023,7 @@ cov_status cov_batched_plan_create(const cov_desc *descs, int count, cov_dtype d
   // the stage form's tables and member regions follow, where offered
   pl->pipe_ok = 0;
   if (pipe_members) {
-    cov::pipe_plan_build(pl->pipe, descs, count, dtype == COV_C128 ? 16 : 8, pl->mean, off);
+    cov::pipe_plan_build(pl->pipe, descs, count, dtype == COV_C128 ? 16 : 8, pl->mean, off, sms);
     if (pl->pipe.total <= kPipeMaxWorkspace || !cta) {
       pl->pipe_ok = 1;
       pl->total = pl->pipe.total;

@@ -352,7 +352,7 @@ bool pipe_members_ok(const cov_desc *descs, int count) {
 }
 
 void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, int mean,
-                     size_t off) {
+                     size_t off, int sms) {
   pp.elem = elem;
   pp.params.resize(count);
   pp.products.clear();
@@ -387,7 +387,7 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     PipeClass &c = kv.second;
     c.key = kv.first;
     int str = 0;
-    // chunks of up to eight tiles of one member; cost = tasks x (a task's rows,
+    // chunks of one member's tasks; cost = tasks x (a task's rows,
     // the member's mean over its row blocks, times its lags, plus its
     // epilogue); costliest first
     struct Chunk {
@@ -395,10 +395,15 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
       long long a, b, cost;
     };
     std::vector<Chunk> ch;
+    // chunks of up to eight tiles, and small enough for about four chunks
+    // an SM (a batch of a few large members is cut finer)
+    long long class_tasks = 0;
+    for (int k : c.members) class_tasks += pp.params[k].n_tasks;
+    const long long fine = std::max(1LL, class_tasks / (4LL * (sms > 0 ? sms : 1)));
     for (int k : c.members) {
       const RecParams &p = pp.params[k];
       const long long w = (long long)((p.n_inner + p.n_rb - 1) / p.n_rb) * p.G + 48;
-      const long long step = 8 * p.tasks_per_tile;
+      const long long step = std::min(8 * p.tasks_per_tile, fine);
       for (long long a = 0; a < p.n_tasks; a += step) {
         const long long b = std::min(p.n_tasks, a + step);
         ch.push_back({k, a, b, (b - a) * w});

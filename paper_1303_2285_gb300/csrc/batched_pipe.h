@@ -43,11 +43,12 @@ struct PipePlan {
 // rule, 8-byte aligned A and R).
 bool pipe_members_ok(const cov_desc *descs, int count);
 
-// Plans every member (plan_recurrence, no tuning cache), groups the members
-// and lays out, from workspace offset `off`, the tables and each member's
-// partial-sum arrays; pp.total = the end of the layout.
+// Plans every member (plan_recurrence, no tuning cache), groups the members,
+// cuts the product tasks into chunks for `sms` SMs and lays out, from
+// workspace offset `off`, the tables and each member's partial-sum arrays;
+// pp.total = the end of the layout.
 void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, int mean,
-                     size_t off);
+                     size_t off, int sms);
 
 // Copies the tables into the workspace, the member plans with their
 // addresses in this workspace (stream-ordered; the plan must stay alive until
