@@ -387,16 +387,15 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     PipeClass &c = kv.second;
     c.key = kv.first;
     int str = 0;
-    // chunks of one member's tasks; cost = tasks x (a task's rows,
-    // the member's mean over its row blocks, times its lags, plus its
-    // epilogue); costliest first
+    // chunks of one member's tasks: up to eight tiles, and small enough for
+    // about four chunks an SM (a batch of a few large members is cut
+    // finer); cost = tasks x (a task's rows, the member's mean over its row
+    // blocks, times its lags, plus its epilogue); costliest first
     struct Chunk {
       int k;
       long long a, b, cost;
     };
     std::vector<Chunk> ch;
-    // chunks of up to eight tiles, and small enough for about four chunks
-    // an SM (a batch of a few large members is cut finer)
     long long class_tasks = 0;
     for (int k : c.members) class_tasks += pp.params[k].n_tasks;
     const long long fine = std::max(1LL, class_tasks / (4LL * (sms > 0 ? sms : 1)));
