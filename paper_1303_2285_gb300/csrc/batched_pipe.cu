@@ -120,6 +120,12 @@ __global__ void __launch_bounds__(256) k_pipe_fringe(const RecParams *__restrict
 }
 
 // ---- 3. reductions, seed, walk and write ----------------------------------------
+// Pairs (combination D, column offset j) that own outputs: j < Q - dc.
+__host__ __device__ inline long long walk_pairs(int P, int Q) {
+  long long n = 0;
+  for (int dc = 0; dc < Q; ++dc) n += (long long)(dc == 0 ? P : 2 * P - 1) * (Q - dc);
+  return n;
+}
 // Thread task: CV[D][j] of combination D for every column offset j (the
 // inner-row box sums: core partials plus the fringe-column sums in the box;
 // suffix and prefix running sums where a box holds Q - 1 fringe columns,
@@ -316,13 +322,23 @@ __global__ void __launch_bounds__(256) k_pipe_walk(const RecParams *__restrict__
   if (t >= total) return;
   const int j = find_member(first, n, t);
   const RecParams &p = mp[members[j]];
-  const long long u = t - first[j];  // (combination fastest, column offset, chunk)
-  const int D = (int)(u % p.n_uc);
-  const long long r = u / p.n_uc;
-  const int jj = (int)(r % p.Q), c = (int)(r / p.Q);
-  int dr, dc;
-  combo_of(p.P, D, dr, dc);
-  if (jj >= p.Q - dc) return;
+  // the member's segments: chunk c, then by column lag dc, column offset
+  // j < Q - dc, and the lag's combinations fastest (only the pairs (D, j)
+  // that own outputs)
+  const long long u = t - first[j];
+  const long long per_chunk = walk_pairs(p.P, p.Q);
+  const int c = (int)(u / per_chunk);
+  long long r = u - c * per_chunk;
+  int dc = 0;
+  for (;; ++dc) {
+    const long long nd = (long long)(dc == 0 ? p.P : 2 * p.P - 1) * (p.Q - dc);
+    if (r < nd) break;
+    r -= nd;
+  }
+  const int ncomb = dc == 0 ? p.P : 2 * p.P - 1;
+  const int jj = (int)(r / ncomb), k = (int)(r % ncomb);
+  const int D = first_combo(p.P, dc) + k;
+  const int dr = dc == 0 ? k : k - (p.P - 1);
   const int adr = dr < 0 ? -dr : dr;
   const int I = p.P - adr, i0 = dr < 0 ? -dr : 0;
   const int is = i0 + c * p.L;
@@ -444,7 +460,7 @@ void pipe_plan_build(PipePlan &pp, const cov_desc *descs, int count, int elem, i
     for (int k : c.members) {
       const RecParams &p = pp.params[k];
       const long long nt = c.key == 0 ? (long long)p.n_uc * (1 + p.NFR)
-                                      : (long long)p.n_uc * p.Q * ((p.P + p.L - 1) / p.L);
+                                      : walk_pairs(p.P, p.Q) * ((p.P + p.L - 1) / p.L);
       c.first.push_back(c.first.back() + nt);
     }
     c.total = c.first.back();
