@@ -743,35 +743,43 @@ def bench_batched(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
 
 def bench_apertures(cov, torch, np, wl, mk_events, stream, fp32_peak, hbm) -> dict:
     """Every 25 x 25 aperture at stride 10 of a 1015 x 1015 image (100 x 100
-    apertures), 10 x 10 window, read in place by one graph-captured launch."""
+    apertures), 10 x 10 window, read in place: the strip launch
+    (cov_estimate_apertures, graph-captured) and, beside it, the batched
+    plan over the same apertures."""
     H = W = 1015
     img = torch.from_numpy(wl.complex_normal((H, W), 77, "c64")).cuda()
+    s = torch.cuda.Stream()
+
+    def time_graph(fn, n=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            fn()
+        torch.cuda.synchronize()
+        ev = mk_events(2 * n)
+        for k in range(n):
+            ev[2 * k].record(stream)
+            g.replay()
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        return sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n)) / n
+
     plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
     ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
     plan.upload(ws)
     tuning = plan.autotune(ws, reps=2)  # untimed
-    s = torch.cuda.Stream()
-    for _ in range(3):
-        plan.run(ws, stream=s)
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=s):
-        plan.run(ws, stream=s)
-    torch.cuda.synchronize()
-    n = 10
-    ev = mk_events(2 * n)
-    for k in range(n):
-        ev[2 * k].record(stream)
-        g.replay()
-        ev[2 * k + 1].record(stream)
-    torch.cuda.synchronize()
+    ms_batched = time_graph(lambda: plan.run(ws, stream=s))
     cov.check_device_status(ws)
-    ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n)) / n
+    ms = time_graph(lambda: cov.apertures(img, (25, 25), (10, 10), 10, 10, out=R, stream=s))
     um = R.shape[0] * cov.plan_info(25, 25, 10, 10)["distinct_products"]
-    return {"apertures": R.shape[0], "ms_per_launch": ms, "apertures_per_s": R.shape[0] / (ms * 1e-3),
+    return {"apertures": R.shape[0], "kernel": "k_apertures (strip launch)", "ms_per_launch": ms,
+            "apertures_per_s": R.shape[0] / (ms * 1e-3),
             "distinct_products_per_s": um / (ms * 1e-3), "fp32_fma_frac": 8.0 * um / (ms * 1e-3) / fp32_peak,
             "r_bytes": R.numel() * 8, "r_write_hbm_frac": R.numel() * 8 / (ms * 1e-3) / hbm,
-            "graph_captured": True, "tuning": tuning}
+            "graph_captured": True, "batched_plan_ms_per_launch": ms_batched,
+            "batched_plan_tuning": tuning}
 
 
 def bench_capon(cov, torch, np, wl, mk_events, stream, fp32_peak) -> dict:
@@ -1003,7 +1011,8 @@ def profile_case(case: str, knobs=None) -> int:  # noqa: C901 - one branch per c
     1024 x 1024 workload, the stencil adjoint of a batch of eight (or, with
     the knob, that many) 256 x 256 inputs with a 12 x 12 window, the 30 x 30 apertures of 25 x 25 (stride
     10, 10 x 10 window) of a 315 x 315 image through the batched launch's
-    default form, and the Capon spectra of those 900 estimates."""
+    default form (knob "strip": the strip launch), and the Capon spectra of
+    those 900 estimates."""
     import numpy as np
     import torch
 
@@ -1037,13 +1046,17 @@ def profile_case(case: str, knobs=None) -> int:  # noqa: C901 - one branch per c
             plan.run(ws)
     elif case == "apertures":
         img = torch.from_numpy(wl.complex_normal((315, 315), 77, "c64")).cuda()
-        plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
-        if knobs:  # the batched plan's form (0, 1 or 2); default: the plan's own
-            plan.set_tuning(int(knobs), 0, 4)
-        ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
-        plan.upload(ws)
-        for _ in range(3):
-            plan.run(ws)
+        if knobs == "strip":  # the strip launch
+            for _ in range(3):
+                cov.apertures(img, (25, 25), (10, 10), 10, 10)
+        else:
+            plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)
+            if knobs:  # the batched plan's form (0, 1 or 2); default: the plan's own
+                plan.set_tuning(int(knobs), 0, 4)
+            ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device="cuda")
+            plan.upload(ws)
+            for _ in range(3):
+                plan.run(ws)
     elif case == "capon":
         img = torch.from_numpy(wl.complex_normal((315, 315), 77, "c64")).cuda()
         plan, R = cov.aperture_batch(img, (25, 25), (10, 10), 10, 10)

@@ -338,6 +338,22 @@ cov_status cov_aperture_descs(const void *image, cov_dtype dtype, int64_t H, int
                               int ap_n, int ap_m, int step_r, int step_c, int P, int Q, void *R,
                               cov_desc *descs, int max_count, int *count);
 
+/* The same apertures computed in one launch, strip by strip (Section 2.3;
+ * Eq. 2.1-2.2 per aperture, through the combinations of Eq. 3.3 and the
+ * diagonal walk of Eq. 3.7-3.8): a CTA takes one row of apertures and the
+ * neighbours in it whose columns fit a 64-column strip of the image, so that
+ * a product under several of them is formed once. image: device, H x W,
+ * leading dimension ld, COV_C64, 8-byte aligned, read only. R: device,
+ * caller-owned, 8-byte aligned, count * (PQ)^2 complex elements with count
+ * and the order of cov_aperture_descs (aperture (a, b) at a * nc + b);
+ * overwritten. Needs no workspace and never allocates. COV_EINVAL on the
+ * argument errors of cov_aperture_descs, a null R or a misaligned pointer;
+ * COV_EUNSUPPORTED for COV_C128, P or Q above 16, ap_n or ap_m above 64.
+ * Stream-ordered; FP32 products and sums, 1/K as the FP32 reciprocal. */
+cov_status cov_estimate_apertures(const void *image, cov_dtype dtype, int64_t H, int64_t W,
+                                  int64_t ld, int ap_n, int ap_m, int step_r, int step_c, int P,
+                                  int Q, void *R, cov_norm norm, cov_stream_t stream);
+
 /* Validates `count` descriptors (HOST array, copied) and builds the task
  * schedule. COV_RECURRENCE (or COV_AUTO) only; every member must satisfy the
  * COV_RECURRENCE shape rule (P, Q <= 32), A and R 8-byte aligned. COV_C64

@@ -23,7 +23,7 @@ __all__ = ["load", "estimate", "estimate_into", "workspace_size", "plan_info",
            "check_device_status", "CovError", "ALGOS", "NORMS", "DTYPES", "STATUS", "autotune",
            "tuning_get", "tuning_set", "tuning_clear", "tuning_save", "tuning_load",
            "covariance", "estimate_backward", "estimate_backward_batch",
-           "backward_workspace_size", "BatchedPlan", "aperture_descs", "aperture_batch",
+           "backward_workspace_size", "BatchedPlan", "aperture_descs", "aperture_batch", "apertures",
            "selftest_timeout", "set_stage_events", "capon_spectrum", "SIGNATURES"]
 
 ALGOS = {"auto": 0, "recurrence": 1, "gemm_tf32x3": 2, "gemm_bf16x3": 3, "direct": 4}
@@ -99,6 +99,8 @@ SIGNATURES = [
     ("cov_batched_workspace_size", _I, [_VP, ctypes.POINTER(_SZ)]),
     ("cov_aperture_descs", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _I, _I, _I, _I, _VP,
                                 ctypes.POINTER(CovDesc), _I, ctypes.POINTER(ctypes.c_int)]),
+    ("cov_estimate_apertures", _I, [_VP, _I, _I64, _I64, _I64, _I, _I, _I, _I, _I, _I, _VP, _I,
+                                    _VP]),
     ("cov_batched_upload", _I, [_VP, _VP, _SZ, _VP]),
     ("cov_estimate_batched", _I, [_VP, _VP, _SZ, _VP]),
     ("cov_batched_plan_destroy", None, [_VP]),
@@ -449,6 +451,32 @@ def aperture_batch(image, ap: tuple, step: tuple, P: int, Q: int, norm: str = "m
     plan = BatchedPlan(None, norm=norm, descs=arr)
     plan._keep = (image, R)
     return plan, R
+
+
+def apertures(image, ap: tuple, step: tuple, P: int, Q: int, norm: str = "mean", out=None,
+              stream=None):
+    """Estimates of every ap[0] x ap[1] aperture at stride step of a complex64
+    CUDA image in one launch (cov_estimate_apertures); returns R of shape
+    (count, PQ, PQ), apertures in row-major order (out: a tensor of that
+    shape to overwrite)."""
+    torch = _torch()
+    if not image.is_cuda or image.dtype != torch.complex64 or image.stride(1) != 1:
+        raise ValueError("image must be a complex64 CUDA tensor with unit column stride")
+    H, W = image.shape
+    n = ctypes.c_int(0)
+    _check(load().cov_aperture_descs(None, DTYPES["c64"], H, W, image.stride(0), ap[0], ap[1],
+                                     step[0], step[1], P, Q, None, None, 0, ctypes.byref(n)),
+           "cov_aperture_descs")
+    shape = (n.value, P * Q, P * Q)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.complex64, device=image.device)
+    elif tuple(out.shape) != shape or out.dtype != torch.complex64 or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous complex64 tensor of shape {shape}")
+    _check(load().cov_estimate_apertures(image.data_ptr(), DTYPES["c64"], H, W, image.stride(0),
+                                         ap[0], ap[1], step[0], step[1], P, Q, out.data_ptr(),
+                                         NORMS[norm], _stream_ptr(stream)),
+           "cov_estimate_apertures")
+    return out
 
 
 def set_stage_events(events) -> None:

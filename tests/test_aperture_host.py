@@ -63,3 +63,20 @@ def test_quarter_million_apertures_plan():
     plan = cov.BatchedPlan(None, descs=arr)
     assert plan.tuning["form"] == 2  # the box form: 25 x 25 apertures, 10 x 10 windows
     assert plan.workspace_bytes >= n * ctypes.sizeof(cov.CovDesc)
+
+
+@pytest.mark.parametrize("args,status", [
+    # (image, dtype, H, W, ld, an, am, sr, sc, P, Q, R, norm): checks made before any CUDA call
+    ((None, 0, 64, 64, 64, 25, 25, 10, 10, 10, 10, 0x2000, 0), 1),     # null image
+    ((0x1000, 0, 64, 64, 64, 25, 25, 10, 10, 10, 10, None, 0), 1),     # null R
+    ((0x1004, 0, 64, 64, 64, 25, 25, 10, 10, 10, 10, 0x2000, 0), 1),   # misaligned image
+    ((0x1000, 0, 64, 64, 64, 25, 25, 10, 10, 10, 10, 0x2000, 2), 1),   # bad norm
+    ((0x1000, 0, 64, 64, 63, 25, 25, 10, 10, 10, 10, 0x2000, 0), 1),   # ld < W
+    ((0x1000, 0, 64, 64, 64, 25, 25, 10, 10, 26, 10, 0x2000, 0), 1),   # P > aperture rows
+    ((0x1000, 1, 64, 64, 64, 25, 25, 10, 10, 10, 10, 0x2000, 0), 5),   # complex128
+    ((0x1000, 0, 64, 64, 64, 25, 25, 10, 10, 17, 10, 0x2000, 0), 5),   # P above 16
+    ((0x1000, 0, 99, 99, 99, 65, 25, 10, 10, 10, 10, 0x2000, 0), 5),   # 65 aperture rows
+    ((0x1000, 0, 99, 99, 99, 25, 65, 10, 10, 10, 10, 0x2000, 0), 5),   # 65 aperture columns
+])
+def test_strip_argument_checks(args, status):
+    assert cov.load().cov_estimate_apertures(*args, None) == status
