@@ -47,75 +47,55 @@ struct ApParams {
   int groups;          // CTAs per row of apertures
   int an, am, sr, sc;  // aperture rows, columns; steps
   int P, Q, G;         // window; apertures a CTA takes
-  int TS;              // table entries per aperture (the largest lag's outputs)
+  int TS;              // table entries per aperture (Q P^2)
   float rK;            // 1/K (COV_MEAN, the FP32 reciprocal) or 1 (COV_SUM)
 };
 
-// Outputs of one column lag for one aperture: dc = 0 has the row lags
-// 0 .. P-1 with P - dr output rows each, Q output columns; dc > 0 the row lags
-// -(P-1) .. P-1 (P^2 output rows), Q - dc output columns.
-inline int ap_table_entries(int P, int Q) {
-  const int z = P * (P + 1) / 2 * Q, o = Q > 1 ? P * P * (Q - 1) : 0;
-  return z > o ? z : o;
-}
-// Strip, the warps' column sums, the lag's output table, two offset tables.
+// The lag's output table of one aperture holds its R blocks (j, j + dc),
+// j < Q - dc, entry (i, i') at j P^2 + i P + i' (dc = 0: the entries i <= i').
+inline int ap_table_entries(int P, int Q) { return Q * P * P; }
+// Strip, the warps' column sums and the lag's output table.
 inline size_t ap_smem_bytes(int an, int P, int Q, int G) {
   return ((size_t)an * kApStrip + (size_t)kApWarps * P * kApVPitch +
-          (size_t)G * ap_table_entries(P, Q)) * sizeof(float2) +
-         3 * kApMaxPQ * sizeof(int);
+          (size_t)G * ap_table_entries(P, Q)) * sizeof(float2);
 }
-
-// n / d for 0 <= n < 2^20 and 1 <= d <= 64 by a multiply-high with
-// m = ceil(2^32 / d): n m / 2^32 = n / d + n (m d - 2^32) / (d 2^32), and the
-// second term stays below 1 / d while n (m d - 2^32) < 2^32, i.e. n < 2^26.
-struct DivSmall {
-  unsigned m;
-  int d;
-  __device__ __forceinline__ void init(int dd) {
-    d = dd;
-    m = dd == 1 ? 0u : 0xffffffffu / (unsigned)dd + 1u;
-  }
-  __device__ __forceinline__ int q(int n) const {
-    return d == 1 ? n : (int)__umulhi((unsigned)n, m);
-  }
-};
 
 __device__ __forceinline__ float2 ap_prod(float2 a, float2 b) {
   float2 v = make_float2(0.f, 0.f);
   cmac_conj(v, a, b);
   return v;
 }
+// Packed FP32x2 add and subtract (each half rounded as add.rn.f32 / sub.rn.f32).
+__device__ __forceinline__ unsigned long long ap_add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long ap_sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 
 __global__ void __launch_bounds__(kApWarps * 32, 2) k_apertures(ApParams p) {
   extern __shared__ __align__(16) unsigned char smem_ap[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int P = p.P, Q = p.Q, DD = P * Q;
+  const int P = p.P, Q = p.Q, DD = P * Q, PP = P * P;
   const int Hb = p.an - P + 1, Wd = p.am - Q + 1;  // box rows, box columns
   const int ay = blockIdx.x / p.groups, g = blockIdx.x - ay * p.groups;
   const int ax0 = g * p.G, Gc = min(p.G, p.nc - ax0);
   const int Sw = (Gc - 1) * p.sc + p.am;  // strip columns under the CTA's apertures
-  float2 *As = (float2 *)smem_ap;                                    // [an][64]
-  float2 *Vw = As + p.an * kApStrip + warp * P * kApVPitch;          // this warp's [P][65]
-  float2 *T = As + p.an * kApStrip + kApWarps * P * kApVPitch;       // [G][TS]
-  int *cumN = (int *)(T + p.G * p.TS);  // dc > 0: output rows of the row lags before dr (+ P - 1)
-  int *cum0 = cumN + 2 * kApMaxPQ;      // dc = 0: the same for dr >= 0
+  float2 *As = (float2 *)smem_ap;                                 // [an][64]
+  float2 *Vw = As + p.an * kApStrip + warp * P * kApVPitch;       // this warp's [P][65]
+  float2 *T = As + p.an * kApStrip + kApWarps * P * kApVPitch;    // [G][TS]
   const float2 *src = p.img + (long long)ay * p.sr * p.ld + (long long)ax0 * p.sc;
   for (int e = tid; e < p.an * kApStrip; e += kApWarps * 32) {
     const int r = e >> 6, c = e & (kApStrip - 1);
     As[e] = c < Sw ? __ldg(src + (long long)r * p.ld + c) : make_float2(0.f, 0.f);
   }
-  if (tid < 2 * P - 1) {
-    int s = 0;
-    for (int k = 0; k < tid; ++k) s += P - abs(k - (P - 1));
-    cumN[tid] = s;
-  }
-  if (tid < P) cum0[tid] = tid * P - tid * (tid - 1) / 2;
   __syncthreads();
 
   float2 *Rg = p.R + ((long long)ay * p.nc + ax0) * DD * DD;
-  DivSmall divP, divG;
-  divP.init(P);
-  divG.init(Gc);
   for (int dc = 0; dc < Q; ++dc) {
     const int J = Q - dc, ncol = Sw - dc;  // output columns; strip columns with a partner
     const int nd = dc ? 2 * P - 1 : P;
@@ -124,11 +104,26 @@ __global__ void __launch_bounds__(kApWarps * 32, 2) k_apertures(ApParams p) {
       const int d = dc ? ((k & 1) ? (k + 1) >> 1 : -(k >> 1)) : k;
       const int I = P - (d < 0 ? -d : d), i0 = d < 0 ? -d : 0;
       // ---- column sums of the products, walked down the diagonal --------
+      // The products of rows r < I - 1 leave the box at output row r + 1:
+      // they are kept in row r + 1 of the warp's column-sum buffer, which
+      // that output row overwrites after reading them.
       const int o1 = lane + 32 < ncol ? 32 : 0;  // the lane's second column (or its first again)
       const float2 *pa = As + i0 * kApStrip + lane;
       const float2 *pb = As + (i0 + d) * kApStrip + lane + dc;
+      float2 *vw = Vw + lane;
       float2 V0 = make_float2(0.f, 0.f), V1 = V0, U0 = V0, U1 = V0;
+      const int nk = min(I - 1, Hb);  // kept rows among the seed's
       int r = 0;
+      for (; r < nk; ++r) {
+        const int o = r * kApStrip;
+        const float2 x0 = ap_prod(pa[o], pb[o]), x1 = ap_prod(pa[o + o1], pb[o + o1]);
+        vw[(r + 1) * kApVPitch] = x0;
+        vw[(r + 1) * kApVPitch + 32] = x1;
+        V0.x += x0.x;
+        V0.y += x0.y;
+        V1.x += x1.x;
+        V1.y += x1.y;
+      }
       for (; r + 1 < Hb; r += 2) {
         const int o = r * kApStrip;
         cmac_conj(V0, pa[o], pb[o]);
@@ -145,76 +140,80 @@ __global__ void __launch_bounds__(kApWarps * 32, 2) k_apertures(ApParams p) {
       V0.y += U0.y;
       V1.x += U1.x;
       V1.y += U1.y;
-      Vw[lane] = V0;
-      Vw[lane + 32] = V1;
+      vw[0] = V0;
+      vw[32] = V1;
       for (int s = 1; s < I; ++s) {  // row s - 1 leaves the box, row s - 1 + Hb enters
-        const int oi = (s - 1 + Hb) * kApStrip, oo = (s - 1) * kApStrip;
-        const float2 x0 = ap_prod(pa[oi], pb[oi]), y0 = ap_prod(pa[oo], pb[oo]);
-        const float2 x1 = ap_prod(pa[oi + o1], pb[oi + o1]), y1 = ap_prod(pa[oo + o1], pb[oo + o1]);
+        const int rin = s - 1 + Hb, oi = rin * kApStrip;
+        const float2 x0 = ap_prod(pa[oi], pb[oi]), x1 = ap_prod(pa[oi + o1], pb[oi + o1]);
+        if (rin < I - 1) {  // a box shorter than the walk: the entering row leaves later
+          vw[(rin + 1) * kApVPitch] = x0;
+          vw[(rin + 1) * kApVPitch + 32] = x1;
+        }
+        const float2 y0 = vw[s * kApVPitch], y1 = vw[s * kApVPitch + 32];
         V0.x += x0.x - y0.x;
         V0.y += x0.y - y0.y;
         V1.x += x1.x - y1.x;
         V1.y += x1.y - y1.y;
-        Vw[s * kApVPitch + lane] = V0;
-        Vw[s * kApVPitch + lane + 32] = V1;
+        vw[s * kApVPitch] = V0;
+        vw[s * kApVPitch + 32] = V1;
       }
       __syncwarp();
-      // ---- window sums along the columns, one (aperture, output row) a lane
-      const int cum = dc ? cumN[d + P - 1] : cum0[d];
+      // ---- window sums along the columns, one (aperture, output row) a
+      // lane; output (s, j) is entry (i0 + s, i0 + s + d) of block j
       for (int q = lane; q < Gc * I; q += 32) {
         const int ap = q / I, s = q - ap * I;
-        const float2 *v = Vw + s * kApVPitch + ap * p.sc;
-        float2 W = v[0], W2 = make_float2(0.f, 0.f);
+        const unsigned long long *v =
+            (const unsigned long long *)(Vw + s * kApVPitch + ap * p.sc);
+        unsigned long long W = v[0], W2 = 0ull;
         int m = 1;
         for (; m + 1 < Wd; m += 2) {
-          W.x += v[m].x;
-          W.y += v[m].y;
-          W2.x += v[m + 1].x;
-          W2.y += v[m + 1].y;
+          W = ap_add2(W, v[m]);
+          W2 = ap_add2(W2, v[m + 1]);
         }
-        if (m < Wd) {
-          W.x += v[m].x;
-          W.y += v[m].y;
-        }
-        W.x += W2.x;
-        W.y += W2.y;
-        float2 *t = T + ap * p.TS + J * (cum + s);
+        if (m < Wd) W = ap_add2(W, v[m]);
+        W = ap_add2(W, W2);
+        unsigned long long *t =
+            (unsigned long long *)(T + ap * p.TS + (i0 + s) * P + i0 + s + d);
         t[0] = W;
         for (int j = 1; j < J; ++j) {  // column j - 1 leaves the window, j - 1 + Wd enters
-          W.x += v[j - 1 + Wd].x - v[j - 1].x;
-          W.y += v[j - 1 + Wd].y - v[j - 1].y;
-          t[j] = W;
+          W = ap_add2(W, ap_sub2(v[j - 1 + Wd], v[j - 1]));
+          t[j * PP] = W;
         }
       }
       __syncwarp();  // the column sums are read before the next row lag overwrites them
     }
     __syncthreads();
-    // ---- R blocks of this lag: (j, j + dc), and for dc > 0 the mirrors ----
-    DivSmall divJ;
-    divJ.init(J);
-    const int total = Gc * J * P * P * (dc ? 2 : 1);
-    for (int e = tid; e < total; e += kApWarps * 32) {
-      const int t1 = divP.q(e), col = e - t1 * P;
-      const int t2 = divP.q(t1), row = t1 - t2 * P;
-      const int t3 = divJ.q(t2), j = t2 - t3 * J;
-      const int pass = divG.q(t3), ap = t3 - pass * Gc;
-      // entry (i, i') of block (j, j + dc): row lag i' - i, output row min(i, i')
-      const int i = pass ? col : row, ip = pass ? row : col;
-      const int dd = ip - i, s = i < ip ? i : ip;
-      float2 v;
-      bool cj = pass != 0;
-      if (dc) {
-        v = T[ap * p.TS + J * (cumN[dd + P - 1] + s) + j];
-      } else {  // the block on the diagonal: entries below it mirror those above
-        v = T[ap * p.TS + J * (cum0[dd < 0 ? -dd : dd] + s) + j];
-        cj = dd < 0;
+    // ---- R blocks of this lag: (j, j + dc), and for dc > 0 the mirrors
+    // (j + dc, j). The two thread halves take alternate j, a thread the
+    // entries w, w + 128, ... of each block.
+    const int half = tid >> 7;
+    for (int w = tid & 127; w < PP; w += 128) {
+      const int row = w / P, col = w - row * P;
+      const int up = row * P + col, lo = col * P + row;  // entry (row, col) and its transpose
+      const bool below = row > col;
+      const float rK = p.rK;
+      for (int ap = 0; ap < Gc; ++ap) {
+        const float2 *Ta = T + ap * p.TS;
+        float2 *Ra = Rg + (long long)ap * DD * DD + (long long)row * DD + col;
+        for (int j = half; j < J; j += 2) {
+          const float2 *Tj = Ta + j * PP;
+          if (dc == 0) {  // a diagonal block: entries below the diagonal mirror those above
+            float2 v = Tj[below ? lo : up];
+            v.x *= rK;
+            v.y = row == col ? 0.f : (below ? -v.y : v.y) * rK;
+            Ra[(long long)P * j * DD + P * j] = v;
+          } else {
+            float2 v = Tj[up];
+            v.x *= rK;
+            v.y *= rK;
+            Ra[(long long)P * j * DD + P * (j + dc)] = v;
+            v = Tj[lo];  // block (j + dc, j): entry (row, col) is the conjugate of (col, row)
+            v.x *= rK;
+            v.y = -v.y * rK;
+            Ra[(long long)P * (j + dc) * DD + P * j] = v;
+          }
+        }
       }
-      v.x *= p.rK;
-      v.y *= p.rK;
-      if (cj) v.y = -v.y;
-      if (dc == 0 && dd == 0) v.y = 0.f;
-      const int rb = pass ? j + dc : j, cb = pass ? j : j + dc;
-      Rg[(long long)ap * DD * DD + (long long)(row + P * rb) * DD + col + P * cb] = v;
     }
     __syncthreads();  // the table is read before the next lag overwrites it
   }

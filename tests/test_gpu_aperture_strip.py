@@ -29,6 +29,7 @@ SHAPES = [  # H, W, aperture, step, P, Q
     (64, 64, (64, 64), (1, 1), 16, 16),      # the largest aperture
     (90, 300, (16, 16), (16, 16), 8, 8),     # apertures side by side, no overlap
     (70, 200, (25, 25), (3, 2), 7, 10),      # many apertures a strip (step 2)
+    (20, 40, (20, 20), (2, 2), 16, 4),       # fewer box rows than output rows (kept products from the walk)
 ]
 
 
