@@ -5,16 +5,20 @@
 //
 // A CTA takes one row of apertures and G neighbours in it: the strip of the
 // image under them (ap_n rows, (G-1) step_c + ap_m <= 64 columns) is staged
-// in shared memory once. Column lag by column lag dc, the warps take the row
-// lags dr of the combinations (dr, dc) of Eq. 3.3; for one combination a warp
+// in shared memory once. Column lag by column lag dc, the warps take groups
+// of four row lags of one sign (dr = d0 .. d0+3, or -d0 .. -(d0+3)) of the
+// combinations (dr, dc) of Eq. 3.3. For one group a warp
 //  - forms the products of Eq. 3.5 over the whole strip, two columns a lane,
 //    and walks their column sums down the diagonal: the sum over the box rows
 //    of the first output row, then per output row one product row in and one
-//    out (Eq. 3.7-3.8);
-//  - builds each aperture's outputs as sums of Wd consecutive column sums,
-//    slid along the output columns (one column sum in, one out), into a
-//    shared-memory table of the lag's outputs.
-// The CTA then writes the R blocks of that lag, (j, j + dc) and their
+//    out (Eq. 3.7-3.8). The four lags share one operand row and slide along
+//    the other, so that in the seed one row of the first operand and seven
+//    rows of the second serve four rows of products for all four lags;
+//  - after each output row, builds each aperture's outputs of that row as
+//    sums of Wd consecutive column sums, slid along the output columns (one
+//    column sum in, one out), one (aperture, lag) a lane, into a shared-
+//    memory table of the lag's R blocks.
+// The CTA then writes the R blocks of that column lag, (j, j + dc) and their
 // conjugate mirrors (j + dc, j), in runs of P contiguous elements.
 //
 // Against one CTA per aperture (the batched box form), a product under k
@@ -33,9 +37,12 @@
 namespace cov {
 namespace {
 
-constexpr int kApWarps = 8;
+constexpr int kApWarps = 4;
+constexpr int kApThreads = kApWarps * 32;
+constexpr int kApLag = 4;      // row lags a warp takes together
+constexpr int kApBlk = 4;      // seed rows a step (register block)
 constexpr int kApStrip = 64;   // strip columns staged by a CTA (two a lane)
-constexpr int kApVPitch = 65;  // row pitch of a warp's column sums, in float2 (spreads the banks)
+constexpr int kApVPitch = 65;  // row pitch of a warp's column sums, in float2
 constexpr int kApMaxPQ = 16;   // P, Q limit
 constexpr int kApMaxRows = 64; // ap_n limit
 
@@ -54,15 +61,43 @@ struct ApParams {
 // The lag's output table of one aperture holds its R blocks (j, j + dc),
 // j < Q - dc, entry (i, i') at j P^2 + i P + i' (dc = 0: the entries i <= i').
 inline int ap_table_entries(int P, int Q) { return Q * P * P; }
-// Strip, the warps' column sums and the lag's output table.
+// The strip with kApLag zero rows below it (read by the lags past the last
+// one of a group), the warps' column sums, the lag's output table.
 inline size_t ap_smem_bytes(int an, int P, int Q, int G) {
-  return ((size_t)an * kApStrip + (size_t)kApWarps * P * kApVPitch +
+  return ((size_t)(an + kApLag) * kApStrip + (size_t)kApWarps * kApLag * kApVPitch +
           (size_t)G * ap_table_entries(P, Q)) * sizeof(float2);
 }
 
-__device__ __forceinline__ float2 ap_prod(float2 a, float2 b) {
+// n / d for 0 <= n < 2^16 and 1 <= d <= 256 by a multiply-high with
+// m = ceil(2^32 / d): n m / 2^32 = n / d + n (m d - 2^32) / (d 2^32), and the
+// second term stays below 1 / d while n (m d - 2^32) < 2^32, i.e. n < 2^24.
+struct DivSmall {
+  unsigned m;
+  int d;
+  __device__ __forceinline__ void init(int dd) {
+    d = dd;
+    m = dd == 1 ? 0u : 0xffffffffu / (unsigned)dd + 1u;
+  }
+  __device__ __forceinline__ int q(int n) const {
+    return d == 1 ? n : (int)__umulhi((unsigned)n, m);
+  }
+};
+
+// acc += a conj(b) with a, b the two operands in their roles: for dr >= 0 the
+// shared operand is a (row r, column x) and the sliding one b (row r + dr,
+// column x + dc); for dr < 0 the shared one is b (row r) and the sliding one
+// a (row r + |dr|).
+template <bool NEG>
+__device__ __forceinline__ void ap_mac(float2 &acc, float2 shared_op, float2 sliding_op) {
+  if (NEG)
+    cmac_conj(acc, sliding_op, shared_op);
+  else
+    cmac_conj(acc, shared_op, sliding_op);
+}
+template <bool NEG>
+__device__ __forceinline__ float2 ap_prod(float2 shared_op, float2 sliding_op) {
   float2 v = make_float2(0.f, 0.f);
-  cmac_conj(v, a, b);
+  ap_mac<NEG>(v, shared_op, sliding_op);
   return v;
 }
 // Packed FP32x2 add and subtract (each half rounded as add.rn.f32 / sub.rn.f32).
@@ -77,141 +112,169 @@ __device__ __forceinline__ unsigned long long ap_sub2(unsigned long long a, unsi
   return d;
 }
 
-__global__ void __launch_bounds__(kApWarps * 32, 2) k_apertures(ApParams p) {
+// Outputs of output row s for the warp's lags: lane (aperture ap, lag k)
+// sums its aperture's Wd column sums and slides along the J output columns.
+template <bool NEG>
+__device__ __forceinline__ void ap_row_pass(const ApParams &p, const float2 *Vw, float2 *T,
+                                            int lane, int s, int d0, int Gc, int Wd, int J) {
+  const int P = p.P, PP = P * P;
+  for (int q = lane; q < Gc * kApLag; q += 32) {
+    const int ap = q / kApLag, k = q - ap * kApLag, dd = d0 + k;  // |dr|
+    if (dd >= P || s >= P - dd) continue;  // a lag past P - 1, or no output row s
+    const unsigned long long *v = (const unsigned long long *)(Vw + k * kApVPitch + ap * p.sc);
+    unsigned long long W = v[0], W2 = 0ull;
+    int m = 1;
+    for (; m + 1 < Wd; m += 2) {
+      W = ap_add2(W, v[m]);
+      W2 = ap_add2(W2, v[m + 1]);
+    }
+    if (m < Wd) W = ap_add2(W, v[m]);
+    W = ap_add2(W, W2);
+    // output (s, j) of lag dr is entry (i0 + s, i0 + s + dr) of block j
+    const int i = NEG ? dd + s : s, ip = NEG ? s : s + dd;
+    unsigned long long *t = (unsigned long long *)(T + ap * p.TS + i * P + ip);
+    t[0] = W;
+    for (int j = 1; j < J; ++j) {  // column j - 1 leaves the window, j - 1 + Wd enters
+      W = ap_add2(W, ap_sub2(v[j - 1 + Wd], v[j - 1]));
+      t[j * PP] = W;
+    }
+  }
+}
+
+// One group of row lags (|dr| = d0 .. d0 + kApLag - 1, sign by NEG) of
+// column lag dc over the strip.
+template <bool NEG>
+__device__ __forceinline__ void ap_group(const ApParams &p, const float2 *As, float2 *Vw,
+                                         float2 *T, int lane, int dc, int d0, int Gc, int ncol) {
+  const int P = p.P, Hb = p.an - P + 1, Wd = p.am - p.Q + 1, J = p.Q - dc;
+  const int Imax = P - d0;  // output rows of the group's first lag
+  const int o1 = lane + 32 < ncol ? 32 : 0;  // the lane's second column (or its first again)
+  const float2 *S0 = As + lane + (NEG ? dc : 0), *S1 = S0 + o1;  // shared operand, row r
+  const float2 *L0 = As + d0 * kApStrip + lane + (NEG ? 0 : dc), *L1 = L0 + o1;  // row r + d0 (+ k)
+  float2 V0[kApLag], V1[kApLag];
+#pragma unroll
+  for (int k = 0; k < kApLag; ++k) V0[k] = V1[k] = make_float2(0.f, 0.f);
+  // seed: box rows 0 .. Hb-1 of output row 0, kApBlk rows a step
+  int r = 0;
+  for (; r + kApBlk <= Hb; r += kApBlk) {
+    float2 s0[kApBlk], s1[kApBlk], l0[kApBlk + kApLag - 1], l1[kApBlk + kApLag - 1];
+#pragma unroll
+    for (int t = 0; t < kApBlk; ++t) {
+      s0[t] = S0[(r + t) * kApStrip];
+      s1[t] = S1[(r + t) * kApStrip];
+    }
+#pragma unroll
+    for (int t = 0; t < kApBlk + kApLag - 1; ++t) {
+      l0[t] = L0[(r + t) * kApStrip];
+      l1[t] = L1[(r + t) * kApStrip];
+    }
+#pragma unroll
+    for (int t = 0; t < kApBlk; ++t)
+#pragma unroll
+      for (int k = 0; k < kApLag; ++k) {
+        ap_mac<NEG>(V0[k], s0[t], l0[t + k]);
+        ap_mac<NEG>(V1[k], s1[t], l1[t + k]);
+      }
+  }
+  for (; r < Hb; ++r) {
+    const float2 s0 = S0[r * kApStrip], s1 = S1[r * kApStrip];
+#pragma unroll
+    for (int k = 0; k < kApLag; ++k) {
+      ap_mac<NEG>(V0[k], s0, L0[(r + k) * kApStrip]);
+      ap_mac<NEG>(V1[k], s1, L1[(r + k) * kApStrip]);
+    }
+  }
+  for (int s = 0;; ++s) {
+#pragma unroll
+    for (int k = 0; k < kApLag; ++k) {
+      Vw[k * kApVPitch + lane] = V0[k];
+      Vw[k * kApVPitch + lane + 32] = V1[k];
+    }
+    __syncwarp();
+    ap_row_pass<NEG>(p, Vw, T, lane, s, d0, Gc, Wd, J);
+    __syncwarp();  // the column sums are read before the next row overwrites them
+    if (s + 1 >= Imax) break;
+    // walk: row s leaves the box, row s + Hb enters
+    const int ri = s + Hb, ro = s;
+    const float2 si0 = S0[ri * kApStrip], si1 = S1[ri * kApStrip];
+    const float2 so0 = S0[ro * kApStrip], so1 = S1[ro * kApStrip];
+#pragma unroll
+    for (int k = 0; k < kApLag; ++k) {
+      const float2 x0 = ap_prod<NEG>(si0, L0[(ri + k) * kApStrip]);
+      const float2 y0 = ap_prod<NEG>(so0, L0[(ro + k) * kApStrip]);
+      const float2 x1 = ap_prod<NEG>(si1, L1[(ri + k) * kApStrip]);
+      const float2 y1 = ap_prod<NEG>(so1, L1[(ro + k) * kApStrip]);
+      V0[k].x += x0.x - y0.x;
+      V0[k].y += x0.y - y0.y;
+      V1[k].x += x1.x - y1.x;
+      V1[k].y += x1.y - y1.y;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kApThreads, 4) k_apertures(ApParams p) {
   extern __shared__ __align__(16) unsigned char smem_ap[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int P = p.P, Q = p.Q, DD = P * Q, PP = P * P;
-  const int Hb = p.an - P + 1, Wd = p.am - Q + 1;  // box rows, box columns
   const int ay = blockIdx.x / p.groups, g = blockIdx.x - ay * p.groups;
   const int ax0 = g * p.G, Gc = min(p.G, p.nc - ax0);
   const int Sw = (Gc - 1) * p.sc + p.am;  // strip columns under the CTA's apertures
-  float2 *As = (float2 *)smem_ap;                                 // [an][64]
-  float2 *Vw = As + p.an * kApStrip + warp * P * kApVPitch;       // this warp's [P][65]
-  float2 *T = As + p.an * kApStrip + kApWarps * P * kApVPitch;    // [G][TS]
+  const int rows = p.an + kApLag;
+  float2 *As = (float2 *)smem_ap;                                // [an + kApLag][64]
+  float2 *Vw = As + rows * kApStrip + warp * kApLag * kApVPitch;  // this warp's [kApLag][65]
+  float2 *T = As + rows * kApStrip + kApWarps * kApLag * kApVPitch;  // [G][TS]
   const float2 *src = p.img + (long long)ay * p.sr * p.ld + (long long)ax0 * p.sc;
-  for (int e = tid; e < p.an * kApStrip; e += kApWarps * 32) {
+  for (int e = tid; e < rows * kApStrip; e += kApThreads) {
     const int r = e >> 6, c = e & (kApStrip - 1);
-    As[e] = c < Sw ? __ldg(src + (long long)r * p.ld + c) : make_float2(0.f, 0.f);
+    As[e] = (c < Sw && r < p.an) ? __ldg(src + (long long)r * p.ld + c) : make_float2(0.f, 0.f);
   }
   __syncthreads();
 
   float2 *Rg = p.R + ((long long)ay * p.nc + ax0) * DD * DD;
+  DivSmall divP, divPP;
+  divP.init(P);
+  divPP.init(PP);
+  const int npos = (P + kApLag - 1) / kApLag, nneg = (P - 1 + kApLag - 1) / kApLag;
   for (int dc = 0; dc < Q; ++dc) {
     const int J = Q - dc, ncol = Sw - dc;  // output columns; strip columns with a partner
-    const int nd = dc ? 2 * P - 1 : P;
-    // row lags in decreasing output rows (0, 1, -1, 2, -2, ...), warps in turn
-    for (int k = warp; k < nd; k += kApWarps) {
-      const int d = dc ? ((k & 1) ? (k + 1) >> 1 : -(k >> 1)) : k;
-      const int I = P - (d < 0 ? -d : d), i0 = d < 0 ? -d : 0;
-      // ---- column sums of the products, walked down the diagonal --------
-      // The products of rows r < I - 1 leave the box at output row r + 1:
-      // they are kept in row r + 1 of the warp's column-sum buffer, which
-      // that output row overwrites after reading them.
-      const int o1 = lane + 32 < ncol ? 32 : 0;  // the lane's second column (or its first again)
-      const float2 *pa = As + i0 * kApStrip + lane;
-      const float2 *pb = As + (i0 + d) * kApStrip + lane + dc;
-      float2 *vw = Vw + lane;
-      float2 V0 = make_float2(0.f, 0.f), V1 = V0, U0 = V0, U1 = V0;
-      const int nk = min(I - 1, Hb);  // kept rows among the seed's
-      int r = 0;
-      for (; r < nk; ++r) {
-        const int o = r * kApStrip;
-        const float2 x0 = ap_prod(pa[o], pb[o]), x1 = ap_prod(pa[o + o1], pb[o + o1]);
-        vw[(r + 1) * kApVPitch] = x0;
-        vw[(r + 1) * kApVPitch + 32] = x1;
-        V0.x += x0.x;
-        V0.y += x0.y;
-        V1.x += x1.x;
-        V1.y += x1.y;
-      }
-      for (; r + 1 < Hb; r += 2) {
-        const int o = r * kApStrip;
-        cmac_conj(V0, pa[o], pb[o]);
-        cmac_conj(V1, pa[o + o1], pb[o + o1]);
-        cmac_conj(U0, pa[o + kApStrip], pb[o + kApStrip]);
-        cmac_conj(U1, pa[o + kApStrip + o1], pb[o + kApStrip + o1]);
-      }
-      if (r < Hb) {
-        const int o = r * kApStrip;
-        cmac_conj(V0, pa[o], pb[o]);
-        cmac_conj(V1, pa[o + o1], pb[o + o1]);
-      }
-      V0.x += U0.x;
-      V0.y += U0.y;
-      V1.x += U1.x;
-      V1.y += U1.y;
-      vw[0] = V0;
-      vw[32] = V1;
-      for (int s = 1; s < I; ++s) {  // row s - 1 leaves the box, row s - 1 + Hb enters
-        const int rin = s - 1 + Hb, oi = rin * kApStrip;
-        const float2 x0 = ap_prod(pa[oi], pb[oi]), x1 = ap_prod(pa[oi + o1], pb[oi + o1]);
-        if (rin < I - 1) {  // a box shorter than the walk: the entering row leaves later
-          vw[(rin + 1) * kApVPitch] = x0;
-          vw[(rin + 1) * kApVPitch + 32] = x1;
-        }
-        const float2 y0 = vw[s * kApVPitch], y1 = vw[s * kApVPitch + 32];
-        V0.x += x0.x - y0.x;
-        V0.y += x0.y - y0.y;
-        V1.x += x1.x - y1.x;
-        V1.y += x1.y - y1.y;
-        vw[s * kApVPitch] = V0;
-        vw[s * kApVPitch + 32] = V1;
-      }
-      __syncwarp();
-      // ---- window sums along the columns, one (aperture, output row) a
-      // lane; output (s, j) is entry (i0 + s, i0 + s + d) of block j
-      for (int q = lane; q < Gc * I; q += 32) {
-        const int ap = q / I, s = q - ap * I;
-        const unsigned long long *v =
-            (const unsigned long long *)(Vw + s * kApVPitch + ap * p.sc);
-        unsigned long long W = v[0], W2 = 0ull;
-        int m = 1;
-        for (; m + 1 < Wd; m += 2) {
-          W = ap_add2(W, v[m]);
-          W2 = ap_add2(W2, v[m + 1]);
-        }
-        if (m < Wd) W = ap_add2(W, v[m]);
-        W = ap_add2(W, W2);
-        unsigned long long *t =
-            (unsigned long long *)(T + ap * p.TS + (i0 + s) * P + i0 + s + d);
-        t[0] = W;
-        for (int j = 1; j < J; ++j) {  // column j - 1 leaves the window, j - 1 + Wd enters
-          W = ap_add2(W, ap_sub2(v[j - 1 + Wd], v[j - 1]));
-          t[j * PP] = W;
-        }
-      }
-      __syncwarp();  // the column sums are read before the next row lag overwrites them
+    // groups in decreasing output rows: dr >= 0 from d0 = 0 and, for dc > 0,
+    // dr < 0 from d0 = 1, alternately; dealt to the warps in a snake
+    const int nu = dc ? npos + nneg : npos;
+    for (int u = 0; u < nu; ++u) {
+      const int rnd = u / kApWarps, pos = u - rnd * kApWarps;
+      if ((rnd & 1 ? kApWarps - 1 - pos : pos) != warp) continue;
+      if (dc && (u & 1))
+        ap_group<true>(p, As, Vw, T, lane, dc, 1 + (u >> 1) * kApLag, Gc, ncol);
+      else
+        ap_group<false>(p, As, Vw, T, lane, dc, (dc ? u >> 1 : u) * kApLag, Gc, ncol);
     }
     __syncthreads();
     // ---- R blocks of this lag: (j, j + dc), and for dc > 0 the mirrors
-    // (j + dc, j). The two thread halves take alternate j, a thread the
-    // entries w, w + 128, ... of each block.
-    const int half = tid >> 7;
-    for (int w = tid & 127; w < PP; w += 128) {
-      const int row = w / P, col = w - row * P;
-      const int up = row * P + col, lo = col * P + row;  // entry (row, col) and its transpose
-      const bool below = row > col;
-      const float rK = p.rK;
-      for (int ap = 0; ap < Gc; ++ap) {
-        const float2 *Ta = T + ap * p.TS;
-        float2 *Ra = Rg + (long long)ap * DD * DD + (long long)row * DD + col;
-        for (int j = half; j < J; j += 2) {
-          const float2 *Tj = Ta + j * PP;
-          if (dc == 0) {  // a diagonal block: entries below the diagonal mirror those above
-            float2 v = Tj[below ? lo : up];
-            v.x *= rK;
-            v.y = row == col ? 0.f : (below ? -v.y : v.y) * rK;
-            Ra[(long long)P * j * DD + P * j] = v;
-          } else {
-            float2 v = Tj[up];
-            v.x *= rK;
-            v.y *= rK;
-            Ra[(long long)P * j * DD + P * (j + dc)] = v;
-            v = Tj[lo];  // block (j + dc, j): entry (row, col) is the conjugate of (col, row)
-            v.x *= rK;
-            v.y = -v.y * rK;
-            Ra[(long long)P * (j + dc) * DD + P * j] = v;
-          }
+    // (j + dc, j); a thread the entries e = tid, tid + 128, ... of (j, entry)
+    const float rK = p.rK;
+    for (int ap = 0; ap < Gc; ++ap) {
+      const float2 *Ta = T + ap * p.TS;
+      float2 *Ra = Rg + (long long)ap * DD * DD;
+      for (int e = tid; e < J * PP; e += kApThreads) {
+        const int j = divPP.q(e), w = e - j * PP;
+        const int row = divP.q(w), col = w - row * P;
+        const float2 *Tj = Ta + j * PP;
+        float2 *Rr = Ra + (long long)row * DD + col;
+        if (dc == 0) {  // a diagonal block: entries below the diagonal mirror those above
+          const bool below = row > col;
+          float2 v = Tj[below ? col * P + row : w];
+          v.x *= rK;
+          v.y = row == col ? 0.f : (below ? -v.y : v.y) * rK;
+          Rr[(long long)P * j * DD + P * j] = v;
+        } else {
+          float2 v = Tj[w];
+          v.x *= rK;
+          v.y *= rK;
+          Rr[(long long)P * j * DD + P * (j + dc)] = v;
+          v = Tj[col * P + row];  // block (j + dc, j): entry (row, col) is the conjugate of (col, row)
+          v.x *= rK;
+          v.y = -v.y * rK;
+          Rr[(long long)P * (j + dc) * DD + P * j] = v;
         }
       }
     }
@@ -268,6 +331,6 @@ extern "C" cov_status cov_estimate_apertures(const void *image, cov_dtype dtype,
   const long long K = (long long)(ap_n - P + 1) * (ap_m - Q + 1);
   p.rK = norm == COV_MEAN ? 1.0f / (float)K : 1.0f;
   const long long grid = nr * p.groups;
-  k_apertures<<<(unsigned)grid, kApWarps * 32, smem, (cudaStream_t)stream>>>(p);
+  k_apertures<<<(unsigned)grid, kApThreads, smem, (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
 }
