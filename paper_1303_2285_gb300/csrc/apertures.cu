@@ -56,6 +56,8 @@ struct ApParams {
   int P, Q, G;         // window; apertures a CTA takes
   int TS;              // table entries per aperture (Q P^2)
   float rK;            // 1/K (COV_MEAN, the FP32 reciprocal) or 1 (COV_SUM)
+  int nsplit;          // CTAs a strip: column-lag ranges [dcb[i], dcb[i + 1])
+  int dcb[kApMaxPQ + 1];
 };
 
 // The lag's output table of one aperture holds its R blocks (j, j + dc),
@@ -94,11 +96,19 @@ __device__ __forceinline__ void ap_mac(float2 &acc, float2 shared_op, float2 sli
   else
     cmac_conj(acc, shared_op, sliding_op);
 }
+// acc -= a conj(b), the operands in the roles of ap_mac.
+__device__ __forceinline__ void cmsub_conj(float2 &acc, float2 a, float2 b) {
+  acc.x = __fmaf_rn(-a.x, b.x, acc.x);
+  acc.x = __fmaf_rn(-a.y, b.y, acc.x);
+  acc.y = __fmaf_rn(-a.y, b.x, acc.y);
+  acc.y = __fmaf_rn(a.x, b.y, acc.y);
+}
 template <bool NEG>
-__device__ __forceinline__ float2 ap_prod(float2 shared_op, float2 sliding_op) {
-  float2 v = make_float2(0.f, 0.f);
-  ap_mac<NEG>(v, shared_op, sliding_op);
-  return v;
+__device__ __forceinline__ void ap_msub(float2 &acc, float2 shared_op, float2 sliding_op) {
+  if (NEG)
+    cmsub_conj(acc, sliding_op, shared_op);
+  else
+    cmsub_conj(acc, shared_op, sliding_op);
 }
 // Packed FP32x2 add and subtract (each half rounded as add.rn.f32 / sub.rn.f32).
 __device__ __forceinline__ unsigned long long ap_add2(unsigned long long a, unsigned long long b) {
@@ -199,15 +209,11 @@ __device__ __forceinline__ void ap_group(const ApParams &p, const float2 *As, fl
     const float2 si0 = S0[ri * kApStrip], si1 = S1[ri * kApStrip];
     const float2 so0 = S0[ro * kApStrip], so1 = S1[ro * kApStrip];
 #pragma unroll
-    for (int k = 0; k < kApLag; ++k) {
-      const float2 x0 = ap_prod<NEG>(si0, L0[(ri + k) * kApStrip]);
-      const float2 y0 = ap_prod<NEG>(so0, L0[(ro + k) * kApStrip]);
-      const float2 x1 = ap_prod<NEG>(si1, L1[(ri + k) * kApStrip]);
-      const float2 y1 = ap_prod<NEG>(so1, L1[(ro + k) * kApStrip]);
-      V0[k].x += x0.x - y0.x;
-      V0[k].y += x0.y - y0.y;
-      V1[k].x += x1.x - y1.x;
-      V1[k].y += x1.y - y1.y;
+    for (int k = 0; k < kApLag; ++k) {  // the entering product added, the leaving one subtracted
+      ap_msub<NEG>(V0[k], so0, L0[(ro + k) * kApStrip]);
+      ap_msub<NEG>(V1[k], so1, L1[(ro + k) * kApStrip]);
+      ap_mac<NEG>(V0[k], si0, L0[(ri + k) * kApStrip]);
+      ap_mac<NEG>(V1[k], si1, L1[(ri + k) * kApStrip]);
     }
   }
 }
@@ -216,7 +222,8 @@ __global__ void __launch_bounds__(kApThreads, 4) k_apertures(ApParams p) {
   extern __shared__ __align__(16) unsigned char smem_ap[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int P = p.P, Q = p.Q, DD = P * Q, PP = P * P;
-  const int ay = blockIdx.x / p.groups, g = blockIdx.x - ay * p.groups;
+  const int strip = blockIdx.x / p.nsplit, part = blockIdx.x - strip * p.nsplit;
+  const int ay = strip / p.groups, g = strip - ay * p.groups;
   const int ax0 = g * p.G, Gc = min(p.G, p.nc - ax0);
   const int Sw = (Gc - 1) * p.sc + p.am;  // strip columns under the CTA's apertures
   const int rows = p.an + kApLag;
@@ -231,11 +238,10 @@ __global__ void __launch_bounds__(kApThreads, 4) k_apertures(ApParams p) {
   __syncthreads();
 
   float2 *Rg = p.R + ((long long)ay * p.nc + ax0) * DD * DD;
-  DivSmall divP, divPP;
+  DivSmall divP;
   divP.init(P);
-  divPP.init(PP);
   const int npos = (P + kApLag - 1) / kApLag, nneg = (P - 1 + kApLag - 1) / kApLag;
-  for (int dc = 0; dc < Q; ++dc) {
+  for (int dc = p.dcb[part]; dc < p.dcb[part + 1]; ++dc) {
     const int J = Q - dc, ncol = Sw - dc;  // output columns; strip columns with a partner
     // groups in decreasing output rows: dr >= 0 from d0 = 0 and, for dc > 0,
     // dr < 0 from d0 = 1, alternately; dealt to the warps in a snake
@@ -250,36 +256,87 @@ __global__ void __launch_bounds__(kApThreads, 4) k_apertures(ApParams p) {
     }
     __syncthreads();
     // ---- R blocks of this lag: (j, j + dc), and for dc > 0 the mirrors
-    // (j + dc, j); a thread the entries e = tid, tid + 128, ... of (j, entry)
+    // (j + dc, j); a thread the entries w = tid, tid + 128, ... of every block
     const float rK = p.rK;
-    for (int ap = 0; ap < Gc; ++ap) {
-      const float2 *Ta = T + ap * p.TS;
-      float2 *Ra = Rg + (long long)ap * DD * DD;
-      for (int e = tid; e < J * PP; e += kApThreads) {
-        const int j = divPP.q(e), w = e - j * PP;
-        const int row = divP.q(w), col = w - row * P;
-        const float2 *Tj = Ta + j * PP;
-        float2 *Rr = Ra + (long long)row * DD + col;
-        if (dc == 0) {  // a diagonal block: entries below the diagonal mirror those above
-          const bool below = row > col;
-          float2 v = Tj[below ? col * P + row : w];
+    for (int w = tid; w < PP; w += kApThreads) {
+      const int row = divP.q(w), col = w - row * P;
+      const int tw = row > col && dc == 0 ? col * P + row : w;  // dc = 0: mirror of the upper entry
+      const float im_sign = dc == 0 && row > col ? -rK : rK;
+      const int tlo = col * P + row;
+      for (int ap = 0; ap < Gc; ++ap) {
+        const float2 *Tj = T + ap * p.TS;
+        float2 *Rd = Rg + (long long)ap * DD * DD + (long long)row * DD + col + P * dc;  // block (0, dc)
+        float2 *Rm = Rg + (long long)ap * DD * DD + (long long)(row + P * dc) * DD + col;  // block (dc, 0)
+        const long long step = (long long)P * DD + P;  // to block (j + 1, j + 1 + dc)
+        for (int j = 0; j < J; ++j, Tj += PP, Rd += step, Rm += step) {
+          float2 v = Tj[tw];
           v.x *= rK;
-          v.y = row == col ? 0.f : (below ? -v.y : v.y) * rK;
-          Rr[(long long)P * j * DD + P * j] = v;
-        } else {
-          float2 v = Tj[w];
-          v.x *= rK;
-          v.y *= rK;
-          Rr[(long long)P * j * DD + P * (j + dc)] = v;
-          v = Tj[col * P + row];  // block (j + dc, j): entry (row, col) is the conjugate of (col, row)
-          v.x *= rK;
-          v.y = -v.y * rK;
-          Rr[(long long)P * (j + dc) * DD + P * j] = v;
+          v.y = dc == 0 && row == col ? 0.f : v.y * im_sign;
+          *Rd = v;
+          if (dc) {  // block (j + dc, j): entry (row, col) is the conjugate of (col, row)
+            float2 u = Tj[tlo];
+            u.x *= rK;
+            u.y = -u.y * rK;
+            *Rm = u;
+          }
         }
       }
     }
     __syncthreads();  // the table is read before the next lag overwrites it
   }
+}
+
+// Splits the column lags 0 .. Q-1 of each strip into p.nsplit contiguous
+// ranges of about equal work, one CTA each, so that the launch has some
+// sixteen CTAs per resident slot and its last wave is short. Work of lag dc,
+// in warp instructions: the products of the groups' seeds and walks (four
+// FMA each), the output rows' window sums, the R elements written.
+void ap_split_lags(ApParams &p, int an, int am, int P, int Q, int G, long long strips, size_t smem) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  const long long per_sm = std::max<long long>(1, std::min<long long>(4, (228 << 10) / (smem + 1024)));
+  const long long slots = sms * per_sm;
+  int n = 1;
+  while (n < Q && strips * n < 16 * slots) ++n;
+  const int Hb = an - P + 1, Wd = am - Q + 1;
+  double cost[kApMaxPQ];
+  for (int dc = 0; dc < Q; ++dc) {
+    const int J = Q - dc;
+    double c = 0;
+    for (int neg = 0; neg < (dc ? 2 : 1); ++neg)
+      for (int d0 = neg; d0 < P; d0 += kApLag) {
+        const int Imax = P - d0;
+        c += 8.0 * kApLag * (Hb + 2.0 * (Imax - 1)) + 2.0 * Imax * (Wd + 3.0 * J);
+      }
+    c += (double)G * J * P * P * (dc ? 2 : 1) * 6.0 / 32.0;
+    cost[dc] = c;
+  }
+  // contiguous ranges with the smallest largest share: best[i][k] = the
+  // smallest largest range cost of lags 0 .. i-1 in k ranges
+  double best[kApMaxPQ + 1][kApMaxPQ + 1];
+  int cut[kApMaxPQ + 1][kApMaxPQ + 1];
+  for (int i = 0; i <= Q; ++i)
+    for (int k = 0; k <= n; ++k) best[i][k] = 1e300, cut[i][k] = 0;
+  best[0][0] = 0;
+  for (int k = 1; k <= n; ++k)
+    for (int i = k; i <= Q; ++i) {
+      double tail = 0;
+      for (int j = i - 1; j >= k - 1; --j) {  // range [j, i)
+        tail += cost[j];
+        const double v = std::max(best[j][k - 1], tail);
+        if (v < best[i][k]) best[i][k] = v, cut[i][k] = j;
+      }
+    }
+  p.nsplit = n;
+  for (int k = n, i = Q; k > 0; --k) {
+    p.dcb[k] = i;
+    i = cut[i][k];
+  }
+  p.dcb[0] = 0;
 }
 
 }  // namespace
@@ -315,6 +372,7 @@ extern "C" cov_status cov_estimate_apertures(const void *image, cov_dtype dtype,
     return COV_ECUDA;
   }
   ApParams p;
+  ap_split_lags(p, ap_n, ap_m, P, Q, G, nr * ((nc + G - 1) / G), smem);
   p.img = (const float2 *)image;
   p.ld = ld;
   p.R = (float2 *)R;
@@ -330,7 +388,8 @@ extern "C" cov_status cov_estimate_apertures(const void *image, cov_dtype dtype,
   p.TS = ap_table_entries(P, Q);
   const long long K = (long long)(ap_n - P + 1) * (ap_m - Q + 1);
   p.rK = norm == COV_MEAN ? 1.0f / (float)K : 1.0f;
-  const long long grid = nr * p.groups;
+  const long long grid = nr * p.groups * p.nsplit;
+  if (grid > 0x7fffffffLL) return COV_EUNSUPPORTED;
   k_apertures<<<(unsigned)grid, kApThreads, smem, (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? COV_OK : COV_ECUDA;
 }
