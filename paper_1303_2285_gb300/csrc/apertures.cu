@@ -272,12 +272,12 @@ __global__ void __launch_bounds__(kApThreads, 4) k_apertures(ApParams p) {
           float2 v = Tj[tw];
           v.x *= rK;
           v.y = dc == 0 && row == col ? 0.f : v.y * im_sign;
-          *Rd = v;
+          __stcs(Rd, v);  // R is written once and not read back: evict first
           if (dc) {  // block (j + dc, j): entry (row, col) is the conjugate of (col, row)
             float2 u = Tj[tlo];
             u.x *= rK;
             u.y = -u.y * rK;
-            *Rm = u;
+            __stcs(Rm, u);
           }
         }
       }
