@@ -11,7 +11,11 @@ restated here in plain NumPy and held to the oracle:
 * the split-precision operand formats of the GEMM form (TF32 hi/lo, BF16
   hi/mid/lo) and the error of the products they keep;
 * the stencil form of the adjoint: dA as a sum over combinations of
-  class-dependent weights times shifted A.
+  class-dependent weights times shifted A;
+* the strip form of the aperture batch (Section 2.3): the apertures side by
+  side share one product image per combination over their strip, column sums
+  walked down it and window sums slid along each aperture's output columns
+  give every aperture's R blocks.
 
 No GPU is needed; integer inputs make the sums exact, so those comparisons are
 bit for bit.
@@ -273,3 +277,59 @@ def test_stencil_weights_depend_on_the_class_only(N, M, P, Q):
                     rep = stencil_weight(H, N, M, P, Q, dr, dc, class_row(row_class(n, N, P), N, P),
                                          class_row(row_class(m, M, Q), M, Q))
                     assert stencil_weight(H, N, M, P, Q, dr, dc, n, m) == rep
+
+
+@pytest.mark.parametrize("H,W,ap,step,P,Q", [(64, 80, (25, 25), (10, 10), 10, 10),
+                                             (47, 51, (20, 17), (9, 5), 4, 3),
+                                             (30, 70, (12, 30), (3, 7), 5, 9),
+                                             (20, 40, (20, 20), (2, 2), 16, 4)])
+def test_strip_of_apertures(oracle_mod, H, W, ap, step, P, Q):
+    """Apertures of one row of apertures, side by side in a strip of at most 64
+    columns: per combination (dr, dc) the products over the strip are formed
+    once, column sums over the Hb = ap_n - P + 1 box rows are walked down the
+    output rows (entering row added, leaving row subtracted), and aperture
+    k's output (s, j) is the sum of the Wd = ap_m - Q + 1 column sums from
+    column k * step_c + j, slid along j. The blocks (j, j + dc) and their
+    conjugate mirrors then fill each aperture's R exactly (integer input)."""
+    A = wl.integer_valued((H, W), 77 + H)
+    an, am = ap
+    sr, sc = step
+    nr, nc = (H - an) // sr + 1, (W - am) // sc + 1
+    G = max(1, min(nc, 1 + (64 - am) // sc))
+    Hb, Wd, D = an - P + 1, am - Q + 1, P * Q
+    formed = 0
+    for a in range(nr):
+        for g0 in range(0, nc, G):
+            Gc = min(G, nc - g0)
+            Sw = (Gc - 1) * sc + am
+            S = A[a * sr:a * sr + an, g0 * sc:g0 * sc + Sw]
+            Rs = np.zeros((Gc, D, D), dtype=complex)
+            for dc in range(Q):
+                for dr in (range(P) if dc == 0 else range(-(P - 1), P)):
+                    i0, I = max(0, -dr), P - abs(dr)
+                    rows = Hb + I - 1
+                    # the strip's product image, once per combination
+                    Pi = S[i0:i0 + rows, :Sw - dc] * np.conj(S[i0 + dr:i0 + dr + rows, dc:Sw])
+                    formed += Pi.size
+                    V = np.zeros((I, Sw - dc), dtype=complex)
+                    V[0] = Pi[:Hb].sum(axis=0)
+                    for s in range(1, I):
+                        V[s] = V[s - 1] + Pi[s - 1 + Hb] - Pi[s - 1]
+                    for k in range(Gc):
+                        for s in range(I):
+                            v = V[s, k * sc:k * sc + Wd + Q - dc - 1]
+                            w = v[:Wd].sum()
+                            for j in range(Q - dc):
+                                if j:
+                                    w = w + v[j - 1 + Wd] - v[j - 1]
+                                i = i0 + s
+                                Rs[k, i + P * j, i + dr + P * (j + dc)] = w
+                                Rs[k, i + dr + P * (j + dc), i + P * j] = np.conj(w)
+            for k in range(Gc):
+                sub = A[a * sr:a * sr + an, (g0 + k) * sc:(g0 + k) * sc + am]
+                want = oracle_mod.cov_window(sub, P, Q, mean=False)
+                assert np.array_equal(Rs[k], want), (a, g0 + k)
+    per_aperture = nr * nc * sum((an - abs(dr)) * (am - dc) for dc in range(Q)
+                                 for dr in (range(P) if dc == 0 else range(-(P - 1), P)))
+    if G > 1:
+        assert formed < per_aperture  # products shared by the apertures of a strip
