@@ -12,14 +12,17 @@
 //    and walks their column sums down the diagonal: the sum over the box rows
 //    of the first output row, then per output row one product row in and one
 //    out (Eq. 3.7-3.8). The four lags share one operand row and slide along
-//    the other, so that in the seed one row of the first operand and seven
-//    rows of the second serve four rows of products for all four lags;
+//    the other: the seed, blocked by four rows, loads four rows of the shared
+//    operand and seven of the sliding one for 16 products a column;
 //  - after each output row, builds each aperture's outputs of that row as
 //    sums of Wd consecutive column sums, slid along the output columns (one
 //    column sum in, one out), one (aperture, lag) a lane, into a shared-
 //    memory table of the lag's R blocks.
 // The CTA then writes the R blocks of that column lag, (j, j + dc) and their
-// conjugate mirrors (j + dc, j), in runs of P contiguous elements.
+// conjugate mirrors (j + dc, j), in runs of P contiguous elements. A strip's
+// column lags are split into contiguous ranges of about equal work, one CTA
+// each (the ranges write disjoint blocks), so that the launch's last wave is
+// short.
 //
 // Against one CTA per aperture (the batched box form), a product under k
 // apertures of the strip is formed once instead of k times, every lane holds
