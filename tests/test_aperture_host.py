@@ -80,3 +80,11 @@ def test_quarter_million_apertures_plan():
 ])
 def test_strip_argument_checks(args, status):
     assert cov.load().cov_estimate_apertures(*args, None) == status
+
+
+def test_strip_wrapper_rejects_host_and_wrong_dtype_images():
+    import torch
+    with pytest.raises(ValueError):
+        cov.apertures(torch.zeros((30, 30), dtype=torch.complex64), (10, 10), (10, 10), 4, 4)
+    with pytest.raises(ValueError):
+        cov.apertures(torch.zeros((30, 30), dtype=torch.complex128), (10, 10), (10, 10), 4, 4)
